@@ -1,0 +1,285 @@
+"""FP64 CPU oracle for sparse CP tensor completion (arXiv:1910.02371).
+
+TEST INFRASTRUCTURE ONLY: tests/, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+package; the product path never does.  It shares no code with the CUDA
+library.
+
+The arithmetic lives in ``oracle.c`` (plain loops in double precision, see
+``oracle.h``); this module only marshals numpy arrays and composes those
+routines the way the paper composes its kernels:
+
+* ALS sweep (Sec. 2.2; Sec. 4, "ALS solve for one factor matrix"): for each
+  mode in turn, the right-hand side is the MTTKRP of the observed values, then
+  Solve Factor with the pattern (unit weights) and lambda; the new factor is
+  used at once (block Gauss-Seidel, Appendix A).
+* Gauss-Newton step (Sec. 2.5): gradient, block-diagonal preconditioner (the
+  diagonal blocks of the Gauss-Newton matrix, applied through Solve Factor with
+  weights phi'' and regularization 2 lambda), preconditioned CG from zero for a
+  fixed number of iterations, then the update.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+LOSSES = {"ls": 0, "poisson_log": 1, "poisson_id": 2}
+
+OK, ERR_ARG, ERR_RANGE, ERR_NOT_SPD, ERR_DOMAIN = 0, 1, 2, 6, 7
+
+
+class OracleError(RuntimeError):
+    def __init__(self, rc, what):
+        super().__init__(f"oracle {what} returned {rc}")
+        self.rc = rc
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so with the host gcc."""
+    src = os.path.join(_HERE, "oracle.c")
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < max(
+            os.path.getmtime(src), os.path.getmtime(os.path.join(_HERE, "oracle.h"))):
+        tmp = _SO + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
+                               "-std=c11", "-o", tmp, src, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_SO)
+        P = ctypes.c_void_p
+        i64 = ctypes.c_int64
+        for name, args in {
+            "orc_counting_sort": [i64, P, i64, P, P],
+            "orc_tttp": [ctypes.c_int, P, i64, P, P, ctypes.c_int, P, P],
+            "orc_mttkrp": [ctypes.c_int, P, i64, P, P, ctypes.c_int, P, ctypes.c_int, P],
+            "orc_solve_factor": [ctypes.c_int, P, i64, P, P, ctypes.c_int, P, ctypes.c_int,
+                                 P, ctypes.c_double, P, P],
+            "orc_loss_terms": [ctypes.c_int, i64, P, P, P, P, P],
+            "orc_loss_grad": [ctypes.c_int, P, i64, P, P, ctypes.c_int, P, ctypes.c_int,
+                              ctypes.c_double, P, P],
+            "orc_ggn_matvec": [ctypes.c_int, P, i64, P, P, ctypes.c_int, P, ctypes.c_int,
+                               ctypes.c_double, P, P],
+        }.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+# ---------------------------------------------------------------- marshalling
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+class _Ptrs:
+    """A C array of pointers plus the arrays it keeps alive."""
+
+    def __init__(self, arrays):
+        self.keep = list(arrays)
+        self.arr = (ctypes.c_void_p * max(1, len(self.keep)))(
+            *[None if a is None else a.ctypes.data for a in self.keep])
+
+    @property
+    def ptr(self):
+        return ctypes.cast(self.arr, ctypes.c_void_p)
+
+
+def _dims(dims):
+    return np.ascontiguousarray(dims, dtype=np.int64)
+
+
+def _idx(idx):
+    return _Ptrs([np.ascontiguousarray(c, dtype=np.int32) for c in idx])
+
+
+def _check(rc, what, allow=()):
+    if rc != OK and rc not in allow:
+        raise OracleError(rc, what)
+    return rc
+
+
+# ---------------------------------------------------------------- kernels
+def counting_sort(key, I):
+    """Stable counting sort by key (Sec. 3.4): (perm, row_ptr)."""
+    key = np.ascontiguousarray(key, dtype=np.int32)
+    m = key.shape[0]
+    perm = np.zeros(max(m, 1), np.int64)
+    row_ptr = np.zeros(int(I) + 1, np.int64)
+    _check(lib().orc_counting_sort(m, _p(key), int(I), _p(perm), _p(row_ptr)), "counting_sort")
+    return perm[:m], row_ptr
+
+
+def pattern(dims, idx, mode):
+    """The mode-`mode` view of the pattern: perm, row_ptr, nonempty rows."""
+    perm, row_ptr = counting_sort(idx[mode], dims[mode])
+    nonempty = np.nonzero(np.diff(row_ptr) > 0)[0].astype(np.int32)
+    return perm, row_ptr, nonempty
+
+
+def tttp(dims, idx, s, factors):
+    """Sec. 3.3: x_e = s_e sum_r prod_{provided n} A^(n)[i_n(e), r]."""
+    N = len(dims)
+    m = len(idx[0])
+    R = next((a.shape[1] for a in factors if a is not None), 1)
+    fs = [None if a is None else _f64(a) for a in factors]
+    x = np.zeros(max(m, 1))
+    ix = _idx(idx)
+    sp = None if s is None else _f64(s)
+    _check(lib().orc_tttp(N, _p(_dims(dims)), m, ix.ptr, _p(sp), R, _Ptrs(fs).ptr, _p(x)), "tttp")
+    return x[:m]
+
+
+def mttkrp(dims, idx, s, factors, mode):
+    """Sec. 3.2: pattern-restricted MTTKRP into mode `mode`."""
+    N = len(dims)
+    m = len(idx[0])
+    R = next(a.shape[1] for i, a in enumerate(factors) if a is not None and i != mode)
+    fs = [None if a is None else _f64(a) for a in factors]
+    out = np.zeros((int(dims[mode]), R))
+    sp = None if s is None else _f64(s)
+    _check(lib().orc_mttkrp(N, _p(_dims(dims)), m, _idx(idx).ptr, _p(sp), R, _Ptrs(fs).ptr,
+                            mode, _p(out)), "mttkrp")
+    return out
+
+
+def solve_factor(dims, idx, s, factors, mode, rhs, lam, out=None):
+    """Sec. 3.4: per-row (G_i + lam I) a_i = rhs_i.  Returns (out, status, rc).
+    Rows whose system is not positive definite keep the contents of `out`."""
+    N = len(dims)
+    m = len(idx[0])
+    rhs = _f64(rhs)
+    R = rhs.shape[1]
+    fs = [None if a is None else _f64(a) for a in factors]
+    out = np.zeros_like(rhs) if out is None else _f64(out).copy()
+    status = np.zeros(int(dims[mode]), np.int8)
+    sp = None if s is None else _f64(s)
+    rc = lib().orc_solve_factor(N, _p(_dims(dims)), m, _idx(idx).ptr, _p(sp), R, _Ptrs(fs).ptr,
+                                mode, _p(rhs), float(lam), _p(out), _p(status))
+    _check(rc, "solve_factor", allow=(ERR_NOT_SPD,))
+    return out, status, rc
+
+
+def loss_terms(loss, t, model):
+    """phi, phi', phi'' (Sec. 2.1, Table 1, Sec. 5.7)."""
+    t = _f64(t)
+    model = _f64(model)
+    m = t.shape[0]
+    phi, d1, d2 = (np.zeros(max(m, 1)) for _ in range(3))
+    _check(lib().orc_loss_terms(LOSSES[loss], m, _p(t), _p(model), _p(phi), _p(d1), _p(d2)),
+           "loss_terms")
+    return phi[:m], d1[:m], d2[:m]
+
+
+def loss_grad(dims, idx, t, factors, loss, lam, want_grad=True):
+    """eq. obj and Table 1: (f, [grad^(d)])."""
+    N = len(dims)
+    m = len(idx[0])
+    R = factors[0].shape[1]
+    fs = [_f64(a) for a in factors]
+    f = np.zeros(1)
+    grads = [np.zeros((int(I), R)) for I in dims] if want_grad else None
+    gp = _Ptrs(grads).ptr if want_grad else None
+    _check(lib().orc_loss_grad(N, _p(_dims(dims)), m, _idx(idx).ptr, _p(_f64(t)), R,
+                               _Ptrs(fs).ptr, LOSSES[loss], float(lam), _p(f), gp), "loss_grad")
+    return float(f[0]), grads
+
+
+def ggn_matvec(dims, idx, t, factors, loss, lam, x):
+    """Sec. 2.5: y = (J^T diag(phi'') J + 2 lam I) x, block per mode."""
+    N = len(dims)
+    m = len(idx[0])
+    R = factors[0].shape[1]
+    fs = [_f64(a) for a in factors]
+    xs = [_f64(a) for a in x]
+    ys = [np.zeros((int(I), R)) for I in dims]
+    _check(lib().orc_ggn_matvec(N, _p(_dims(dims)), m, _idx(idx).ptr, _p(_f64(t)), R,
+                                _Ptrs(fs).ptr, LOSSES[loss], float(lam), _Ptrs(xs).ptr,
+                                _Ptrs(ys).ptr), "ggn_matvec")
+    return ys
+
+
+# ---------------------------------------------------------------- compositions
+def model_entries(dims, idx, factors):
+    """m_e = <u_i, v_j, w_k> at the observed coordinates (eq. 2), via TTTP."""
+    return tttp(dims, idx, None, factors)
+
+
+def als_sweep(dims, idx, t, factors, lam):
+    """One ALS sweep for least squares (Sec. 2.2; Sec. 4 listing for one factor):
+    rhs = MTTKRP(T, d); A^(d) = Solve_Factor(Omega, d, rhs, lam), modes in order."""
+    A = [_f64(a).copy() for a in factors]
+    for d in range(len(dims)):
+        rhs = mttkrp(dims, idx, t, A, d)
+        A[d], _, rc = solve_factor(dims, idx, None, A, d, rhs, lam, out=A[d])
+        if rc != OK:
+            raise OracleError(rc, "als_sweep")
+    return A
+
+
+def precond_apply(dims, idx, t, factors, loss, lam, r):
+    """Block-diagonal preconditioner of the Gauss-Newton matrix (Sec. 2.5):
+    per mode d and row k, (sum phi'' h h^T + 2 lam I)^-1 r^(d)_k -- Solve Factor
+    with weights phi'' and regularization 2 lam."""
+    model = model_entries(dims, idx, factors)
+    _, _, d2 = loss_terms(loss, t, model)
+    out = []
+    for d in range(len(dims)):
+        z, _, rc = solve_factor(dims, idx, d2, factors, d, r[d], 2.0 * lam)
+        if rc != OK:
+            raise OracleError(rc, "precond_apply")
+        out.append(z)
+    return out
+
+
+def _dot(a, b):
+    return float(sum(np.vdot(x.ravel(), y.ravel()) for x, y in zip(a, b)))
+
+
+def pcg(dims, idx, t, factors, loss, lam, b, n_iter, precondition=True):
+    """Preconditioned CG on the Gauss-Newton system from x0 = 0 for a fixed
+    number of iterations (Hestenes-Stiefel recurrences)."""
+    x = [np.zeros_like(_f64(v)) for v in b]
+    r = [_f64(v).copy() for v in b]
+    z = precond_apply(dims, idx, t, factors, loss, lam, r) if precondition else [v.copy() for v in r]
+    p = [v.copy() for v in z]
+    rz = _dot(r, z)
+    for _ in range(n_iter):
+        Ap = ggn_matvec(dims, idx, t, factors, loss, lam, p)
+        alpha = rz / _dot(p, Ap)
+        x = [xi + alpha * pi for xi, pi in zip(x, p)]
+        r = [ri - alpha * api for ri, api in zip(r, Ap)]
+        z = precond_apply(dims, idx, t, factors, loss, lam, r) if precondition else [v.copy() for v in r]
+        rz_new = _dot(r, z)
+        beta = rz_new / rz
+        rz = rz_new
+        p = [zi + beta * pi for zi, pi in zip(z, p)]
+    return x
+
+
+def ggn_step(dims, idx, t, factors, loss, lam, n_iter, precondition=True):
+    """One Gauss-Newton step (Sec. 2.5): solve H dx = -grad by PCG, A += dx."""
+    _, g = loss_grad(dims, idx, t, factors, loss, lam)
+    dx = pcg(dims, idx, t, factors, loss, lam, [-v for v in g], n_iter, precondition)
+    return [_f64(a) + d for a, d in zip(factors, dx)]
+
+
+def objective(dims, idx, t, factors, loss, lam):
+    return loss_grad(dims, idx, t, factors, loss, lam, want_grad=False)[0]
