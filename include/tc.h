@@ -1,0 +1,220 @@
+/*
+ * tc.h -- C ABI of the GB300 (sm_103a) sparse CP tensor-completion kernels.
+ *
+ * The operations are the multi-tensor kernels of "Parallel Algorithms for
+ * Tensor Completion in the CP Format" (arXiv:1910.02371):
+ *   - the per-mode sorted pattern of the observed entries   (Sec. 3.4, counting sort)
+ *   - TTTP, the sampled multilinear inner product            (Sec. 3.3)
+ *   - MTTKRP restricted to the observed entries              (Sec. 3.2, Appendix A)
+ *   - Solve Factor, the per-row regularized normal equations (Sec. 3.4, Sec. 2.2)
+ *   - the objective and its gradient for a generalized loss  (eq. obj, Table 1)
+ *   - the Gauss-Newton matrix-vector product                 (Sec. 2.5, Appendix A)
+ *   - the block-diagonal preconditioner and the PCG driver   (Sec. 2.5)
+ * for order-3 tensors (the order the paper develops its algorithms for).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Pointers.  Arrays of nonzeros, factor matrices and outputs are DEVICE
+ * pointers on the pattern's device; `dims`, pointer arrays (`const void *const
+ * *factors` etc.) and scalars are host values.  The caller owns every buffer it
+ * passes; a tc_pattern owns the sorted copies it makes and frees them in
+ * tc_pattern_destroy.  No call keeps a caller pointer after it returns, except
+ * that a tc_cg object keeps the ones given at its creation (see below).
+ *
+ * Layout.  A factor matrix A^(n) is row-major I_n x R with row stride R, in the
+ * pattern's dtype (float or double).  Index arrays are int32.  Every array of
+ * length nnz that crosses the ABI is in PATTERN ORDER: the nonzeros sorted by
+ * their mode-0 index, equal indices kept in input order (stable).  perm of mode
+ * 0 (tc_pattern_view) maps pattern order back to input order.
+ *
+ * Weights.  Calls that take per-nonzero weights accept
+ *   TC_W_ONE    -- s_e = 1: the pattern Omega-hat itself,
+ *   TC_W_VALUES -- the values given to tc_build_pattern (the tensor T),
+ *   TC_W_ARRAY  -- a caller array `s` of nnz weights in pattern order.
+ *
+ * Streams.  Every call is asynchronous on `stream` (a cudaStream_t; NULL is the
+ * legacy default stream) and records the device work in stream order.
+ * Argument errors are returned at once and launch nothing.  Errors found on
+ * the device (an index out of range, a system that is not positive definite,
+ * a loss evaluated outside its domain, a CG breakdown) set the pattern's device
+ * status word; tc_last_error synchronizes the stream and returns and clears it.
+ * No kernel traps or asserts.
+ *
+ * Sizes.  nnz and all offsets are int64.  R (the CP rank) is 1..64.
+ * nnz == 0 is legal and gives zero outputs.
+ *
+ * Threading.  Calls on different patterns are independent.  Calls on one
+ * pattern from several host threads must be serialized by the caller.
+ */
+#ifndef TC_H
+#define TC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *tc_stream_t; /* the same type as cudaStream_t */
+
+typedef enum {
+    TC_OK = 0,
+    TC_ERR_ARG = 1,         /* bad argument: NULL pointer, size, mode, rank, dtype */
+    TC_ERR_RANGE = 2,       /* an index outside [0, I_n) */
+    TC_ERR_DUPLICATE = 3,   /* a coordinate occurs twice (checked on request) */
+    TC_ERR_OOM = 4,         /* device allocation failed */
+    TC_ERR_CUDA = 5,        /* a CUDA runtime call failed */
+    TC_ERR_NOT_SPD = 6,     /* a row system had a pivot <= 0; that row was not written */
+    TC_ERR_DOMAIN = 7,      /* Poisson identity-link loss at a model entry <= 0 */
+    TC_ERR_BREAKDOWN = 8,   /* CG: p^T H p <= 0; later iterations left x unchanged */
+    TC_ERR_UNSUPPORTED = 9  /* a valid request this build does not implement */
+} tc_status;
+
+typedef enum { TC_F32 = 0, TC_F64 = 1 } tc_dtype;
+
+/* phi(t, m) of eq. obj: least squares (t - m)^2 (Sec. 2.1); Poisson with the
+ * log link exp(m) - t m (Sec. 5.7); Poisson with the identity link
+ * m - t log m, m > 0 (Sec. 2.1). */
+typedef enum { TC_LOSS_LS = 0, TC_LOSS_POISSON_LOG = 1, TC_LOSS_POISSON_ID = 2 } tc_loss;
+
+typedef enum { TC_W_ONE = 0, TC_W_VALUES = 1, TC_W_ARRAY = 2 } tc_weights;
+
+/* tc_build_pattern flags */
+#define TC_PATTERN_CHECK_DUPLICATES 1u  /* extra sort that rejects repeated coordinates */
+
+typedef struct tc_pattern tc_pattern;
+
+/* ------------------------------------------------------------------ pattern */
+
+/* Builds the per-mode sorted copies of a sparse tensor (Sec. 3.4: the data is
+ * sorted by the mode index with a counting sort so that each row's nonzeros are
+ * contiguous; Sec. 3.1: only nonempty rows are listed, as in the doubly
+ * compressed formats).
+ *   order   tensor order; must be 3.
+ *   dims    host int64[order], I_n >= 1 and I_n <= 2^31 - 1.
+ *   nnz     number of observed entries, >= 0.
+ *   idx     host array of `order` device int32 pointers idx[n][e], input order.
+ *   vals    device array of nnz values in input order (dtype), or NULL.
+ *   dtype   TC_F32 or TC_F64: the type of vals and of every factor used later.
+ * On success *out owns device copies; the call synchronizes `stream` once and
+ * reports TC_ERR_RANGE / TC_ERR_DUPLICATE directly (no pattern is returned). */
+tc_status tc_build_pattern(int order, const int64_t *dims, int64_t nnz,
+                           const int32_t *const *idx, const void *vals, tc_dtype dtype,
+                           unsigned flags, tc_stream_t stream, tc_pattern **out);
+
+/* Frees the pattern's device memory (after synchronizing its device). */
+tc_status tc_pattern_destroy(tc_pattern *p);
+
+/* Read-only device views of mode `mode`, for tests and callers that want the
+ * raw structure: row_ptr[I_mode + 1] (row i's nonzeros are sorted positions
+ * row_ptr[i] .. row_ptr[i+1]-1); perm[nnz] (sorted position -> input position;
+ * equal indices keep input order); nonempty_rows[n_nonempty] (ascending).
+ * Any output pointer may be NULL. */
+tc_status tc_pattern_view(const tc_pattern *p, int mode, const int64_t **row_ptr,
+                          const int64_t **perm, const int32_t **nonempty_rows,
+                          int64_t *n_nonempty);
+
+/* nnz, order, dims and dtype of a pattern (host values). */
+tc_status tc_pattern_info(const tc_pattern *p, int64_t *nnz, int *order, int64_t *dims,
+                          tc_dtype *dtype);
+
+/* Synchronizes `stream`, returns the first device error recorded on pattern p
+ * since the last call (TC_OK if none) and clears it. */
+tc_status tc_last_error(tc_pattern *p, tc_stream_t stream);
+
+/* ------------------------------------------------------------------ kernels */
+
+/* TTTP (Sec. 3.3): x_e = s_e * sum_{r<R} prod_{n : factors[n] != NULL} A^(n)[i_n(e), r].
+ * A NULL factor skips its mode; at least one factor must be given.
+ * x: device array of nnz outputs in pattern order (overwritten). */
+tc_status tc_tttp(const tc_pattern *p, tc_weights w, const void *s, int R,
+                  const void *const *factors, void *x, tc_stream_t stream);
+
+/* MTTKRP restricted to the pattern (Sec. 3.2; Appendix A, gradient as MTTKRP):
+ * out[i, r] (+)= sum_{e : i_mode(e) = i} s_e prod_{n != mode} A^(n)[i_n(e), r].
+ * out: device I_mode x R, overwritten (accumulate == 0) or added to.
+ * factors[mode] is not read and may be NULL. */
+tc_status tc_mttkrp(const tc_pattern *p, tc_weights w, const void *s, int R,
+                    const void *const *factors, int mode, void *out, int accumulate,
+                    tc_stream_t stream);
+
+/* Solve Factor (Sec. 3.4 with the normal equations of Sec. 2.2): for every row
+ * i of mode `mode`,
+ *   G_i = sum_{e in row i} s_e h_e h_e^T,   h_e = hadamard_{n != mode} A^(n)[i_n(e)],
+ *   (G_i + lambda I) a_i = rhs_i,
+ * solved by an unpivoted FP64 Cholesky of each R x R system (G_i is summed in
+ * the pattern's dtype).  rhs, out: device I_mode x R; out may alias rhs or
+ * factors[mode].  A row with a pivot <= 0 is left unwritten, gets
+ * row_status[i] = 1 (device int8[I_mode], may be NULL; other rows get 0) and
+ * records TC_ERR_NOT_SPD.  An empty row solves lambda a_i = rhs_i. */
+tc_status tc_solve_factor(const tc_pattern *p, tc_weights w, const void *s, int R,
+                          const void *const *factors, int mode, const void *rhs,
+                          double lambda, void *out, int8_t *row_status, tc_stream_t stream);
+
+/* Objective and gradient (eq. obj; Table 1; Appendix A):
+ *   f = sum_e phi(t_e, m_e) + lambda sum_n ||A^(n)||_F^2,  m_e = sum_r prod_n A^(n)[i_n(e), r]
+ *   grad^(n) = MTTKRP(phi', n) + 2 lambda A^(n),
+ * with t the pattern's values (tc_build_pattern needs vals).
+ * loss_out: device double, written (not accumulated); may be NULL.
+ * grads: host array of `order` device I_n x R outputs; the array or any entry
+ * may be NULL to skip that gradient. */
+tc_status tc_loss_grad(const tc_pattern *p, tc_loss loss, int R, const void *const *factors,
+                       double lambda, double *loss_out, void *const *grads, tc_stream_t stream);
+
+/* Gauss-Newton matrix-vector product (Sec. 2.5 with the phi' terms dropped;
+ * Appendix A):  z_e = sum_p <x^(p)[i_p(e)], h^(p)_e>,
+ *   y^(d)[k, r] = sum_{e : i_d(e) = k} phi''_e z_e h^(d)_{e r} + 2 lambda x^(d)[k, r].
+ * x, y: host arrays of `order` device I_n x R blocks; y must not alias x. */
+tc_status tc_ggn_matvec(const tc_pattern *p, tc_loss loss, int R, const void *const *factors,
+                        const void *const *x, double lambda, void *const *y, tc_stream_t stream);
+
+/* ------------------------------------------------------------------ GGN / PCG */
+
+/* A preconditioned-CG solver for the Gauss-Newton system H dx = b at fixed
+ * factors (Sec. 2.5).  The preconditioner is the block diagonal of H: per mode
+ * d and row k, P_k = sum_{e in row k} phi''_e h_e h_e^T + 2 lambda I, factored
+ * once by FP64 Cholesky (the Solve Factor systems with weights phi''), applied
+ * by two triangular solves.  The iteration runs from x0 = 0 for a fixed count,
+ * with FP64 inner products and step lengths kept on the device; it is captured
+ * once into a CUDA graph and replayed.
+ *
+ * tc_cg_create keeps `p`, the factor pointers, and allocates its work vectors;
+ * the factor contents may change between solves (call tc_cg_setup again). */
+typedef struct tc_cg tc_cg;
+
+tc_status tc_cg_create(const tc_pattern *p, tc_loss loss, int R, const void *const *factors,
+                       double lambda, int precondition, tc_cg **out);
+tc_status tc_cg_destroy(tc_cg *cg);
+
+/* Builds (or rebuilds) the preconditioner at the current factor values. */
+tc_status tc_cg_setup(tc_cg *cg, tc_stream_t stream);
+
+/* Applies the preconditioner: z^(d) = P^-1 r^(d) for all modes (after setup). */
+tc_status tc_cg_precond_apply(tc_cg *cg, const void *const *r, void *const *z,
+                              tc_stream_t stream);
+
+/* Runs `iters` PCG iterations on H dx = b from dx = 0.  b, dx: host arrays of
+ * `order` device I_n x R blocks (dx overwritten).  rz_out (device double[iters+1],
+ * may be NULL) receives r^T z before each iteration.  The first call with a
+ * given (b, dx, iters) captures a CUDA graph; later calls replay it. */
+tc_status tc_cg_solve(tc_cg *cg, const void *const *b, void *const *dx, int iters,
+                      double *rz_out, tc_stream_t stream);
+
+/* One Gauss-Newton step at the current factors: gradient, preconditioner,
+ * `iters` PCG iterations on H dx = -grad, then A^(n) += dx^(n) in place.
+ * loss_out (device double, may be NULL) receives f before the step. */
+tc_status tc_ggn_step(tc_cg *cg, int iters, double *loss_out, tc_stream_t stream);
+
+/* ------------------------------------------------------------------ misc */
+
+/* Number of kernel launches this library has issued in the calling process
+ * (graph replays count the kernels they contain).  For launch accounting. */
+int64_t tc_launch_count(void);
+
+/* Human-readable name of a status code. */
+const char *tc_status_string(tc_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,407 @@
+// Preconditioned conjugate gradients on the Gauss-Newton system (Sec. 2.5):
+// implicit matrix-vector products, the block-diagonal preconditioner applied
+// through the per-row Cholesky factors, FP64 inner products and step lengths
+// kept on the device, and the fixed-count loop captured once in a CUDA graph.
+#include "internal.cuh"
+
+#include <new>
+
+namespace tc {
+
+// device scalars of one solve
+enum { S_RZ = 0, S_PAP = 1, S_RZNEW = 2, S_STOP = 3, S_COUNT = 8 };
+
+// mode == 0: z = P^-1 r and scal[acc] += r.z  (start of the iteration)
+// mode == 1: alpha = rz / pAp; x += alpha p; r -= alpha Ap; z = P^-1 r; scal[acc] += r.z
+// One warp per row (grid-stride); chol == null means P = I.
+template <typename T>
+__global__ void __launch_bounds__(256) cg_update_kernel(int mode, int64_t I, int R,
+                                                        const double *__restrict__ chol, T *x, T *r,
+                                                        const T *__restrict__ p,
+                                                        const T *__restrict__ Ap, T *z,
+                                                        double *scal, int acc, int *status) {
+    __shared__ double sb[8][TC_MAX_RANK];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    double alpha = 0.0;
+    if (mode == 1) {
+        const double rz = scal[S_RZ], pap = scal[S_PAP];
+        const bool stopped = scal[S_STOP] != 0.0;
+        if (!stopped && rz != 0.0) {
+            if (pap > 0.0 && isfinite(pap)) alpha = rz / pap;
+            else if (blockIdx.x == 0 && threadIdx.x == 0) {
+                record_error(status, TC_ERR_BREAKDOWN);
+                scal[S_STOP] = 1.0;
+            }
+        }
+    }
+    double dot = 0.0;
+    double *bv = sb[wib];
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib; i < I; i += nwarps) {
+        const int64_t off = i * (int64_t)R;
+        for (int q = lane; q < R; q += 32) {
+            T rv = r[off + q];
+            if (mode == 1) {
+                x[off + q] = (T)((double)x[off + q] + alpha * (double)p[off + q]);
+                rv = (T)((double)rv - alpha * (double)Ap[off + q]);
+                r[off + q] = rv;
+            }
+            bv[q] = (double)rv;
+        }
+        __syncwarp();
+        if (chol) {
+            const double *Lo = chol + i * (int64_t)R * R;
+            for (int j = 0; j < R; ++j) {
+                const double yj = bv[j] / Lo[j * R + j];
+                __syncwarp();
+                for (int q = j + 1 + lane; q < R; q += 32) bv[q] -= Lo[q * R + j] * yj;
+                if (lane == 0) bv[j] = yj;
+                __syncwarp();
+            }
+            for (int j = R - 1; j >= 0; --j) {
+                const double xj = bv[j] / Lo[j * R + j];
+                __syncwarp();
+                for (int q = lane; q < j; q += 32) bv[q] -= Lo[j * R + q] * xj;
+                if (lane == 0) bv[j] = xj;
+                __syncwarp();
+            }
+        }
+        for (int q = lane; q < R; q += 32) {
+            const T zv = (T)bv[q];
+            z[off + q] = zv;
+            dot += (double)r[off + q] * (double)zv;
+        }
+        __syncwarp();
+    }
+    block_add(dot, scal + acc);
+}
+
+// p = z + beta p with beta = rz_new / rz
+template <typename T>
+__global__ void cg_dir_kernel(int64_t n, const T *__restrict__ z, T *p, const double *scal) {
+    const double rz = scal[S_RZ];
+    const double beta = rz != 0.0 ? scal[S_RZNEW] / rz : 0.0;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+         q += (int64_t)gridDim.x * blockDim.x)
+        p[q] = (T)((double)z[q] + beta * (double)p[q]);
+}
+
+__global__ void cg_scalar_kernel(double *scal, double *rz_hist, int slot) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        if (rz_hist) rz_hist[slot] = scal[S_RZNEW];
+        scal[S_RZ] = scal[S_RZNEW];
+        scal[S_PAP] = 0.0;
+        scal[S_RZNEW] = 0.0;
+    }
+}
+
+__global__ void cg_start_kernel(double *scal, double *rz_hist) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        if (rz_hist) rz_hist[0] = scal[S_RZNEW];
+        scal[S_RZ] = scal[S_RZNEW];
+        scal[S_PAP] = 0.0;
+        scal[S_RZNEW] = 0.0;
+        scal[S_STOP] = 0.0;
+    }
+}
+
+// y = a x + b y (elementwise)
+template <typename T>
+__global__ void axpby_kernel(int64_t n, T a, const T *__restrict__ x, T b, T *y) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+         q += (int64_t)gridDim.x * blockDim.x)
+        y[q] = a * x[q] + b * y[q];
+}
+
+}  // namespace tc
+
+using namespace tc;
+
+struct tc_cg {
+    const tc_pattern *p = nullptr;
+    tc_loss loss = TC_LOSS_LS;
+    int R = 0;
+    void *A[TC_ORDER] = {nullptr, nullptr, nullptr};
+    double lambda = 0.0;
+    int precond = 1;
+    double *chol[TC_ORDER] = {nullptr, nullptr, nullptr};
+    void *r[TC_ORDER] = {}, *z[TC_ORDER] = {}, *pv[TC_ORDER] = {}, *Ap[TC_ORDER] = {};
+    void *grad[TC_ORDER] = {}, *dx[TC_ORDER] = {};
+    double *scal = nullptr;
+    cudaStream_t own = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    // cached graph
+    cudaGraphExec_t exec = nullptr;
+    const void *key_b[TC_ORDER] = {}, *key_dx[TC_ORDER] = {};
+    int key_iters = -1;
+    double *key_rz = nullptr;
+    int64_t graph_launches = 0;
+};
+
+namespace tc {
+
+static int sms() {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+}
+
+template <typename T>
+static void enqueue_update(tc_cg *cg, int mode, int acc, cudaStream_t st) {
+    const tc_pattern *p = cg->p;
+    for (int d = 0; d < TC_ORDER; ++d) {
+        const int64_t I = p->dims[d];
+        int64_t blocks = (I + 7) / 8;
+        if (blocks > 4LL * sms()) blocks = 4LL * sms();
+        if (blocks < 1) blocks = 1;
+        cg_update_kernel<T><<<(unsigned)blocks, 256, 0, st>>>(
+            mode, I, cg->R, cg->precond ? cg->chol[d] : nullptr, (T *)cg->dx[d], (T *)cg->r[d],
+            (const T *)cg->pv[d], (const T *)cg->Ap[d], (T *)cg->z[d], cg->scal, acc, p->status);
+        count_launch();
+    }
+}
+
+template <typename T>
+static void enqueue_dir(tc_cg *cg, cudaStream_t st) {
+    for (int d = 0; d < TC_ORDER; ++d) {
+        const int64_t n = cg->p->dims[d] * cg->R;
+        int64_t blocks = (n + 255) / 256;
+        if (blocks > 8LL * sms()) blocks = 8LL * sms();
+        cg_dir_kernel<T><<<(unsigned)blocks, 256, 0, st>>>(n, (const T *)cg->z[d], (T *)cg->pv[d],
+                                                          cg->scal);
+        count_launch();
+    }
+}
+
+// Enqueues a full solve of `iters` iterations on st (graph-capturable: no
+// host synchronization, no allocation).  cg->dx receives the solution; the
+// right-hand side is in b.
+template <typename T>
+static tc_status enqueue_solve(tc_cg *cg, const void *const *b, void *const *dx, int iters,
+                               double *rz_out, cudaStream_t st) {
+    const tc_pattern *p = cg->p;
+    const size_t es = sizeof(T);
+    void *save_dx[TC_ORDER];
+    for (int d = 0; d < TC_ORDER; ++d) {
+        save_dx[d] = cg->dx[d];
+        cg->dx[d] = dx[d];
+        const size_t bytes = (size_t)p->dims[d] * cg->R * es;
+        TC_CUDA(cudaMemsetAsync(dx[d], 0, bytes, st));
+        TC_CUDA(cudaMemcpyAsync(cg->r[d], b[d], bytes, cudaMemcpyDeviceToDevice, st));
+    }
+    TC_CUDA(cudaMemsetAsync(cg->scal, 0, sizeof(double) * S_COUNT, st));
+    enqueue_update<T>(cg, 0, S_RZNEW, st);                 // z0 = P^-1 r0, rz
+    for (int d = 0; d < TC_ORDER; ++d)
+        TC_CUDA(cudaMemcpyAsync(cg->pv[d], cg->z[d], (size_t)p->dims[d] * cg->R * es,
+                                cudaMemcpyDeviceToDevice, st));
+    cg_start_kernel<<<1, 32, 0, st>>>(cg->scal, rz_out);
+    count_launch();
+    for (int it = 0; it < iters; ++it) {
+        tc_status rc = launch_ggn_matvec(p, cg->loss, cg->R, (const void *const *)cg->A,
+                                         (const void *const *)cg->pv, cg->lambda, cg->Ap,
+                                         cg->scal + S_PAP, st);
+        if (rc != TC_OK) return rc;
+        enqueue_update<T>(cg, 1, S_RZNEW, st);
+        enqueue_dir<T>(cg, st);
+        cg_scalar_kernel<<<1, 32, 0, st>>>(cg->scal, rz_out, it + 1);
+        count_launch();
+    }
+    for (int d = 0; d < TC_ORDER; ++d) cg->dx[d] = save_dx[d];
+    return TC_OK;
+}
+
+static void free_cg(tc_cg *cg) {
+    if (!cg) return;
+    for (int d = 0; d < TC_ORDER; ++d) {
+        cudaFree(cg->chol[d]);
+        cudaFree(cg->r[d]);
+        cudaFree(cg->z[d]);
+        cudaFree(cg->pv[d]);
+        cudaFree(cg->Ap[d]);
+        cudaFree(cg->grad[d]);
+        cudaFree(cg->dx[d]);
+    }
+    cudaFree(cg->scal);
+    if (cg->exec) cudaGraphExecDestroy(cg->exec);
+    if (cg->own) cudaStreamDestroy(cg->own);
+    if (cg->ev_in) cudaEventDestroy(cg->ev_in);
+    if (cg->ev_out) cudaEventDestroy(cg->ev_out);
+    delete cg;
+}
+
+}  // namespace tc
+
+extern "C" {
+
+tc_status tc_cg_create(const tc_pattern *p, tc_loss loss, int R, const void *const *factors,
+                       double lambda, int precondition, tc_cg **out) {
+    if (!p || !factors || !out || R < 1 || R > TC_MAX_RANK) return TC_ERR_ARG;
+    if (loss < TC_LOSS_LS || loss > TC_LOSS_POISSON_ID) return TC_ERR_ARG;
+    if (!p->has_vals) return TC_ERR_ARG;
+    for (int d = 0; d < TC_ORDER; ++d)
+        if (!factors[d]) return TC_ERR_ARG;
+    tc_cg *cg = new (std::nothrow) tc_cg();
+    if (!cg) return TC_ERR_OOM;
+    cg->p = p;
+    cg->loss = loss;
+    cg->R = R;
+    cg->lambda = lambda;
+    cg->precond = precondition ? 1 : 0;
+    const size_t es = tsize(p->dtype);
+    bool ok = true;
+    for (int d = 0; d < TC_ORDER && ok; ++d) {
+        cg->A[d] = const_cast<void *>(factors[d]);
+        const size_t bytes = (size_t)p->dims[d] * R * es;
+        ok = ok && cudaMalloc(&cg->r[d], bytes) == cudaSuccess;
+        ok = ok && cudaMalloc(&cg->z[d], bytes) == cudaSuccess;
+        ok = ok && cudaMalloc(&cg->pv[d], bytes) == cudaSuccess;
+        ok = ok && cudaMalloc(&cg->Ap[d], bytes) == cudaSuccess;
+        ok = ok && cudaMalloc(&cg->grad[d], bytes) == cudaSuccess;
+        ok = ok && cudaMalloc(&cg->dx[d], bytes) == cudaSuccess;
+        if (cg->precond)
+            ok = ok && cudaMalloc((void **)&cg->chol[d], sizeof(double) * p->dims[d] * R * R) ==
+                           cudaSuccess;
+    }
+    ok = ok && cudaMalloc((void **)&cg->scal, sizeof(double) * S_COUNT) == cudaSuccess;
+    ok = ok && cudaStreamCreateWithFlags(&cg->own, cudaStreamNonBlocking) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&cg->ev_in, cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&cg->ev_out, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        free_cg(cg);
+        return TC_ERR_OOM;
+    }
+    *out = cg;
+    return TC_OK;
+}
+
+tc_status tc_cg_destroy(tc_cg *cg) {
+    if (!cg) return TC_ERR_ARG;
+    cudaDeviceSynchronize();
+    free_cg(cg);
+    return TC_OK;
+}
+
+tc_status tc_cg_setup(tc_cg *cg, tc_stream_t stream) {
+    if (!cg) return TC_ERR_ARG;
+    if (!cg->precond) return TC_OK;
+    for (int d = 0; d < TC_ORDER; ++d) {
+        tc_status rc = launch_solve_factor(cg->p, TC_W_ONE, nullptr, cg->R,
+                                           (const void *const *)cg->A, d, nullptr,
+                                           2.0 * cg->lambda, nullptr, nullptr, 1, cg->loss,
+                                           cg->chol[d], (cudaStream_t)stream);
+        if (rc != TC_OK) return rc;
+    }
+    return cudaGetLastError() == cudaSuccess ? TC_OK : TC_ERR_CUDA;
+}
+
+tc_status tc_cg_precond_apply(tc_cg *cg, const void *const *r, void *const *z,
+                              tc_stream_t stream) {
+    if (!cg || !r || !z) return TC_ERR_ARG;
+    const size_t es = tsize(cg->p->dtype);
+    for (int d = 0; d < TC_ORDER; ++d) {
+        if (!r[d] || !z[d]) return TC_ERR_ARG;
+        if (cg->precond) {
+            tc_status rc = launch_chol_apply(cg->p, cg->R, d, cg->chol[d], r[d], z[d],
+                                             (cudaStream_t)stream);
+            if (rc != TC_OK) return rc;
+        } else if (r[d] != z[d]) {
+            TC_CUDA(cudaMemcpyAsync(z[d], r[d], (size_t)cg->p->dims[d] * cg->R * es,
+                                    cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+        }
+    }
+    return cudaGetLastError() == cudaSuccess ? TC_OK : TC_ERR_CUDA;
+}
+
+tc_status tc_cg_solve(tc_cg *cg, const void *const *b, void *const *dx, int iters,
+                      double *rz_out, tc_stream_t stream) {
+    if (!cg || !b || !dx || iters < 0) return TC_ERR_ARG;
+    for (int d = 0; d < TC_ORDER; ++d)
+        if (!b[d] || !dx[d]) return TC_ERR_ARG;
+    cudaStream_t caller = (cudaStream_t)stream;
+    bool same = cg->exec && cg->key_iters == iters && cg->key_rz == rz_out;
+    for (int d = 0; d < TC_ORDER && same; ++d) same = cg->key_b[d] == b[d] && cg->key_dx[d] == dx[d];
+    if (!same) {
+        if (cg->exec) {
+            cudaGraphExecDestroy(cg->exec);
+            cg->exec = nullptr;
+        }
+        const int64_t before = g_launches;
+        TC_CUDA(cudaStreamBeginCapture(cg->own, cudaStreamCaptureModeThreadLocal));
+        tc_status rc = cg->p->dtype == TC_F64
+                           ? enqueue_solve<double>(cg, b, dx, iters, rz_out, cg->own)
+                           : enqueue_solve<float>(cg, b, dx, iters, rz_out, cg->own);
+        cudaGraph_t graph = nullptr;
+        cudaError_t ce = cudaStreamEndCapture(cg->own, &graph);
+        if (rc != TC_OK || ce != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc != TC_OK ? rc : TC_ERR_CUDA;
+        }
+        ce = cudaGraphInstantiate(&cg->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) {
+            cg->exec = nullptr;
+            return TC_ERR_CUDA;
+        }
+        cg->graph_launches = g_launches - before;
+        g_launches = before;
+        cg->key_iters = iters;
+        cg->key_rz = rz_out;
+        for (int d = 0; d < TC_ORDER; ++d) {
+            cg->key_b[d] = b[d];
+            cg->key_dx[d] = dx[d];
+        }
+    }
+    // order the replay after the caller's prior work and the caller's later work after it
+    TC_CUDA(cudaEventRecord(cg->ev_in, caller));
+    TC_CUDA(cudaStreamWaitEvent(cg->own, cg->ev_in, 0));
+    TC_CUDA(cudaGraphLaunch(cg->exec, cg->own));
+    TC_CUDA(cudaEventRecord(cg->ev_out, cg->own));
+    TC_CUDA(cudaStreamWaitEvent(caller, cg->ev_out, 0));
+    count_launch((int)cg->graph_launches);
+    return TC_OK;
+}
+
+tc_status tc_ggn_step(tc_cg *cg, int iters, double *loss_out, tc_stream_t stream) {
+    if (!cg || iters < 0) return TC_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const tc_pattern *p = cg->p;
+    tc_status rc = launch_loss_grad(p, cg->loss, cg->R, (const void *const *)cg->A, cg->lambda,
+                                    loss_out, cg->grad, st);
+    if (rc != TC_OK) return rc;
+    // b = -grad (in place)
+    for (int d = 0; d < TC_ORDER; ++d) {
+        const int64_t n = p->dims[d] * cg->R;
+        int64_t blocks = (n + 255) / 256;
+        if (blocks > 8LL * sms()) blocks = 8LL * sms();
+        if (p->dtype == TC_F64)
+            axpby_kernel<double><<<(unsigned)blocks, 256, 0, st>>>(n, 0.0, (const double *)cg->grad[d],
+                                                                  -1.0, (double *)cg->grad[d]);
+        else
+            axpby_kernel<float><<<(unsigned)blocks, 256, 0, st>>>(n, 0.0f, (const float *)cg->grad[d],
+                                                                 -1.0f, (float *)cg->grad[d]);
+        count_launch();
+    }
+    rc = tc_cg_setup(cg, stream);
+    if (rc != TC_OK) return rc;
+    // the solution goes to the solver's own buffer dx, then A += dx
+    void *dxb[TC_ORDER];
+    for (int d = 0; d < TC_ORDER; ++d) dxb[d] = cg->dx[d];
+    rc = tc_cg_solve(cg, (const void *const *)cg->grad, dxb, iters, nullptr, stream);
+    if (rc != TC_OK) return rc;
+    for (int d = 0; d < TC_ORDER; ++d) {
+        const int64_t n = p->dims[d] * cg->R;
+        int64_t blocks = (n + 255) / 256;
+        if (blocks > 8LL * sms()) blocks = 8LL * sms();
+        if (p->dtype == TC_F64)
+            axpby_kernel<double><<<(unsigned)blocks, 256, 0, st>>>(n, 1.0, (const double *)cg->dx[d],
+                                                                  1.0, (double *)cg->A[d]);
+        else
+            axpby_kernel<float><<<(unsigned)blocks, 256, 0, st>>>(n, 1.0f, (const float *)cg->dx[d],
+                                                                 1.0f, (float *)cg->A[d]);
+        count_launch();
+    }
+    return cudaGetLastError() == cudaSuccess ? TC_OK : TC_ERR_CUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,250 @@
+// Internal declarations and device helpers of libtc (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <initializer_list>
+
+#include "../../include/tc.h"
+
+#define TC_ORDER 3
+#define TC_MAX_RANK 64
+
+// ------------------------------------------------------------------ host side
+struct ModeData {
+    int64_t *row_ptr = nullptr;   // I_d + 1
+    int64_t *perm = nullptr;      // nnz: sorted position -> input position
+    int64_t *to0 = nullptr;       // nnz: mode-d position -> mode-0 position (d > 0)
+    int32_t *nz_rows = nullptr;   // n_ne nonempty rows, ascending
+    int64_t *nz_ptr = nullptr;    // n_ne + 1 offsets of the nonempty rows
+    int64_t n_ne = 0;
+    int32_t *cols[TC_ORDER - 1] = {nullptr, nullptr};  // other modes, ascending mode order
+    void *vals = nullptr;         // nnz values in this mode's order (or null)
+};
+
+struct tc_pattern {
+    int order = 0;
+    int64_t dims[TC_ORDER] = {0, 0, 0};
+    int64_t nnz = 0;
+    tc_dtype dtype = TC_F32;
+    int has_vals = 0;
+    int device = 0;
+    ModeData md[TC_ORDER];
+    int *status = nullptr;        // device word: first error recorded, 0 if none
+    double *dscratch = nullptr;   // device doubles for reductions (kScratchDoubles)
+};
+
+constexpr int kScratchDoubles = 64;
+
+namespace tc {
+
+extern int64_t g_launches;
+inline void count_launch(int n = 1) { g_launches += n; }
+
+inline size_t tsize(tc_dtype t) { return t == TC_F64 ? 8 : 4; }
+
+// Other modes of `mode`, ascending.
+inline void other_modes(int mode, int &o1, int &o2) {
+    o1 = mode == 0 ? 1 : 0;
+    o2 = mode == 2 ? 1 : 2;
+}
+
+// Padded rank tier: the compile-time row width a kernel is instantiated for.
+inline int rank_tier(int R) {
+    if (R <= 8) return 8;
+    if (R <= 16) return 16;
+    if (R <= 32) return 32;
+    return 64;
+}
+
+// Rows may use 16-byte vector loads when the row stride is a multiple of 16
+// bytes and the rank fills the tier.
+inline bool vec_ok(int R, int tier, size_t es) { return R == tier && (R * es) % 16 == 0; }
+
+// Every non-null pointer 16-byte aligned (a caller may pass an offset view).
+inline bool aligned16(std::initializer_list<const void *> ptrs) {
+    for (const void *q : ptrs)
+        if (q && (reinterpret_cast<uintptr_t>(q) & 15u)) return false;
+    return true;
+}
+
+#define TC_CUDA(call)                                      \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return TC_ERR_CUDA;         \
+    } while (0)
+
+// Device-side weights description.
+template <typename T>
+struct Weights {
+    int kind;            // TC_W_ONE / TC_W_VALUES / TC_W_ARRAY
+    const T *s;          // values or array in this traversal's order (mode 0 / VALUES)
+    const int64_t *to0;  // for TC_W_ARRAY in a mode d > 0: index into s (pattern order)
+};
+
+// ---------------------------------------------------------------- kernel launchers
+// (defined in the .cu files; each returns TC_OK or an error)
+tc_status launch_tttp(const tc_pattern *p, tc_weights w, const void *s, int R,
+                      const void *const *A, void *x, cudaStream_t st);
+tc_status launch_mttkrp(const tc_pattern *p, tc_weights w, const void *s, int R,
+                        const void *const *A, int mode, void *out, int accumulate,
+                        cudaStream_t st);
+tc_status launch_loss_grad(const tc_pattern *p, tc_loss loss, int R, const void *const *A,
+                           double lambda, double *loss_out, void *const *grads, cudaStream_t st);
+tc_status launch_ggn_matvec(const tc_pattern *p, tc_loss loss, int R, const void *const *A,
+                            const void *const *x, double lambda, void *const *y,
+                            double *dot_out, cudaStream_t st);
+// Gram + Cholesky per row.  If chol_out != null the (lower) Cholesky factors are
+// stored (FP64, I_d x R x R) instead of solving.
+tc_status launch_solve_factor(const tc_pattern *p, tc_weights w, const void *s, int R,
+                              const void *const *A, int mode, const void *rhs, double lambda,
+                              void *out, int8_t *row_status, int use_loss_d2, tc_loss loss,
+                              double *chol_out, cudaStream_t st);
+tc_status launch_chol_apply(const tc_pattern *p, int R, int mode, const double *chol,
+                            const void *r, void *z, cudaStream_t st);
+tc_status build_pattern_impl(int order, const int64_t *dims, int64_t nnz,
+                             const int32_t *const *idx, const void *vals, tc_dtype dtype,
+                             unsigned flags, cudaStream_t st, tc_pattern **out);
+void free_pattern(tc_pattern *p);
+
+}  // namespace tc
+
+// ------------------------------------------------------------------ device side
+#ifdef __CUDACC__
+namespace tc {
+
+// Lane layout of one row of a factor: V consecutive elements per lane (one
+// 16-byte vector), G lanes per nonzero, NG nonzeros per warp step.
+template <typename T, int RT>
+struct Lay {
+    static constexpr int V = 16 / (int)sizeof(T);
+    static constexpr int G = RT / V;
+    static constexpr int NG = 32 / G;
+};
+
+__device__ __forceinline__ void record_error(int *status, int code) {
+    atomicCAS(status, 0, code);
+}
+
+template <typename T, int V, bool VEC>
+__device__ __forceinline__ void load_slice(T (&v)[V], const T *__restrict__ A, int64_t row, int R,
+                                           int lg) {
+    const T *ptr = A + row * (int64_t)R + lg * V;
+    if constexpr (VEC) {
+        if constexpr (sizeof(T) == 4) {
+            float4 q = __ldg(reinterpret_cast<const float4 *>(ptr));
+            v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+        } else {
+            double2 q = __ldg(reinterpret_cast<const double2 *>(ptr));
+            v[0] = q.x; v[1] = q.y;
+        }
+    } else {
+#pragma unroll
+        for (int t = 0; t < V; ++t) v[t] = (lg * V + t < R) ? __ldg(ptr + t) : T(0);
+    }
+}
+
+template <typename T, int V, bool VEC>
+__device__ __forceinline__ void store_slice(T *__restrict__ A, int64_t row, int R, int lg,
+                                            const T (&v)[V]) {
+    T *ptr = A + row * (int64_t)R + lg * V;
+    if constexpr (VEC) {
+        if constexpr (sizeof(T) == 4) {
+            *reinterpret_cast<float4 *>(ptr) = make_float4(v[0], v[1], v[2], v[3]);
+        } else {
+            *reinterpret_cast<double2 *>(ptr) = make_double2(v[0], v[1]);
+        }
+    } else {
+#pragma unroll
+        for (int t = 0; t < V; ++t)
+            if (lg * V + t < R) ptr[t] = v[t];
+    }
+}
+
+template <typename T, int V>
+__device__ __forceinline__ void atomic_add_slice(T *__restrict__ A, int64_t row, int R, int lg,
+                                                 const T (&v)[V]) {
+    T *ptr = A + row * (int64_t)R + lg * V;
+#pragma unroll
+    for (int t = 0; t < V; ++t)
+        if (lg * V + t < R) atomicAdd(ptr + t, v[t]);
+}
+
+// Sum over the G lanes of one nonzero group (G is a power of two, groups are
+// aligned on G lanes).
+template <int G, typename T>
+__device__ __forceinline__ T group_sum(T v) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Adds v summed over the block to *dst with one atomic; every thread of the
+// block must call it (blockDim.x a multiple of 32, at most 1024).
+__device__ __forceinline__ void block_add(double v, double *dst) {
+    __shared__ double red[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    v = warp_sum(v);
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        v = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+        v = warp_sum(v);
+        if (lane == 0 && v != 0.0) atomicAdd(dst, v);
+    }
+    __syncthreads();
+}
+
+// Largest index q in [lo, hi] with a[q] <= key (a ascending, a[lo] <= key).
+__device__ __forceinline__ int64_t search_le(const int64_t *__restrict__ a, int64_t lo, int64_t hi,
+                                             int64_t key) {
+    while (lo < hi) {
+        int64_t mid = (lo + hi + 1) >> 1;
+        if (__ldg(a + mid) <= key) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Weight s_e of the nonzero at sorted position q of the current traversal.
+template <typename T>
+__device__ __forceinline__ T weight_at(const Weights<T> &w, int64_t q) {
+    if (w.kind == TC_W_ONE) return T(1);
+    if (w.to0) return __ldg(w.s + __ldg(w.to0 + q));
+    return __ldcs(w.s + q);
+}
+
+// phi, phi' and phi'' of eq. obj / Table 1 at model entry m and value t.
+template <typename T>
+__device__ __forceinline__ void loss_terms(int loss, T t, T m, T &phi, T &d1, T &d2, bool &dom_ok) {
+    if (loss == TC_LOSS_LS) {
+        T r = t - m;
+        phi = r * r;
+        d1 = T(2) * (m - t);
+        d2 = T(2);
+    } else if (loss == TC_LOSS_POISSON_LOG) {
+        T ex = exp(m);
+        phi = ex - t * m;
+        d1 = ex - t;
+        d2 = ex;
+    } else {
+        if (!(m > T(0))) {
+            dom_ok = false;
+            phi = d1 = d2 = T(0);
+            return;
+        }
+        phi = m - t * log(m);
+        d1 = T(1) - t / m;
+        d2 = t / (m * m);
+    }
+}
+
+}  // namespace tc
+#endif

@@ -1,0 +1,544 @@
+// Segmented sweeps over one mode's sorted nonzeros: TTTP (Sec. 3.3), MTTKRP
+// (Sec. 3.2), the gradient of eq. obj (Table 1, Appendix A) and the
+// Gauss-Newton matrix-vector product (Sec. 2.5).
+//
+// Work decomposition.  Each warp owns a contiguous chunk of the sorted
+// nonzeros.  A nonzero is handled by G lanes, each holding V consecutive
+// entries (one 16-byte vector) of every factor row it touches, so a warp step
+// covers NG = 32/G consecutive nonzeros.  Row membership is decoded from the
+// compressed row offsets (nonempty rows only), so no per-nonzero row index is
+// stored or read.  Row sums are formed by a segmented scan across the NG
+// groups of a step plus a carry between steps; a finished row is written once
+// with plain stores, and only the first and last row of a chunk, which other
+// chunks may share, are added atomically.
+#include "internal.cuh"
+
+namespace tc {
+
+enum { OP_MTTKRP = 0, OP_GRAD = 1, OP_GGN = 2 };
+
+template <typename T>
+struct SweepParams {
+    const int32_t *nz_rows;
+    const int64_t *nz_ptr;
+    int64_t n_ne, nnz, chunk;
+    const int32_t *c1, *c2;       // indices of the two other modes, this mode's order
+    Weights<T> w;                 // OP_MTTKRP weights
+    const T *t;                   // observed values, this mode's order (GRAD / GGN)
+    const T *Ad, *A1, *A2;        // factor of this mode and of the two others
+    const T *Xd, *X1, *X2;        // GGN direction blocks
+    int R, loss, accumulate;
+    T *out;                       // I_d x R (may be null for a loss-only pass)
+    double *loss_acc;             // GRAD: += sum phi
+    double *dot_acc;              // += sum_rows dot_with[row] . (flushed partial row)
+    const T *dot_with;
+    int *status;
+};
+
+template <typename T, int RT, bool VEC, int OP>
+__global__ void __launch_bounds__(256) sweep_kernel(const SweepParams<T> P) {
+    using L = Lay<T, RT>;
+    constexpr int V = L::V, G = L::G, NG = L::NG;
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, g = lane / G, lg = lane % G;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t c0 = warp * P.chunk;
+    const bool active = c0 < P.nnz;     // idle warps still join the block reductions
+    const int64_t cend = active ? min(c0 + P.chunk, P.nnz) : c0;
+    const int64_t *__restrict__ nzp = P.nz_ptr;
+    const int R = P.R;
+
+    int64_t cur = active ? search_le(nzp, 0, P.n_ne - 1, c0) : 0;
+    const int64_t first_cr = cur;
+    const bool first_shared = active && __ldg(nzp + cur) < c0;
+    const int64_t last_cr = active ? search_le(nzp, cur, P.n_ne - 1, cend - 1) : 0;
+    const bool last_shared = active && __ldg(nzp + last_cr + 1) > cend;
+
+    T carry[V];
+#pragma unroll
+    for (int t = 0; t < V; ++t) carry[t] = T(0);
+    int64_t carry_cr = -1;
+    double lacc = 0.0, dacc = 0.0;
+    bool dom_ok = true;
+
+    auto flush = [&](int64_t cr, const T(&v)[V]) {
+        if (!P.out) return;
+        const int64_t row = __ldg(P.nz_rows + cr);
+        if ((cr == first_cr && first_shared) || (cr == last_cr && last_shared)) {
+            atomic_add_slice<T, V>(P.out, row, R, lg, v);
+        } else if (P.accumulate) {
+            T o[V];
+            T *ptr = P.out + row * (int64_t)R + lg * V;
+#pragma unroll
+            for (int t = 0; t < V; ++t) o[t] = (lg * V + t < R) ? ptr[t] + v[t] : T(0);
+            store_slice<T, V, VEC>(P.out, row, R, lg, o);
+        } else {
+            store_slice<T, V, VEC>(P.out, row, R, lg, v);
+        }
+        if (P.dot_acc) {
+            T dw[V];
+            load_slice<T, V, VEC>(dw, P.dot_with, row, R, lg);
+#pragma unroll
+            for (int t = 0; t < V; ++t) dacc += (double)dw[t] * (double)v[t];
+        }
+    };
+
+    for (int64_t base = c0; base < cend; base += NG) {
+        const int64_t q = base + g;
+        const bool valid = q < cend;
+        const int64_t lastpos = min(base + NG, cend) - 1;
+        int64_t cr;
+        if (__ldg(nzp + cur + 1) > lastpos) cr = cur;   // the whole step lies in one row
+        else cr = search_le(nzp, cur, min(cur + NG - 1, P.n_ne - 1), valid ? q : lastpos);
+
+        // Tail lanes of the last step read the last valid position and their
+        // contribution is dropped, so every lane takes part in the shuffles.
+        const int64_t qq = valid ? q : lastpos;
+        T c[V];
+        {
+            const int32_t j = __ldcs(P.c1 + qq), k = __ldcs(P.c2 + qq);
+            T b[V], e[V];
+            load_slice<T, V, VEC>(b, P.A1, j, R, lg);
+            load_slice<T, V, VEC>(e, P.A2, k, R, lg);
+            if constexpr (OP == OP_MTTKRP) {
+                const T s = weight_at(P.w, qq);
+#pragma unroll
+                for (int t = 0; t < V; ++t) c[t] = s * b[t] * e[t];
+            } else {
+                const int32_t row = __ldg(P.nz_rows + cr);
+                T a[V];
+                load_slice<T, V, VEC>(a, P.Ad, row, R, lg);
+                const T tv = __ldcs(P.t + qq);
+                T part = T(0);
+#pragma unroll
+                for (int t = 0; t < V; ++t) part += a[t] * b[t] * e[t];
+                if constexpr (OP == OP_GRAD) {
+                    const T m = group_sum<G>(part);
+                    T phi, d1, d2;
+                    loss_terms(P.loss, tv, m, phi, d1, d2, dom_ok);
+#pragma unroll
+                    for (int t = 0; t < V; ++t) c[t] = d1 * b[t] * e[t];
+                    if (lg == 0 && valid) lacc += (double)phi;
+                } else {
+                    T xa[V], xb[V], xc[V];
+                    load_slice<T, V, VEC>(xa, P.Xd, row, R, lg);
+                    load_slice<T, V, VEC>(xb, P.X1, j, R, lg);
+                    load_slice<T, V, VEC>(xc, P.X2, k, R, lg);
+                    T zp = T(0);
+#pragma unroll
+                    for (int t = 0; t < V; ++t)
+                        zp += xa[t] * b[t] * e[t] + a[t] * xb[t] * e[t] + a[t] * b[t] * xc[t];
+                    const T z = group_sum<G>(zp);
+                    T d2 = T(2);
+                    if (P.loss != TC_LOSS_LS) {
+                        const T m = group_sum<G>(part);
+                        T phi, d1;
+                        loss_terms(P.loss, tv, m, phi, d1, d2, dom_ok);
+                    }
+                    const T wz = d2 * z;
+#pragma unroll
+                    for (int t = 0; t < V; ++t) c[t] = wz * b[t] * e[t];
+                }
+            }
+        }
+        if (!valid) {
+#pragma unroll
+            for (int t = 0; t < V; ++t) c[t] = T(0);
+        }
+        if (!valid) cr = -1;
+
+        // a carried row that does not continue into this step is complete
+        const int64_t cr0 = __shfl_sync(FULL, cr, 0);
+        if (carry_cr >= 0 && carry_cr != cr0) {
+            if (g == 0) flush(carry_cr, carry);
+            carry_cr = -1;
+        }
+        // segmented inclusive scan over the NG groups of this step
+#pragma unroll
+        for (int d = 1; d < NG; d <<= 1) {
+            const int64_t ocr = __shfl_up_sync(FULL, cr, d * G);
+            T o[V];
+#pragma unroll
+            for (int t = 0; t < V; ++t) o[t] = __shfl_up_sync(FULL, c[t], d * G);
+            if (g >= d && ocr == cr) {
+#pragma unroll
+                for (int t = 0; t < V; ++t) c[t] += o[t];
+            }
+        }
+        if (carry_cr >= 0 && cr == carry_cr) {
+#pragma unroll
+            for (int t = 0; t < V; ++t) c[t] += carry[t];
+        }
+        const int64_t ncr = __shfl_down_sync(FULL, cr, G);
+        if (valid && g < NG - 1 && ncr != cr) flush(cr, c);
+        const int64_t lcr = __shfl_sync(FULL, cr, (NG - 1) * G);
+#pragma unroll
+        for (int t = 0; t < V; ++t) carry[t] = __shfl_sync(FULL, c[t], (NG - 1) * G + lg);
+        carry_cr = lcr;
+        if (base + NG < cend) cur = lcr + ((__ldg(nzp + lcr + 1) <= base + NG) ? 1 : 0);
+    }
+    if (carry_cr >= 0 && g == 0) flush(carry_cr, carry);
+
+    if constexpr (OP != OP_MTTKRP) {
+        if (!dom_ok) record_error(P.status, TC_ERR_DOMAIN);
+    }
+    if constexpr (OP == OP_GRAD) {
+        if (P.loss_acc) block_add(lacc, P.loss_acc);
+    }
+    if (P.dot_acc) block_add(dacc, P.dot_acc);
+}
+
+// ------------------------------------------------------------------ TTTP
+template <typename T>
+struct TttpParams {
+    const int32_t *nz_rows;
+    const int64_t *nz_ptr;
+    int64_t n_ne, nnz, chunk;
+    const int32_t *c1, *c2;
+    Weights<T> w;
+    const T *A0, *A1, *A2;        // any may be null (mode skipped)
+    int R;
+    T *x;
+};
+
+template <typename T, int RT, bool VEC>
+__global__ void __launch_bounds__(256) tttp_kernel(const TttpParams<T> P) {
+    using L = Lay<T, RT>;
+    constexpr int V = L::V, G = L::G, NG = L::NG;
+    const int lane = threadIdx.x & 31, g = lane / G, lg = lane % G;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t c0 = warp * P.chunk;
+    if (c0 >= P.nnz) return;
+    const int64_t cend = min(c0 + P.chunk, P.nnz);
+    const int64_t *__restrict__ nzp = P.nz_ptr;
+    const int R = P.R;
+    int64_t cur = P.A0 ? search_le(nzp, 0, P.n_ne - 1, c0) : 0;
+
+    for (int64_t base = c0; base < cend; base += NG) {
+        const int64_t q = base + g;
+        const bool valid = q < cend;
+        const int64_t lastpos = min(base + NG, cend) - 1;
+        T prod[V];
+#pragma unroll
+        for (int t = 0; t < V; ++t) prod[t] = T(1);
+        if (P.A0) {
+            int64_t cr;
+            if (__ldg(nzp + cur + 1) > lastpos) cr = cur;
+            else cr = search_le(nzp, cur, min(cur + NG - 1, P.n_ne - 1), valid ? q : lastpos);
+            if (valid) {
+                T a[V];
+                load_slice<T, V, VEC>(a, P.A0, __ldg(P.nz_rows + cr), R, lg);
+#pragma unroll
+                for (int t = 0; t < V; ++t) prod[t] *= a[t];
+            }
+            const int64_t lcr = __shfl_sync(0xffffffffu, cr, (NG - 1) * G);
+            if (base + NG < cend) cur = lcr + ((__ldg(nzp + lcr + 1) <= base + NG) ? 1 : 0);
+        }
+        T s = T(0);
+        if (valid) {
+            if (P.A1) {
+                T b[V];
+                load_slice<T, V, VEC>(b, P.A1, __ldcs(P.c1 + q), R, lg);
+#pragma unroll
+                for (int t = 0; t < V; ++t) prod[t] *= b[t];
+            }
+            if (P.A2) {
+                T e[V];
+                load_slice<T, V, VEC>(e, P.A2, __ldcs(P.c2 + q), R, lg);
+#pragma unroll
+                for (int t = 0; t < V; ++t) prod[t] *= e[t];
+            }
+            s = weight_at(P.w, q);
+        }
+        T part = T(0);
+#pragma unroll
+        for (int t = 0; t < V; ++t) part += (lg * V + t < R) ? prod[t] : T(0);
+        const T m = group_sum<G>(part);
+        if (valid && lg == 0) __stcs(P.x + q, s * m);
+    }
+}
+
+// ------------------------------------------------------------------ small kernels
+// y = alpha * x (n elements); optional dot += alpha * x.x (FP64).
+template <typename T>
+__global__ void scale_kernel(T *__restrict__ y, const T *__restrict__ x, T alpha, int64_t n,
+                             double *dot) {
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const T v = x[i];
+        y[i] = alpha * v;
+        acc += (double)alpha * (double)v * (double)v;
+    }
+    if (dot) {
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if ((threadIdx.x & 31) == 0) atomicAdd(dot, acc);
+    }
+}
+
+// acc += scale * sum x^2 (FP64)
+template <typename T>
+__global__ void sumsq_kernel(const T *__restrict__ x, int64_t n, double scale, double *acc) {
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = (double)x[i];
+        s += v * v;
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(acc, scale * s);
+}
+
+// ------------------------------------------------------------------ launchers
+static int g_sm_count = 0;
+static int sm_count() {
+    if (!g_sm_count) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev);
+        if (g_sm_count <= 0) g_sm_count = 1;
+    }
+    return g_sm_count;
+}
+
+static int64_t pick_chunk(int64_t nnz, int NG) {
+    // about 8 steps per warp at least, and enough warps to fill the GPU
+    const int64_t min_chunk = (int64_t)NG * 8;
+    const int64_t target_warps = (int64_t)sm_count() * 64;
+    int64_t c = (nnz + target_warps - 1) / target_warps;
+    c = ((c + NG - 1) / NG) * NG;
+    if (c < min_chunk) c = min_chunk;
+    if (c > (int64_t)NG * 64) c = (int64_t)NG * 64;
+    return c;
+}
+
+template <typename T>
+static Weights<T> make_weights(const tc_pattern *p, int mode, tc_weights w, const void *s) {
+    Weights<T> W{(int)w, nullptr, nullptr};
+    if (w == TC_W_VALUES) W.s = (const T *)p->md[mode].vals;
+    else if (w == TC_W_ARRAY) {
+        W.s = (const T *)s;
+        if (mode != 0) W.to0 = p->md[mode].to0;
+    }
+    return W;
+}
+
+template <typename T, int OP>
+static void launch_sweep_t(const SweepParams<T> &P, int tier, bool vec, cudaStream_t st) {
+    const int threads = 256;
+    auto go = [&](auto kern, int NG) {
+        SweepParams<T> Q = P;
+        Q.chunk = pick_chunk(P.nnz, NG);
+        const int64_t warps = (P.nnz + Q.chunk - 1) / Q.chunk;
+        const int64_t blocks = (warps * 32 + threads - 1) / threads;
+        kern<<<(unsigned)blocks, threads, 0, st>>>(Q);
+        count_launch();
+    };
+#define TC_SWEEP_CASE(RT)                                                              \
+    case RT:                                                                           \
+        if (vec) go(sweep_kernel<T, RT, true, OP>, Lay<T, RT>::NG);                    \
+        else go(sweep_kernel<T, RT, false, OP>, Lay<T, RT>::NG);                       \
+        break;
+    switch (tier) {
+        TC_SWEEP_CASE(8)
+        TC_SWEEP_CASE(16)
+        TC_SWEEP_CASE(32)
+        TC_SWEEP_CASE(64)
+    }
+#undef TC_SWEEP_CASE
+}
+
+template <typename T>
+static SweepParams<T> base_params(const tc_pattern *p, int mode, int R) {
+    const ModeData &md = p->md[mode];
+    SweepParams<T> P{};
+    P.nz_rows = md.nz_rows;
+    P.nz_ptr = md.nz_ptr;
+    P.n_ne = md.n_ne;
+    P.nnz = p->nnz;
+    P.c1 = md.cols[0];
+    P.c2 = md.cols[1];
+    P.t = (const T *)md.vals;
+    P.R = R;
+    P.status = p->status;
+    return P;
+}
+
+template <typename T>
+static void launch_scale(T *y, const T *x, T alpha, int64_t n, double *dot, cudaStream_t st) {
+    const int threads = 256;
+    int64_t blocks = (n + threads - 1) / threads;
+    if (blocks > (int64_t)sm_count() * 8) blocks = (int64_t)sm_count() * 8;
+    if (blocks < 1) blocks = 1;
+    scale_kernel<T><<<(unsigned)blocks, threads, 0, st>>>(y, x, alpha, n, dot);
+    count_launch();
+}
+
+template <typename T>
+static void launch_sumsq(const T *x, int64_t n, double scale, double *acc, cudaStream_t st) {
+    const int threads = 256;
+    int64_t blocks = (n + threads - 1) / threads;
+    if (blocks > (int64_t)sm_count() * 8) blocks = (int64_t)sm_count() * 8;
+    if (blocks < 1) blocks = 1;
+    sumsq_kernel<T><<<(unsigned)blocks, threads, 0, st>>>(x, n, scale, acc);
+    count_launch();
+}
+
+template <typename T>
+static tc_status tttp_t(const tc_pattern *p, tc_weights w, const void *s, int R,
+                        const void *const *A, void *x, cudaStream_t st) {
+    if (p->nnz == 0) return TC_OK;
+    const ModeData &md = p->md[0];
+    TttpParams<T> P{};
+    P.nz_rows = md.nz_rows;
+    P.nz_ptr = md.nz_ptr;
+    P.n_ne = md.n_ne;
+    P.nnz = p->nnz;
+    P.c1 = md.cols[0];
+    P.c2 = md.cols[1];
+    P.w = make_weights<T>(p, 0, w, s);
+    P.A0 = (const T *)A[0];
+    P.A1 = (const T *)A[1];
+    P.A2 = (const T *)A[2];
+    P.R = R;
+    P.x = (T *)x;
+    const int tier = rank_tier(R);
+    const bool vec = vec_ok(R, tier, sizeof(T)) && aligned16({A[0], A[1], A[2]});
+    const int threads = 256;
+    auto go = [&](auto kern, int NG) {
+        TttpParams<T> Q = P;
+        Q.chunk = pick_chunk(P.nnz, NG);
+        const int64_t warps = (P.nnz + Q.chunk - 1) / Q.chunk;
+        const int64_t blocks = (warps * 32 + threads - 1) / threads;
+        kern<<<(unsigned)blocks, threads, 0, st>>>(Q);
+        count_launch();
+    };
+#define TC_TTTP_CASE(RT)                                                     \
+    case RT:                                                                 \
+        if (vec) go(tttp_kernel<T, RT, true>, Lay<T, RT>::NG);               \
+        else go(tttp_kernel<T, RT, false>, Lay<T, RT>::NG);                  \
+        break;
+    switch (tier) {
+        TC_TTTP_CASE(8)
+        TC_TTTP_CASE(16)
+        TC_TTTP_CASE(32)
+        TC_TTTP_CASE(64)
+    }
+#undef TC_TTTP_CASE
+    return TC_OK;
+}
+
+tc_status launch_tttp(const tc_pattern *p, tc_weights w, const void *s, int R,
+                      const void *const *A, void *x, cudaStream_t st) {
+    return p->dtype == TC_F64 ? tttp_t<double>(p, w, s, R, A, x, st)
+                              : tttp_t<float>(p, w, s, R, A, x, st);
+}
+
+template <typename T>
+static tc_status mttkrp_t(const tc_pattern *p, tc_weights w, const void *s, int R,
+                          const void *const *A, int mode, void *out, int accumulate,
+                          cudaStream_t st) {
+    const size_t bytes = (size_t)p->dims[mode] * R * sizeof(T);
+    if (!accumulate) {
+        TC_CUDA(cudaMemsetAsync(out, 0, bytes, st));
+    }
+    if (p->nnz == 0) return TC_OK;
+    int o1, o2;
+    other_modes(mode, o1, o2);
+    SweepParams<T> P = base_params<T>(p, mode, R);
+    P.w = make_weights<T>(p, mode, w, s);
+    P.A1 = (const T *)A[o1];
+    P.A2 = (const T *)A[o2];
+    P.out = (T *)out;
+    P.accumulate = accumulate;
+    const int tier = rank_tier(R);
+    const bool vec = vec_ok(R, tier, sizeof(T)) && aligned16({A[o1], A[o2], out});
+    launch_sweep_t<T, OP_MTTKRP>(P, tier, vec, st);
+    return TC_OK;
+}
+
+tc_status launch_mttkrp(const tc_pattern *p, tc_weights w, const void *s, int R,
+                        const void *const *A, int mode, void *out, int accumulate,
+                        cudaStream_t st) {
+    return p->dtype == TC_F64 ? mttkrp_t<double>(p, w, s, R, A, mode, out, accumulate, st)
+                              : mttkrp_t<float>(p, w, s, R, A, mode, out, accumulate, st);
+}
+
+template <typename T>
+static tc_status loss_grad_t(const tc_pattern *p, tc_loss loss, int R, const void *const *A,
+                             double lambda, double *loss_out, void *const *grads,
+                             cudaStream_t st) {
+    const int tier = rank_tier(R);
+    bool vec = vec_ok(R, tier, sizeof(T)) && aligned16({A[0], A[1], A[2]});
+    if (grads) vec = vec && aligned16({grads[0], grads[1], grads[2]});
+    if (loss_out) {
+        TC_CUDA(cudaMemsetAsync(loss_out, 0, sizeof(double), st));
+        for (int n = 0; n < TC_ORDER; ++n)
+            launch_sumsq<T>((const T *)A[n], p->dims[n] * R, lambda, loss_out, st);
+    }
+    bool loss_done = (loss_out == nullptr) || p->nnz == 0;
+    for (int d = 0; d < TC_ORDER; ++d) {
+        T *g = grads ? (T *)grads[d] : nullptr;
+        if (!g && (loss_done || d < TC_ORDER - 1)) continue;
+        if (g) launch_scale<T>(g, (const T *)A[d], (T)(2.0 * lambda), p->dims[d] * R, nullptr, st);
+        if (p->nnz == 0) continue;
+        int o1, o2;
+        other_modes(d, o1, o2);
+        SweepParams<T> P = base_params<T>(p, d, R);
+        P.Ad = (const T *)A[d];
+        P.A1 = (const T *)A[o1];
+        P.A2 = (const T *)A[o2];
+        P.loss = loss;
+        P.out = g;
+        P.accumulate = 1;
+        P.loss_acc = loss_done ? nullptr : loss_out;
+        loss_done = true;
+        launch_sweep_t<T, OP_GRAD>(P, tier, vec, st);
+    }
+    return TC_OK;
+}
+
+tc_status launch_loss_grad(const tc_pattern *p, tc_loss loss, int R, const void *const *A,
+                           double lambda, double *loss_out, void *const *grads, cudaStream_t st) {
+    return p->dtype == TC_F64 ? loss_grad_t<double>(p, loss, R, A, lambda, loss_out, grads, st)
+                              : loss_grad_t<float>(p, loss, R, A, lambda, loss_out, grads, st);
+}
+
+template <typename T>
+static tc_status ggn_t(const tc_pattern *p, tc_loss loss, int R, const void *const *A,
+                       const void *const *x, double lambda, void *const *y, double *dot_out,
+                       cudaStream_t st) {
+    const int tier = rank_tier(R);
+    const bool vec = vec_ok(R, tier, sizeof(T)) && aligned16({A[0], A[1], A[2]}) &&
+                     aligned16({x[0], x[1], x[2]}) && aligned16({y[0], y[1], y[2]});
+    for (int d = 0; d < TC_ORDER; ++d) {
+        launch_scale<T>((T *)y[d], (const T *)x[d], (T)(2.0 * lambda), p->dims[d] * R, dot_out,
+                        st);
+        if (p->nnz == 0) continue;
+        int o1, o2;
+        other_modes(d, o1, o2);
+        SweepParams<T> P = base_params<T>(p, d, R);
+        P.Ad = (const T *)A[d];
+        P.A1 = (const T *)A[o1];
+        P.A2 = (const T *)A[o2];
+        P.Xd = (const T *)x[d];
+        P.X1 = (const T *)x[o1];
+        P.X2 = (const T *)x[o2];
+        P.loss = loss;
+        P.out = (T *)y[d];
+        P.accumulate = 1;
+        P.dot_acc = dot_out;
+        P.dot_with = (const T *)x[d];
+        launch_sweep_t<T, OP_GGN>(P, tier, vec, st);
+    }
+    return TC_OK;
+}
+
+tc_status launch_ggn_matvec(const tc_pattern *p, tc_loss loss, int R, const void *const *A,
+                            const void *const *x, double lambda, void *const *y,
+                            double *dot_out, cudaStream_t st) {
+    return p->dtype == TC_F64 ? ggn_t<double>(p, loss, R, A, x, lambda, y, dot_out, st)
+                              : ggn_t<float>(p, loss, R, A, x, lambda, y, dot_out, st);
+}
+
+}  // namespace tc

@@ -1,0 +1,33 @@
+"""Algorithms composed from the C-ABI calls (Sec. 2 and Sec. 4 of the paper).
+
+* ``als_sweep`` -- alternating least squares (Sec. 2.2): for each mode, the
+  right-hand sides are the MTTKRP of the observed tensor, then Solve Factor
+  with the pattern and lambda overwrites that factor (block Gauss-Seidel order).
+* ``GaussNewton`` -- the generalized Gauss-Newton method with implicit
+  preconditioned CG (Sec. 2.5), one ``tc_ggn_step`` per call.
+Every arithmetic step runs in libtc kernels; this module only orders calls.
+"""
+from __future__ import annotations
+
+from . import tc
+
+
+def als_sweep(p: "tc.Pattern", factors, lam: float, rhs=None, row_status=None, stream=None):
+    """One ALS sweep in place over modes 0, 1, 2.  rhs: optional work buffers."""
+    for d in range(len(factors)):
+        b = tc.mttkrp(p, factors, d, weights="values", out=None if rhs is None else rhs[d],
+                      stream=stream)
+        tc.solve_factor(p, factors, d, b, lam, weights=None, out=factors[d],
+                        row_status=None if row_status is None else row_status[d], stream=stream)
+    return factors
+
+
+class GaussNewton:
+    """Generalized Gauss-Newton steps for a loss in {"ls", "poisson_log",
+    "poisson_id"}; the factors are updated in place."""
+
+    def __init__(self, p: "tc.Pattern", factors, loss: str, lam: float, precondition=True):
+        self.cg = tc.CG(p, factors, loss, lam, precondition)
+
+    def step(self, cg_iters: int, loss_out=None, stream=None):
+        self.cg.ggn_step(cg_iters, loss_out=loss_out, stream=stream)

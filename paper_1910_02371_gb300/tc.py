@@ -1,0 +1,287 @@
+"""Thin Python binding of libtc (include/tc.h): argument marshalling only.
+
+Every function here converts torch CUDA tensors to device pointers, passes the
+current CUDA stream, calls the C entry point of the same name and raises
+``TcError`` on a non-OK status.  There is no fallback: if ``libtc.so`` is not
+built the import of this module fails.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtc.so")
+
+OK, ERR_ARG, ERR_RANGE, ERR_DUPLICATE, ERR_OOM, ERR_CUDA, ERR_NOT_SPD, ERR_DOMAIN, \
+    ERR_BREAKDOWN, ERR_UNSUPPORTED = range(10)
+F32, F64 = 0, 1
+LOSSES = {"ls": 0, "poisson_log": 1, "poisson_id": 2}
+W_ONE, W_VALUES, W_ARRAY = 0, 1, 2
+CHECK_DUPLICATES = 1
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is not built: run paper_1910_02371_gb300.build.build()")
+
+_lib = ctypes.CDLL(LIB_PATH)
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_I64 = ctypes.c_int64
+_D = ctypes.c_double
+
+_SIGS = {
+    "tc_build_pattern": [_I, _P, _I64, _P, _P, _I, ctypes.c_uint, _P, _P],
+    "tc_pattern_destroy": [_P],
+    "tc_pattern_view": [_P, _I, _P, _P, _P, _P],
+    "tc_pattern_info": [_P, _P, _P, _P, _P],
+    "tc_last_error": [_P, _P],
+    "tc_tttp": [_P, _I, _P, _I, _P, _P, _P],
+    "tc_mttkrp": [_P, _I, _P, _I, _P, _I, _P, _I, _P],
+    "tc_solve_factor": [_P, _I, _P, _I, _P, _I, _P, _D, _P, _P, _P],
+    "tc_loss_grad": [_P, _I, _I, _P, _D, _P, _P, _P],
+    "tc_ggn_matvec": [_P, _I, _I, _P, _P, _D, _P, _P],
+    "tc_cg_create": [_P, _I, _I, _P, _D, _I, _P],
+    "tc_cg_destroy": [_P],
+    "tc_cg_setup": [_P, _P],
+    "tc_cg_precond_apply": [_P, _P, _P, _P],
+    "tc_cg_solve": [_P, _P, _P, _I, _P, _P],
+    "tc_ggn_step": [_P, _I, _P, _P],
+}
+for _name, _args in _SIGS.items():
+    _fn = getattr(_lib, _name)
+    _fn.argtypes = _args
+    _fn.restype = _I
+_lib.tc_launch_count.argtypes = []
+_lib.tc_launch_count.restype = _I64
+_lib.tc_status_string.argtypes = [_I]
+_lib.tc_status_string.restype = ctypes.c_char_p
+
+
+class TcError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {_lib.tc_status_string(status).decode()} ({status})")
+        self.status = status
+
+
+def _check(rc: int, what: str, allow=()):
+    if rc != OK and rc not in allow:
+        raise TcError(rc, what)
+    return rc
+
+
+def _ptr(t) -> Optional[int]:
+    return None if t is None else t.data_ptr()
+
+
+def _ptrs(ts: Sequence) -> ctypes.Array:
+    return (ctypes.c_void_p * len(ts))(*[_ptr(t) for t in ts])
+
+
+def _stream(stream=None) -> int:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return s.cuda_stream
+
+
+def _dtype_code(dt: torch.dtype) -> int:
+    if dt == torch.float32:
+        return F32
+    if dt == torch.float64:
+        return F64
+    raise TypeError(f"unsupported dtype {dt}")
+
+
+def launch_count() -> int:
+    """tc_launch_count: kernels this library has launched in this process."""
+    return int(_lib.tc_launch_count())
+
+
+class Pattern:
+    """Owner of a tc_pattern (tc_build_pattern / tc_pattern_destroy)."""
+
+    def __init__(self, handle: int, dims, nnz: int, dtype: torch.dtype, device):
+        self.handle = ctypes.c_void_p(handle)
+        self.dims = tuple(int(d) for d in dims)
+        self.nnz = int(nnz)
+        self.dtype = dtype
+        self.device = device
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            _lib.tc_pattern_destroy(h)
+            self.handle = None
+
+    def view(self, mode: int):
+        """tc_pattern_view as tensors (copies): row_ptr, perm, nonempty_rows."""
+        rp, pm, nz = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+        nne = ctypes.c_int64()
+        _check(_lib.tc_pattern_view(self.handle, mode, ctypes.byref(rp), ctypes.byref(pm),
+                                    ctypes.byref(nz), ctypes.byref(nne)), "tc_pattern_view")
+        torch.cuda.current_stream().synchronize()
+        I = self.dims[mode]
+
+        def grab(ptr, n, dt):
+            out = torch.empty(n, dtype=dt, device=self.device)
+            if n:
+                nbytes = n * out.element_size()
+                _cuda_memcpy_d2d(out.data_ptr(), ptr.value, nbytes)
+            return out
+
+        return (grab(rp, I + 1, torch.int64), grab(pm, self.nnz, torch.int64),
+                grab(nz, nne.value, torch.int32))
+
+
+def _cuda_memcpy_d2d(dst: int, src: int, nbytes: int):
+    # device-to-device copy of a raw pointer through torch (no extra runtime)
+    st = torch.cuda.current_stream()
+    src_t = _raw_tensor(src, nbytes)
+    dst_t = _raw_tensor(dst, nbytes)
+    dst_t.copy_(src_t)
+    st.synchronize()
+
+
+def _raw_tensor(ptr: int, nbytes: int):
+    """A uint8 CUDA tensor view of raw device memory (no ownership)."""
+    class _Holder:
+        __cuda_array_interface__ = {
+            "shape": (nbytes,), "typestr": "|u1", "data": (ptr, False), "version": 3,
+            "strides": None,
+        }
+    return torch.as_tensor(_Holder(), device="cuda")
+
+
+def build_pattern(idx: Sequence[torch.Tensor], dims: Sequence[int], vals: Optional[torch.Tensor] = None,
+                  dtype: torch.dtype = torch.float32, check_duplicates: bool = False,
+                  stream=None) -> Pattern:
+    """tc_build_pattern.  idx: `order` int32 CUDA tensors of length nnz (input
+    order); vals: nnz values of `dtype` or None."""
+    order = len(idx)
+    nnz = int(idx[0].numel())
+    for c in idx:
+        if c.dtype != torch.int32 or not c.is_cuda or not c.is_contiguous() or c.numel() != nnz:
+            raise ValueError("idx must be contiguous int32 CUDA tensors of equal length")
+    if vals is not None and (vals.dtype != dtype or not vals.is_contiguous() or vals.numel() != nnz):
+        raise ValueError("vals must be contiguous, of the pattern dtype and length nnz")
+    dims_arr = (ctypes.c_int64 * order)(*[int(d) for d in dims])
+    out = ctypes.c_void_p()
+    _check(_lib.tc_build_pattern(order, dims_arr, nnz, _ptrs(idx), _ptr(vals), _dtype_code(dtype),
+                                 CHECK_DUPLICATES if check_duplicates else 0, _stream(stream),
+                                 ctypes.byref(out)), "tc_build_pattern")
+    return Pattern(out.value, dims, nnz, dtype, idx[0].device)
+
+
+def last_error(p: Pattern, stream=None) -> int:
+    """tc_last_error: synchronizes and returns (and clears) the device status."""
+    return int(_lib.tc_last_error(p.handle, _stream(stream)))
+
+
+def _wcode(w):
+    if w is None or w == "one":
+        return W_ONE, None
+    if isinstance(w, str) and w == "values":
+        return W_VALUES, None
+    return W_ARRAY, w
+
+
+def tttp(p: Pattern, factors, weights=None, out=None, R=None, stream=None):
+    """tc_tttp.  weights: None/"one" (Omega-hat), "values" (the tensor) or a
+    tensor of nnz weights in pattern order.  Returns x in pattern order."""
+    R = R or next(f.shape[1] for f in factors if f is not None)
+    wk, s = _wcode(weights)
+    if out is None:
+        out = torch.empty(p.nnz, dtype=p.dtype, device=p.device)
+    _check(_lib.tc_tttp(p.handle, wk, _ptr(s), R, _ptrs(factors), _ptr(out), _stream(stream)),
+           "tc_tttp")
+    return out
+
+
+def mttkrp(p: Pattern, factors, mode: int, weights="values", out=None, accumulate=False, R=None,
+           stream=None):
+    """tc_mttkrp into an I_mode x R tensor."""
+    R = R or next(f.shape[1] for i, f in enumerate(factors) if f is not None and i != mode)
+    wk, s = _wcode(weights)
+    if out is None:
+        out = torch.empty((p.dims[mode], R), dtype=p.dtype, device=p.device)
+    _check(_lib.tc_mttkrp(p.handle, wk, _ptr(s), R, _ptrs(factors), mode, _ptr(out),
+                          1 if accumulate else 0, _stream(stream)), "tc_mttkrp")
+    return out
+
+
+def solve_factor(p: Pattern, factors, mode: int, rhs: torch.Tensor, lam: float, weights=None,
+                 out=None, row_status=None, stream=None):
+    """tc_solve_factor: per-row (G_i + lam I) a_i = rhs_i."""
+    R = rhs.shape[1]
+    wk, s = _wcode(weights)
+    if out is None:
+        out = torch.empty_like(rhs)
+    _check(_lib.tc_solve_factor(p.handle, wk, _ptr(s), R, _ptrs(factors), mode, _ptr(rhs),
+                                float(lam), _ptr(out), _ptr(row_status), _stream(stream)),
+           "tc_solve_factor")
+    return out
+
+
+def loss_grad(p: Pattern, factors, loss: str, lam: float, want_loss=True, want_grad=True,
+              grads=None, stream=None):
+    """tc_loss_grad: (loss as a 1-element float64 tensor or None, [grads] or None)."""
+    R = factors[0].shape[1]
+    loss_t = torch.empty(1, dtype=torch.float64, device=p.device) if want_loss else None
+    if want_grad and grads is None:
+        grads = [torch.empty_like(f) for f in factors]
+    gp = _ptrs(grads) if want_grad else None
+    _check(_lib.tc_loss_grad(p.handle, LOSSES[loss], R, _ptrs(factors), float(lam), _ptr(loss_t),
+                             gp, _stream(stream)), "tc_loss_grad")
+    return loss_t, (grads if want_grad else None)
+
+
+def ggn_matvec(p: Pattern, factors, x, loss: str, lam: float, y=None, stream=None):
+    """tc_ggn_matvec: y = (J^T diag(phi'') J + 2 lam I) x."""
+    R = factors[0].shape[1]
+    if y is None:
+        y = [torch.empty_like(v) for v in x]
+    _check(_lib.tc_ggn_matvec(p.handle, LOSSES[loss], R, _ptrs(factors), _ptrs(x), float(lam),
+                              _ptrs(y), _stream(stream)), "tc_ggn_matvec")
+    return y
+
+
+class CG:
+    """tc_cg_*: preconditioned CG on the Gauss-Newton system and GGN steps.
+    The factor tensors are kept (and updated in place by ggn_step)."""
+
+    def __init__(self, p: Pattern, factors, loss: str, lam: float, precondition=True):
+        self.p = p
+        self.factors = list(factors)
+        self.R = factors[0].shape[1]
+        h = ctypes.c_void_p()
+        _check(_lib.tc_cg_create(p.handle, LOSSES[loss], self.R, _ptrs(self.factors), float(lam),
+                                 1 if precondition else 0, ctypes.byref(h)), "tc_cg_create")
+        self.handle = h
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            _lib.tc_cg_destroy(h)
+            self.handle = None
+
+    def setup(self, stream=None):
+        _check(_lib.tc_cg_setup(self.handle, _stream(stream)), "tc_cg_setup")
+
+    def precond_apply(self, r, z=None, stream=None):
+        if z is None:
+            z = [torch.empty_like(v) for v in r]
+        _check(_lib.tc_cg_precond_apply(self.handle, _ptrs(r), _ptrs(z), _stream(stream)),
+               "tc_cg_precond_apply")
+        return z
+
+    def solve(self, b, iters: int, dx=None, rz=None, stream=None):
+        if dx is None:
+            dx = [torch.empty_like(v) for v in b]
+        _check(_lib.tc_cg_solve(self.handle, _ptrs(b), _ptrs(dx), int(iters), _ptr(rz),
+                                _stream(stream)), "tc_cg_solve")
+        return dx
+
+    def ggn_step(self, iters: int, loss_out=None, stream=None):
+        _check(_lib.tc_ggn_step(self.handle, int(iters), _ptr(loss_out), _stream(stream)),
+               "tc_ggn_step")
