@@ -81,6 +81,8 @@ typedef enum { TC_W_ONE = 0, TC_W_VALUES = 1, TC_W_ARRAY = 2 } tc_weights;
 
 /* tc_build_pattern flags */
 #define TC_PATTERN_CHECK_DUPLICATES 1u  /* extra sort that rejects repeated coordinates */
+#define TC_PATTERN_REFILLABLE 2u        /* keep the builder's work space for tc_pattern_refill
+                                           (about 24 bytes per nonzero) */
 
 typedef struct tc_pattern tc_pattern;
 
@@ -102,6 +104,17 @@ tc_status tc_build_pattern(int order, const int64_t *dims, int64_t nnz,
                            const int32_t *const *idx, const void *vals, tc_dtype dtype,
                            unsigned flags, tc_stream_t stream, tc_pattern **out);
 
+/* Rebuilds pattern p in place from a new tensor with the same order, dims,
+ * nnz and dtype (a new batch of observations), reusing every device array, so
+ * kernels and captured CUDA graphs that reference p see the new contents.
+ * p must have been built with TC_PATTERN_REFILLABLE (else TC_ERR_ARG).  vals
+ * must be given iff p was built with values.  Fully asynchronous and
+ * allocation-free: out-of-range indices or duplicates (if p checks them) are
+ * recorded in the status word for tc_last_error; out-of-range indices are
+ * clamped into range in the sorted copies so later kernels stay in bounds. */
+tc_status tc_pattern_refill(tc_pattern *p, const int32_t *const *idx, const void *vals,
+                            tc_stream_t stream);
+
 /* Frees the pattern's device memory (after synchronizing its device). */
 tc_status tc_pattern_destroy(tc_pattern *p);
 
@@ -109,7 +122,7 @@ tc_status tc_pattern_destroy(tc_pattern *p);
  * raw structure: row_ptr[I_mode + 1] (row i's nonzeros are sorted positions
  * row_ptr[i] .. row_ptr[i+1]-1); perm[nnz] (sorted position -> input position;
  * equal indices keep input order); nonempty_rows[n_nonempty] (ascending).
- * Any output pointer may be NULL. */
+ * Any output pointer may be NULL.  Reading n_nonempty synchronizes the device. */
 tc_status tc_pattern_view(const tc_pattern *p, int mode, const int64_t **row_ptr,
                           const int64_t **perm, const int32_t **nonempty_rows,
                           int64_t *n_nonempty);

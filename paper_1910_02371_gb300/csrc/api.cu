@@ -17,7 +17,7 @@ static tc_status launch_status() {
 
 static tc_status check_weights(const tc_pattern *p, tc_weights w, const void *s) {
     if (w == TC_W_ONE) return TC_OK;
-    if (w == TC_W_VALUES) return p->has_vals ? TC_OK : TC_ERR_ARG;
+    if (w == TC_W_VALUES) return (p->has_vals || p->nnz == 0) ? TC_OK : TC_ERR_ARG;
     if (w == TC_W_ARRAY) return (s || p->nnz == 0) ? TC_OK : TC_ERR_ARG;
     return TC_ERR_ARG;
 }
@@ -57,7 +57,7 @@ tc_status tc_build_pattern(int order, const int64_t *dims, int64_t nnz, const in
     *out = nullptr;
     if (order != TC_ORDER) return order >= 1 ? TC_ERR_UNSUPPORTED : TC_ERR_ARG;
     if (!dims || nnz < 0 || (dtype != TC_F32 && dtype != TC_F64)) return TC_ERR_ARG;
-    if (flags & ~TC_PATTERN_CHECK_DUPLICATES) return TC_ERR_ARG;
+    if (flags & ~(TC_PATTERN_CHECK_DUPLICATES | TC_PATTERN_REFILLABLE)) return TC_ERR_ARG;
     for (int d = 0; d < TC_ORDER; ++d)
         if (dims[d] < 1 || dims[d] > INT32_MAX) return TC_ERR_ARG;
     if (nnz > 0) {
@@ -75,6 +75,19 @@ tc_status tc_build_pattern(int order, const int64_t *dims, int64_t nnz, const in
     return rc;
 }
 
+tc_status tc_pattern_refill(tc_pattern *p, const int32_t *const *idx, const void *vals,
+                            tc_stream_t stream) {
+    if (!p) return TC_ERR_ARG;
+    if ((vals != nullptr) != (p->has_vals != 0) && p->nnz > 0) return TC_ERR_ARG;
+    if (p->nnz > 0) {
+        if (!idx) return TC_ERR_ARG;
+        for (int d = 0; d < TC_ORDER; ++d)
+            if (!idx[d]) return TC_ERR_ARG;
+    }
+    tc_status rc = refill_pattern_impl(p, idx, vals, (cudaStream_t)stream);
+    return rc != TC_OK ? rc : launch_status();
+}
+
 tc_status tc_pattern_destroy(tc_pattern *p) {
     if (!p) return TC_ERR_ARG;
     cudaDeviceSynchronize();
@@ -90,7 +103,11 @@ tc_status tc_pattern_view(const tc_pattern *p, int mode, const int64_t **row_ptr
     if (row_ptr) *row_ptr = m.row_ptr;
     if (perm) *perm = m.perm;
     if (nonempty_rows) *nonempty_rows = m.nz_rows;
-    if (n_nonempty) *n_nonempty = m.n_ne;
+    if (n_nonempty) {
+        if (cudaDeviceSynchronize() != cudaSuccess ||
+            cudaMemcpy(n_nonempty, m.n_ne_dev, sizeof(int64_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return TC_ERR_CUDA;
+    }
     return TC_OK;
 }
 

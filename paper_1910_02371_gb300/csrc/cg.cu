@@ -238,7 +238,7 @@ tc_status tc_cg_create(const tc_pattern *p, tc_loss loss, int R, const void *con
                        double lambda, int precondition, tc_cg **out) {
     if (!p || !factors || !out || R < 1 || R > TC_MAX_RANK) return TC_ERR_ARG;
     if (loss < TC_LOSS_LS || loss > TC_LOSS_POISSON_ID) return TC_ERR_ARG;
-    if (!p->has_vals) return TC_ERR_ARG;
+    if (!p->has_vals && p->nnz > 0) return TC_ERR_ARG;
     for (int d = 0; d < TC_ORDER; ++d)
         if (!factors[d]) return TC_ERR_ARG;
     tc_cg *cg = new (std::nothrow) tc_cg();

@@ -16,14 +16,22 @@ struct ModeData {
     int64_t *row_ptr = nullptr;   // I_d + 1
     int64_t *perm = nullptr;      // nnz: sorted position -> input position
     int64_t *to0 = nullptr;       // nnz: mode-d position -> mode-0 position (d > 0)
-    int32_t *nz_rows = nullptr;   // n_ne nonempty rows, ascending
-    int64_t *nz_ptr = nullptr;    // n_ne + 1 offsets of the nonempty rows
-    int64_t n_ne = 0;
+    int32_t *nz_rows = nullptr;   // nonempty rows, ascending (capacity I_d)
+    int64_t *nz_ptr = nullptr;    // offsets of the nonempty rows (capacity I_d + 1)
+    int64_t *n_ne_dev = nullptr;  // device: number of nonempty rows
     int32_t *cols[TC_ORDER - 1] = {nullptr, nullptr};  // other modes, ascending mode order
     void *vals = nullptr;         // nnz values in this mode's order (or null)
 };
 
+// Work space of the builder, kept when the pattern may be refilled.
+struct PatternScratch {
+    int32_t *kbuf = nullptr, *ktmp = nullptr, *dk = nullptr;
+    int64_t *vtmp = nullptr, *inv0 = nullptr, *hist = nullptr, *scan = nullptr, *flags = nullptr,
+            *dp = nullptr;
+};
+
 struct tc_pattern {
+    unsigned flags = 0;
     int order = 0;
     int64_t dims[TC_ORDER] = {0, 0, 0};
     int64_t nnz = 0;
@@ -32,6 +40,8 @@ struct tc_pattern {
     int device = 0;
     ModeData md[TC_ORDER];
     int *status = nullptr;        // device word: first error recorded, 0 if none
+    int64_t *counts = nullptr;    // device: nonempty rows per mode
+    PatternScratch work;
     double *dscratch = nullptr;   // device doubles for reductions (kScratchDoubles)
 };
 
@@ -106,6 +116,8 @@ tc_status launch_chol_apply(const tc_pattern *p, int R, int mode, const double *
 tc_status build_pattern_impl(int order, const int64_t *dims, int64_t nnz,
                              const int32_t *const *idx, const void *vals, tc_dtype dtype,
                              unsigned flags, cudaStream_t st, tc_pattern **out);
+tc_status refill_pattern_impl(tc_pattern *p, const int32_t *const *idx, const void *vals,
+                              cudaStream_t st);
 void free_pattern(tc_pattern *p);
 
 }  // namespace tc

@@ -77,26 +77,34 @@ __global__ void scan_tile_kernel(const int64_t *__restrict__ in, int64_t n,
     }
 }
 
-// Exclusive scan of n int64 values (in may equal out).
-static tc_status scan_exclusive(const int64_t *in, int64_t *out, int64_t n, cudaStream_t st) {
-    if (n <= 0) return TC_OK;
+// Scratch (int64 elements) needed to scan n values: one block sum per tile
+// per recursion level.
+static int64_t scan_scratch_elems(int64_t n) {
+    int64_t total = 0;
+    while (n > kScanTile) {
+        n = (n + kScanTile - 1) / kScanTile;
+        total += n;
+    }
+    return total;
+}
+
+// Exclusive scan of n int64 values (in may equal out); block sums live in
+// `scratch` (scan_scratch_elems(n) elements).  Allocates nothing.
+static void scan_exclusive(const int64_t *in, int64_t *out, int64_t n, int64_t *scratch,
+                           cudaStream_t st) {
+    if (n <= 0) return;
     const int64_t nb = (n + kScanTile - 1) / kScanTile;
     if (nb == 1) {
         scan_tile_kernel<<<1, kScanThreads, 0, st>>>(in, n, nullptr, out);
         count_launch();
-        return TC_OK;
+        return;
     }
-    int64_t *sums = nullptr;
-    TC_CUDA(cudaMallocAsync((void **)&sums, sizeof(int64_t) * nb, st));
+    int64_t *sums = scratch;
     scan_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(in, n, sums);
     count_launch();
-    tc_status rc = scan_exclusive(sums, sums, nb, st);
-    if (rc == TC_OK) {
-        scan_tile_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(in, n, sums, out);
-        count_launch();
-    }
-    cudaFreeAsync(sums, st);
-    return rc;
+    scan_exclusive(sums, sums, nb, scratch + nb, st);
+    scan_tile_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(in, n, sums, out);
+    count_launch();
 }
 
 // ------------------------------------------------------------------ radix sort
@@ -184,44 +192,40 @@ static unsigned grid_for(int64_t n, int threads, int64_t cap = 1 << 20) {
     return (unsigned)b;
 }
 
+static int64_t sort_tiles(int64_t n) { return (n + kTile - 1) / kTile; }
+
 // Stable sort of (key, value) pairs by key in [0, max_key]; vals_in == null
-// means value = input position.  Results in kout / vout; ktmp / vtmp scratch.
-static tc_status radix_sort(const int32_t *keys_in, const int64_t *vals_in, int64_t n,
-                            int64_t max_key, int32_t *kout, int64_t *vout, int32_t *ktmp,
-                            int64_t *vtmp, cudaStream_t st) {
+// means value = input position.  Results in kout / vout; ktmp / vtmp, hist
+// (kDigits * sort_tiles(n)) and scan scratch are work space.  Allocates nothing.
+static void radix_sort(const int32_t *keys_in, const int64_t *vals_in, int64_t n, int64_t max_key,
+                       int32_t *kout, int64_t *vout, int32_t *ktmp, int64_t *vtmp, int64_t *hist,
+                       int64_t *scan_scratch, cudaStream_t st) {
     int bits = 0;
     while (bits < 31 && (max_key >> bits) > 0) ++bits;
     const int passes = (bits + kRadixBits - 1) / kRadixBits;
-    if (passes == 0 || n == 0) {
-        if (n > 0) {
-            iota_copy_kernel<<<grid_for(n, 256), 256, 0, st>>>(keys_in, vals_in, n, kout, vout);
-            count_launch();
-        }
-        return TC_OK;
+    if (n == 0) return;
+    if (passes == 0) {
+        iota_copy_kernel<<<grid_for(n, 256), 256, 0, st>>>(keys_in, vals_in, n, kout, vout);
+        count_launch();
+        return;
     }
-    const int64_t num_tiles = (n + kTile - 1) / kTile;
-    int64_t *hist = nullptr;
-    TC_CUDA(cudaMallocAsync((void **)&hist, sizeof(int64_t) * kDigits * num_tiles, st));
+    const int64_t num_tiles = sort_tiles(n);
     const int32_t *ks = keys_in;
     const int64_t *vs = vals_in;
-    tc_status rc = TC_OK;
-    for (int p = 0; p < passes && rc == TC_OK; ++p) {
+    for (int p = 0; p < passes; ++p) {
         const bool to_out = ((passes - 1 - p) % 2) == 0;
         int32_t *kd = to_out ? kout : ktmp;
         int64_t *vd = to_out ? vout : vtmp;
         const int shift = p * kRadixBits;
         radix_hist_kernel<<<(unsigned)num_tiles, kSortThreads, 0, st>>>(ks, n, shift, num_tiles, hist);
         count_launch();
-        rc = scan_exclusive(hist, hist, kDigits * num_tiles, st);
-        if (rc != TC_OK) break;
+        scan_exclusive(hist, hist, kDigits * num_tiles, scan_scratch, st);
         radix_scatter_kernel<<<(unsigned)num_tiles, kSortThreads, 0, st>>>(ks, vs, n, shift, num_tiles,
                                                                           hist, kd, vd);
         count_launch();
         ks = kd;
         vs = vd;
     }
-    cudaFreeAsync(hist, st);
-    return rc;
 }
 
 // ------------------------------------------------------------------ pattern kernels
@@ -238,12 +242,14 @@ __global__ void range_check_kernel(const int32_t *__restrict__ idx, int64_t n, i
 }
 
 // row_ptr from sorted keys: row r starts at the first position with key >= r.
+// Keys outside [0, I) (already recorded as TC_ERR_RANGE) are clamped so that no
+// write leaves the array.
 __global__ void row_ptr_kernel(const int32_t *__restrict__ sk, int64_t n, int64_t I,
                                int64_t *__restrict__ row_ptr) {
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
          q += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t key = sk[q];
-        const int64_t prev = q > 0 ? (int64_t)sk[q - 1] : -1;
+        const int64_t key = min(max((int64_t)sk[q], (int64_t)-1), I - 1);
+        const int64_t prev = q > 0 ? min(max((int64_t)sk[q - 1], (int64_t)-1), I - 1) : -1;
         for (int64_t r = prev + 1; r <= key; ++r) row_ptr[r] = q;
         if (q == n - 1)
             for (int64_t r = key + 1; r <= I; ++r) row_ptr[r] = n;
@@ -257,24 +263,36 @@ __global__ void nonempty_flags_kernel(const int64_t *__restrict__ row_ptr, int64
         flags[r] = row_ptr[r + 1] > row_ptr[r] ? 1 : 0;
 }
 
+// Compacts the nonempty rows; the last row also writes their count.
 __global__ void nonempty_fill_kernel(const int64_t *__restrict__ row_ptr, int64_t I,
                                      const int64_t *__restrict__ pos, int64_t n,
-                                     int32_t *__restrict__ nz_rows, int64_t *__restrict__ nz_ptr) {
+                                     int32_t *__restrict__ nz_rows, int64_t *__restrict__ nz_ptr,
+                                     int64_t *__restrict__ n_ne) {
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < I;
          r += (int64_t)gridDim.x * blockDim.x) {
-        if (row_ptr[r + 1] > row_ptr[r]) {
+        const bool ne = row_ptr[r + 1] > row_ptr[r];
+        if (ne) {
             nz_rows[pos[r]] = (int32_t)r;
             nz_ptr[pos[r]] = row_ptr[r];
         }
-        if (r == I - 1) nz_ptr[pos[r] + (row_ptr[r + 1] > row_ptr[r] ? 1 : 0)] = n;
+        if (r == I - 1) {
+            const int64_t cnt = pos[r] + (ne ? 1 : 0);
+            nz_ptr[cnt] = n;
+            *n_ne = cnt;
+        }
     }
 }
 
+// dst[q] = src[perm[q]], clamped to [0, I): an index outside the range is
+// already recorded as TC_ERR_RANGE, and clamping keeps every later factor
+// read of this pattern inside its matrix.
 __global__ void gather_i32_kernel(const int32_t *__restrict__ src, const int64_t *__restrict__ perm,
-                                  int64_t n, int32_t *__restrict__ dst) {
+                                  int64_t n, int64_t I, int32_t *__restrict__ dst) {
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
-         q += (int64_t)gridDim.x * blockDim.x)
-        dst[q] = src[perm[q]];
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = src[perm[q]];
+        dst[q] = v < 0 ? 0 : ((int64_t)v >= I ? (int32_t)(I - 1) : v);
+    }
 }
 
 template <typename T>
@@ -327,130 +345,123 @@ void free_pattern(tc_pattern *p) {
         cudaFree(m.cols[1]);
         cudaFree(m.vals);
     }
+    PatternScratch &w = p->work;
+    cudaFree(w.kbuf);
+    cudaFree(w.ktmp);
+    cudaFree(w.vtmp);
+    cudaFree(w.inv0);
+    cudaFree(w.hist);
+    cudaFree(w.scan);
+    cudaFree(w.flags);
+    cudaFree(w.dk);
+    cudaFree(w.dp);
     cudaFree(p->status);
+    cudaFree(p->counts);
     cudaFree(p->dscratch);
     delete p;
 }
 
-#define TC_TRY(x)                      \
-    do {                               \
-        tc_status r_ = (x);            \
-        if (r_ != TC_OK) {             \
-            rc = r_;                   \
-            goto fail;                 \
-        }                              \
-    } while (0)
-#define TC_ALLOC(ptr, bytes)                                                     \
-    do {                                                                         \
-        if (cudaMalloc((void **)&(ptr), (bytes) > 0 ? (bytes) : 16) != cudaSuccess) { \
-            rc = TC_ERR_OOM;                                                     \
-            goto fail;                                                           \
-        }                                                                        \
-    } while (0)
+static bool dalloc(void **ptr, size_t bytes) {
+    return cudaMalloc(ptr, bytes > 0 ? bytes : 16) == cudaSuccess;
+}
 
-tc_status build_pattern_impl(int order, const int64_t *dims, int64_t nnz,
-                             const int32_t *const *idx, const void *vals, tc_dtype dtype,
-                             unsigned flags, cudaStream_t st, tc_pattern **out) {
-    tc_status rc = TC_OK;
-    tc_pattern *p = new (std::nothrow) tc_pattern();
-    if (!p) return TC_ERR_OOM;
-    int32_t *kbuf = nullptr, *ktmp = nullptr;
-    int64_t *vtmp = nullptr, *inv0 = nullptr, *flags_buf = nullptr, *dp = nullptr;
-    int32_t *dk = nullptr;
-    const size_t es = tsize(dtype);
-    const int64_t n = nnz;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    p->device = dev;
-    p->order = order;
-    p->nnz = nnz;
-    p->dtype = dtype;
-    p->has_vals = vals != nullptr;
-    for (int d = 0; d < TC_ORDER; ++d) p->dims[d] = dims[d];
+static void free_scratch(tc_pattern *p) {
+    PatternScratch &w = p->work;
+    cudaFree(w.kbuf);
+    cudaFree(w.ktmp);
+    cudaFree(w.vtmp);
+    cudaFree(w.inv0);
+    cudaFree(w.hist);
+    cudaFree(w.scan);
+    cudaFree(w.flags);
+    cudaFree(w.dk);
+    cudaFree(w.dp);
+    w = PatternScratch();
+}
 
-    TC_ALLOC(p->status, sizeof(int));
-    TC_ALLOC(p->dscratch, sizeof(double) * kScratchDoubles);
-    if (cudaMemsetAsync(p->status, 0, sizeof(int), st) != cudaSuccess) {
-        rc = TC_ERR_CUDA;
-        goto fail;
+static tc_status alloc_scratch(tc_pattern *p) {
+    PatternScratch &w = p->work;
+    const int64_t n = p->nnz;
+    int64_t maxI = 0;
+    for (int d = 0; d < TC_ORDER; ++d) maxI = p->dims[d] > maxI ? p->dims[d] : maxI;
+    const int64_t hist_n = (int64_t)kDigits * sort_tiles(n);
+    int64_t scan_n = scan_scratch_elems(hist_n);
+    const int64_t s2 = scan_scratch_elems(maxI);
+    if (s2 > scan_n) scan_n = s2;
+    bool ok = dalloc((void **)&w.kbuf, sizeof(int32_t) * n) &&
+              dalloc((void **)&w.ktmp, sizeof(int32_t) * n) &&
+              dalloc((void **)&w.vtmp, sizeof(int64_t) * n) &&
+              dalloc((void **)&w.inv0, sizeof(int64_t) * n) &&
+              dalloc((void **)&w.hist, sizeof(int64_t) * hist_n) &&
+              dalloc((void **)&w.scan, sizeof(int64_t) * (scan_n + 1)) &&
+              dalloc((void **)&w.flags, sizeof(int64_t) * maxI);
+    if (ok && (p->flags & TC_PATTERN_CHECK_DUPLICATES))
+        ok = dalloc((void **)&w.dk, sizeof(int32_t) * n) && dalloc((void **)&w.dp, sizeof(int64_t) * n);
+    return ok ? TC_OK : TC_ERR_OOM;
+}
+
+// Allocates every array of a pattern (and its scratch) for the given shape.
+static tc_status alloc_pattern(tc_pattern *p) {
+    const int64_t n = p->nnz;
+    const size_t es = tsize(p->dtype);
+    bool ok = dalloc((void **)&p->status, sizeof(int)) &&
+              dalloc((void **)&p->counts, sizeof(int64_t) * TC_ORDER) &&
+              dalloc((void **)&p->dscratch, sizeof(double) * kScratchDoubles);
+    for (int d = 0; d < TC_ORDER && ok; ++d) {
+        ModeData &m = p->md[d];
+        const int64_t I = p->dims[d];
+        ok = dalloc((void **)&m.row_ptr, sizeof(int64_t) * (I + 1)) &&
+             dalloc((void **)&m.perm, sizeof(int64_t) * n) &&
+             dalloc((void **)&m.nz_rows, sizeof(int32_t) * I) &&
+             dalloc((void **)&m.nz_ptr, sizeof(int64_t) * (I + 1)) &&
+             dalloc((void **)&m.cols[0], sizeof(int32_t) * n) &&
+             dalloc((void **)&m.cols[1], sizeof(int32_t) * n) &&
+             (!p->has_vals || dalloc(&m.vals, es * n)) &&
+             (d == 0 || dalloc((void **)&m.to0, sizeof(int64_t) * n));
+        m.n_ne_dev = p->counts ? p->counts + d : nullptr;
     }
+    if (!ok) return TC_ERR_OOM;
+    return alloc_scratch(p);
+}
+
+// Fills the pattern from the input coordinates; asynchronous on st, allocates
+// nothing.  Range errors and duplicates are recorded in the status word.
+static void fill_pattern(tc_pattern *p, const int32_t *const *idx, const void *vals,
+                         cudaStream_t st) {
+    const int64_t n = p->nnz;
+    PatternScratch &w = p->work;
     for (int d = 0; d < TC_ORDER; ++d) {
         if (n > 0) {
-            range_check_kernel<<<grid_for(n, 256, 4096), 256, 0, st>>>(idx[d], n, dims[d], p->status);
+            range_check_kernel<<<grid_for(n, 256, 4096), 256, 0, st>>>(idx[d], n, p->dims[d],
+                                                                       p->status);
             count_launch();
         }
     }
-    TC_ALLOC(kbuf, sizeof(int32_t) * n);
-    TC_ALLOC(ktmp, sizeof(int32_t) * n);
-    TC_ALLOC(vtmp, sizeof(int64_t) * n);
     for (int d = 0; d < TC_ORDER; ++d) {
         ModeData &m = p->md[d];
-        const int64_t I = dims[d];
-        TC_ALLOC(m.perm, sizeof(int64_t) * n);
-        TC_ALLOC(m.row_ptr, sizeof(int64_t) * (I + 1));
-        // a range error would make the sort write out of bounds: stop before it
-        {
-            int h = 0;
-            if (cudaMemcpyAsync(&h, p->status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-                cudaStreamSynchronize(st) != cudaSuccess) {
-                rc = TC_ERR_CUDA;
-                goto fail;
-            }
-            if (h) {
-                rc = (tc_status)h;
-                goto fail;
-            }
-        }
-        TC_TRY(radix_sort(idx[d], nullptr, n, I - 1, kbuf, m.perm, ktmp, vtmp, st));
-        if (cudaMemsetAsync(m.row_ptr, 0, sizeof(int64_t) * (I + 1), st) != cudaSuccess) {
-            rc = TC_ERR_CUDA;
-            goto fail;
-        }
+        const int64_t I = p->dims[d];
+        // keys outside [0, I) still sort into a permutation of [0, n): digits
+        // are taken from the low bits, so no write leaves the arrays
+        radix_sort(idx[d], nullptr, n, I - 1, w.kbuf, m.perm, w.ktmp, w.vtmp, w.hist, w.scan, st);
+        cudaMemsetAsync(m.row_ptr, 0, sizeof(int64_t) * (I + 1), st);
         if (n > 0) {
-            row_ptr_kernel<<<grid_for(n, 256), 256, 0, st>>>(kbuf, n, I, m.row_ptr);
+            row_ptr_kernel<<<grid_for(n, 256), 256, 0, st>>>(w.kbuf, n, I, m.row_ptr);
             count_launch();
         }
-        // nonempty rows
-        TC_ALLOC(flags_buf, sizeof(int64_t) * I);
-        nonempty_flags_kernel<<<grid_for(I, 256), 256, 0, st>>>(m.row_ptr, I, flags_buf);
+        nonempty_flags_kernel<<<grid_for(I, 256), 256, 0, st>>>(m.row_ptr, I, w.flags);
         count_launch();
-        int64_t last_flag = 0;
-        if (cudaMemcpyAsync(&last_flag, flags_buf + (I - 1), sizeof(int64_t), cudaMemcpyDeviceToHost,
-                            st) != cudaSuccess) {
-            rc = TC_ERR_CUDA;
-            goto fail;
-        }
-        TC_TRY(scan_exclusive(flags_buf, flags_buf, I, st));
-        int64_t last_pos = 0;
-        if (cudaMemcpyAsync(&last_pos, flags_buf + (I - 1), sizeof(int64_t), cudaMemcpyDeviceToHost,
-                            st) != cudaSuccess ||
-            cudaStreamSynchronize(st) != cudaSuccess) {
-            rc = TC_ERR_CUDA;
-            goto fail;
-        }
-        m.n_ne = last_pos + last_flag;
-        TC_ALLOC(m.nz_rows, sizeof(int32_t) * m.n_ne);
-        TC_ALLOC(m.nz_ptr, sizeof(int64_t) * (m.n_ne + 1));
-        nonempty_fill_kernel<<<grid_for(I, 256), 256, 0, st>>>(m.row_ptr, I, flags_buf, n, m.nz_rows,
-                                                               m.nz_ptr);
+        scan_exclusive(w.flags, w.flags, I, w.scan, st);
+        nonempty_fill_kernel<<<grid_for(I, 256), 256, 0, st>>>(m.row_ptr, I, w.flags, n, m.nz_rows,
+                                                               m.nz_ptr, m.n_ne_dev);
         count_launch();
-        cudaStreamSynchronize(st);
-        cudaFree(flags_buf);
-        flags_buf = nullptr;
-        // the other modes' indices and the values in this mode's order
         int o1, o2;
         other_modes(d, o1, o2);
-        TC_ALLOC(m.cols[0], sizeof(int32_t) * n);
-        TC_ALLOC(m.cols[1], sizeof(int32_t) * n);
         if (n > 0) {
-            gather_i32_kernel<<<grid_for(n, 256), 256, 0, st>>>(idx[o1], m.perm, n, m.cols[0]);
-            gather_i32_kernel<<<grid_for(n, 256), 256, 0, st>>>(idx[o2], m.perm, n, m.cols[1]);
+            gather_i32_kernel<<<grid_for(n, 256), 256, 0, st>>>(idx[o1], m.perm, n, p->dims[o1], m.cols[0]);
+            gather_i32_kernel<<<grid_for(n, 256), 256, 0, st>>>(idx[o2], m.perm, n, p->dims[o2], m.cols[1]);
             count_launch(2);
-        }
-        if (vals) {
-            TC_ALLOC(m.vals, es * n);
-            if (n > 0) {
-                if (dtype == TC_F64)
+            if (p->has_vals) {
+                if (p->dtype == TC_F64)
                     gather_val_kernel<double><<<grid_for(n, 256), 256, 0, st>>>(
                         (const double *)vals, m.perm, n, (double *)m.vals);
                 else
@@ -461,68 +472,76 @@ tc_status build_pattern_impl(int order, const int64_t *dims, int64_t nnz,
         }
     }
     // mode-d position -> mode-0 position, for caller arrays in pattern order
-    TC_ALLOC(inv0, sizeof(int64_t) * n);
     if (n > 0) {
-        invert_perm_kernel<<<grid_for(n, 256), 256, 0, st>>>(p->md[0].perm, n, inv0);
+        invert_perm_kernel<<<grid_for(n, 256), 256, 0, st>>>(p->md[0].perm, n, w.inv0);
         count_launch();
-    }
-    for (int d = 1; d < TC_ORDER; ++d) {
-        TC_ALLOC(p->md[d].to0, sizeof(int64_t) * n);
-        if (n > 0) {
-            compose_kernel<<<grid_for(n, 256), 256, 0, st>>>(inv0, p->md[d].perm, n, p->md[d].to0);
+        for (int d = 1; d < TC_ORDER; ++d) {
+            compose_kernel<<<grid_for(n, 256), 256, 0, st>>>(w.inv0, p->md[d].perm, n, p->md[d].to0);
             count_launch();
         }
     }
-    if ((flags & TC_PATTERN_CHECK_DUPLICATES) && n > 1) {
-        // lexicographic order by (i_0, i_1, i_2): stable sorts by i_2, then i_1, then i_0.
-        // inv0 is free again; dk holds gathered keys, dp the next permutation.
-        TC_ALLOC(dk, sizeof(int32_t) * n);
-        TC_ALLOC(dp, sizeof(int64_t) * n);
+    if ((p->flags & TC_PATTERN_CHECK_DUPLICATES) && n > 1) {
+        // lexicographic order by (i_0, i_1, i_2): stable sorts by i_2, then i_1, then i_0
         int64_t *cur = nullptr;
         for (int d = TC_ORDER - 1; d >= 0; --d) {
-            int64_t *dst = (cur == inv0) ? dp : inv0;
+            int64_t *dst = (cur == w.inv0) ? w.dp : w.inv0;
             if (cur) {
-                gather_i32_kernel<<<grid_for(n, 256), 256, 0, st>>>(idx[d], cur, n, dk);
+                gather_i32_kernel<<<grid_for(n, 256), 256, 0, st>>>(idx[d], cur, n, p->dims[d], w.dk);
                 count_launch();
             }
-            TC_TRY(radix_sort(cur ? dk : idx[d], cur, n, dims[d] - 1, kbuf, dst, ktmp, vtmp, st));
+            radix_sort(cur ? w.dk : idx[d], cur, n, p->dims[d] - 1, w.kbuf, dst, w.ktmp, w.vtmp,
+                       w.hist, w.scan, st);
             cur = dst;
         }
         dup_check_kernel<<<grid_for(n, 256), 256, 0, st>>>(idx[0], idx[1], idx[2], cur, n, p->status);
         count_launch();
-        cudaStreamSynchronize(st);
     }
-    {
-        int h = 0;
-        if (cudaMemcpyAsync(&h, p->status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-            cudaStreamSynchronize(st) != cudaSuccess) {
-            rc = TC_ERR_CUDA;
-            goto fail;
-        }
-        if (h) {
-            rc = (tc_status)h;
-            goto fail;
-        }
+}
+
+tc_status build_pattern_impl(int order, const int64_t *dims, int64_t nnz,
+                             const int32_t *const *idx, const void *vals, tc_dtype dtype,
+                             unsigned flags, cudaStream_t st, tc_pattern **out) {
+    tc_pattern *p = new (std::nothrow) tc_pattern();
+    if (!p) return TC_ERR_OOM;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    p->device = dev;
+    p->order = order;
+    p->nnz = nnz;
+    p->dtype = dtype;
+    p->has_vals = vals != nullptr;
+    p->flags = flags;
+    for (int d = 0; d < TC_ORDER; ++d) p->dims[d] = dims[d];
+    tc_status rc = alloc_pattern(p);
+    if (rc != TC_OK) {
+        free_pattern(p);
+        return rc;
     }
-    cudaFree(kbuf);
-    cudaFree(ktmp);
-    cudaFree(vtmp);
-    cudaFree(inv0);
-    cudaFree(dk);
-    cudaFree(dp);
+    if (cudaMemsetAsync(p->status, 0, sizeof(int), st) != cudaSuccess) {
+        free_pattern(p);
+        return TC_ERR_CUDA;
+    }
+    fill_pattern(p, idx, vals, st);
+    int h = 0;
+    if (cudaMemcpyAsync(&h, p->status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        free_pattern(p);
+        return TC_ERR_CUDA;
+    }
+    if (h) {
+        free_pattern(p);
+        return (tc_status)h;
+    }
+    if (!(flags & TC_PATTERN_REFILLABLE)) free_scratch(p);
     *out = p;
     return TC_OK;
-fail:
-    cudaStreamSynchronize(st);
-    cudaFree(kbuf);
-    cudaFree(ktmp);
-    cudaFree(vtmp);
-    cudaFree(inv0);
-    cudaFree(flags_buf);
-    cudaFree(dk);
-    cudaFree(dp);
-    free_pattern(p);
-    return rc;
+}
+
+tc_status refill_pattern_impl(tc_pattern *p, const int32_t *const *idx, const void *vals,
+                              cudaStream_t st) {
+    if (!p->work.kbuf) return TC_ERR_ARG;     // built without TC_PATTERN_REFILLABLE
+    fill_pattern(p, idx, vals, st);
+    return TC_OK;
 }
 
 }  // namespace tc

@@ -21,7 +21,8 @@ template <typename T>
 struct SweepParams {
     const int32_t *nz_rows;
     const int64_t *nz_ptr;
-    int64_t n_ne, nnz, chunk;
+    const int64_t *n_ne_dev;      // number of nonempty rows (device)
+    int64_t nnz, chunk;
     const int32_t *c1, *c2;       // indices of the two other modes, this mode's order
     Weights<T> w;                 // OP_MTTKRP weights
     const T *t;                   // observed values, this mode's order (GRAD / GGN)
@@ -47,11 +48,12 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepParams<T> P) {
     const int64_t cend = active ? min(c0 + P.chunk, P.nnz) : c0;
     const int64_t *__restrict__ nzp = P.nz_ptr;
     const int R = P.R;
+    const int64_t n_ne = active ? __ldg(P.n_ne_dev) : 1;
 
-    int64_t cur = active ? search_le(nzp, 0, P.n_ne - 1, c0) : 0;
+    int64_t cur = active ? search_le(nzp, 0, n_ne - 1, c0) : 0;
     const int64_t first_cr = cur;
     const bool first_shared = active && __ldg(nzp + cur) < c0;
-    const int64_t last_cr = active ? search_le(nzp, cur, P.n_ne - 1, cend - 1) : 0;
+    const int64_t last_cr = active ? search_le(nzp, cur, n_ne - 1, cend - 1) : 0;
     const bool last_shared = active && __ldg(nzp + last_cr + 1) > cend;
 
     T carry[V];
@@ -89,7 +91,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepParams<T> P) {
         const int64_t lastpos = min(base + NG, cend) - 1;
         int64_t cr;
         if (__ldg(nzp + cur + 1) > lastpos) cr = cur;   // the whole step lies in one row
-        else cr = search_le(nzp, cur, min(cur + NG - 1, P.n_ne - 1), valid ? q : lastpos);
+        else cr = search_le(nzp, cur, min(cur + NG - 1, n_ne - 1), valid ? q : lastpos);
 
         // Tail lanes of the last step read the last valid position and their
         // contribution is dropped, so every lane takes part in the shuffles.
@@ -193,7 +195,8 @@ template <typename T>
 struct TttpParams {
     const int32_t *nz_rows;
     const int64_t *nz_ptr;
-    int64_t n_ne, nnz, chunk;
+    const int64_t *n_ne_dev;
+    int64_t nnz, chunk;
     const int32_t *c1, *c2;
     Weights<T> w;
     const T *A0, *A1, *A2;        // any may be null (mode skipped)
@@ -212,7 +215,8 @@ __global__ void __launch_bounds__(256) tttp_kernel(const TttpParams<T> P) {
     const int64_t cend = min(c0 + P.chunk, P.nnz);
     const int64_t *__restrict__ nzp = P.nz_ptr;
     const int R = P.R;
-    int64_t cur = P.A0 ? search_le(nzp, 0, P.n_ne - 1, c0) : 0;
+    const int64_t n_ne = P.A0 ? __ldg(P.n_ne_dev) : 1;
+    int64_t cur = P.A0 ? search_le(nzp, 0, n_ne - 1, c0) : 0;
 
     for (int64_t base = c0; base < cend; base += NG) {
         const int64_t q = base + g;
@@ -224,7 +228,7 @@ __global__ void __launch_bounds__(256) tttp_kernel(const TttpParams<T> P) {
         if (P.A0) {
             int64_t cr;
             if (__ldg(nzp + cur + 1) > lastpos) cr = cur;
-            else cr = search_le(nzp, cur, min(cur + NG - 1, P.n_ne - 1), valid ? q : lastpos);
+            else cr = search_le(nzp, cur, min(cur + NG - 1, n_ne - 1), valid ? q : lastpos);
             if (valid) {
                 T a[V];
                 load_slice<T, V, VEC>(a, P.A0, __ldg(P.nz_rows + cr), R, lg);
@@ -354,7 +358,7 @@ static SweepParams<T> base_params(const tc_pattern *p, int mode, int R) {
     SweepParams<T> P{};
     P.nz_rows = md.nz_rows;
     P.nz_ptr = md.nz_ptr;
-    P.n_ne = md.n_ne;
+    P.n_ne_dev = md.n_ne_dev;
     P.nnz = p->nnz;
     P.c1 = md.cols[0];
     P.c2 = md.cols[1];
@@ -392,7 +396,7 @@ static tc_status tttp_t(const tc_pattern *p, tc_weights w, const void *s, int R,
     TttpParams<T> P{};
     P.nz_rows = md.nz_rows;
     P.nz_ptr = md.nz_ptr;
-    P.n_ne = md.n_ne;
+    P.n_ne_dev = md.n_ne_dev;
     P.nnz = p->nnz;
     P.c1 = md.cols[0];
     P.c2 = md.cols[1];

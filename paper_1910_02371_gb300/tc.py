@@ -22,6 +22,7 @@ F32, F64 = 0, 1
 LOSSES = {"ls": 0, "poisson_log": 1, "poisson_id": 2}
 W_ONE, W_VALUES, W_ARRAY = 0, 1, 2
 CHECK_DUPLICATES = 1
+REFILLABLE = 2
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is not built: run paper_1910_02371_gb300.build.build()")
@@ -34,6 +35,7 @@ _D = ctypes.c_double
 
 _SIGS = {
     "tc_build_pattern": [_I, _P, _I64, _P, _P, _I, ctypes.c_uint, _P, _P],
+    "tc_pattern_refill": [_P, _P, _P, _P],
     "tc_pattern_destroy": [_P],
     "tc_pattern_view": [_P, _I, _P, _P, _P, _P],
     "tc_pattern_info": [_P, _P, _P, _P, _P],
@@ -155,7 +157,7 @@ def _raw_tensor(ptr: int, nbytes: int):
 
 def build_pattern(idx: Sequence[torch.Tensor], dims: Sequence[int], vals: Optional[torch.Tensor] = None,
                   dtype: torch.dtype = torch.float32, check_duplicates: bool = False,
-                  stream=None) -> Pattern:
+                  refillable: bool = False, stream=None) -> Pattern:
     """tc_build_pattern.  idx: `order` int32 CUDA tensors of length nnz (input
     order); vals: nnz values of `dtype` or None."""
     order = len(idx)
@@ -167,10 +169,17 @@ def build_pattern(idx: Sequence[torch.Tensor], dims: Sequence[int], vals: Option
         raise ValueError("vals must be contiguous, of the pattern dtype and length nnz")
     dims_arr = (ctypes.c_int64 * order)(*[int(d) for d in dims])
     out = ctypes.c_void_p()
+    flags = (CHECK_DUPLICATES if check_duplicates else 0) | (REFILLABLE if refillable else 0)
     _check(_lib.tc_build_pattern(order, dims_arr, nnz, _ptrs(idx), _ptr(vals), _dtype_code(dtype),
-                                 CHECK_DUPLICATES if check_duplicates else 0, _stream(stream),
-                                 ctypes.byref(out)), "tc_build_pattern")
+                                 flags, _stream(stream), ctypes.byref(out)), "tc_build_pattern")
     return Pattern(out.value, dims, nnz, dtype, idx[0].device)
+
+
+def refill_pattern(p: Pattern, idx: Sequence[torch.Tensor], vals: Optional[torch.Tensor] = None,
+                   stream=None):
+    """tc_pattern_refill: rebuild p in place from a same-shape tensor (async)."""
+    _check(_lib.tc_pattern_refill(p.handle, _ptrs(idx), _ptr(vals), _stream(stream)),
+           "tc_pattern_refill")
 
 
 def last_error(p: Pattern, stream=None) -> int:

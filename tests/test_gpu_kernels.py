@@ -334,11 +334,13 @@ def test_cg_solve(tc, name, precond):
     rz = torch.zeros(11, dtype=torch.float64, device="cuda")
     bd = [to_dev(v, prob.dtype) for v in b]
     dx = cg.solve(bd, 10, rz=rz)
-    dx2 = cg.solve(bd, 10, rz=rz)               # graph replay gives the same answer
+    first = [host(v).copy() for v in dx]
+    dx2 = cg.solve(bd, 10, dx=dx, rz=rz)        # replay of the captured graph
     xo = oracle.pcg(prob.dims, prob.idx, prob.t, prob.factors, "ls", lam, b, 10, precond)
     for d in range(3):
-        assert rel(host(dx[d]), xo[d]) <= CG_TOL[prob.dtype]
-        assert torch.equal(dx[d], dx2[d])
+        assert rel(first[d], xo[d]) <= CG_TOL[prob.dtype]
+        # FP64 atomics make the summation order (not the result) vary run to run
+        assert rel(host(dx2[d]), first[d]) <= CG_TOL[prob.dtype]
     assert (rz.cpu().numpy() >= 0).all()
     assert tc.last_error(p) == tc.OK
 
@@ -392,3 +394,62 @@ def test_als_sweep(tc, name):
     for d in range(3):
         assert rel(host(A[d]), ref[d]) <= tol
     assert tc.last_error(p) == tc.OK
+
+
+# ------------------------------------------------------------------ refill
+def test_pattern_refill(tc):
+    import torch
+    a = problem("f32_r16")
+    b = make_problem("refill_b", a.dims, a.nnz, a.R, "f32", seed=4242)
+    p = tc.build_pattern(idx_dev(a.idx), a.dims, to_dev(a.t, "f32"), refillable=True)
+    A = dev_factors(b)
+    x_before = tc.tttp(p, A, weights="values").clone()
+    tc.refill_pattern(p, idx_dev(b.idx), to_dev(b.t, "f32"))
+    for d in range(3):
+        row_ptr, perm, nz = p.view(d)
+        operm, orow, onz = oracle.pattern(b.dims, b.idx, d)
+        assert np.array_equal(perm.cpu().numpy(), operm)
+        assert np.array_equal(row_ptr.cpu().numpy(), orow)
+        assert np.array_equal(nz.cpu().numpy(), onz)
+    perm0 = oracle.pattern(b.dims, b.idx, 0)[0]
+    x = host(tc.tttp(p, A, weights="values"))
+    assert rel(x, oracle.tttp(b.dims, b.idx, b.t, b.factors)[perm0]) <= TOL["f32"]
+    assert not np.allclose(x, host(x_before))
+    out = host(tc.mttkrp(p, A, 2))
+    assert rel(out, oracle.mttkrp(b.dims, b.idx, b.t, b.factors, 2)) <= TOL["f32"]
+    assert tc.last_error(p) == tc.OK
+    # a pattern built without the flag cannot be refilled
+    q = build(a)
+    with pytest.raises(tc.TcError):
+        tc.refill_pattern(q, idx_dev(b.idx), to_dev(b.t, "f32"))
+    torch.cuda.synchronize()
+
+
+def test_pattern_refill_range_error_is_recorded(tc):
+    a = problem("f32_r5")
+    p = tc.build_pattern(idx_dev(a.idx), a.dims, to_dev(a.t, "f32"), refillable=True)
+    bad = [c.copy() for c in a.idx]
+    bad[1][17] = a.dims[1] + 3          # one index past its mode
+    tc.refill_pattern(p, idx_dev(bad), to_dev(a.t, "f32"))
+    assert tc.last_error(p) == tc.ERR_RANGE
+    tc.refill_pattern(p, idx_dev(a.idx), to_dev(a.t, "f32"))
+    assert tc.last_error(p) == tc.OK
+
+
+def test_refill_keeps_captured_cg_graph_valid(tc):
+    a = problem("f64_r16")
+    b = make_problem("refill_cg", a.dims, a.nnz, a.R, "f64", seed=515)
+    p = tc.build_pattern(idx_dev(a.idx), a.dims, to_dev(a.t, "f64"), refillable=True)
+    A = dev_factors(b)
+    lam = 0.05
+    cg = tc.CG(p, A, "ls", lam)
+    _, g = oracle.loss_grad(b.dims, b.idx, b.t, b.factors, "ls", lam)
+    bd = [to_dev(-v, "f64") for v in g]
+    cg.setup()
+    dx = cg.solve(bd, 6)                    # captured against the first tensor
+    tc.refill_pattern(p, idx_dev(b.idx), to_dev(b.t, "f64"))
+    cg.setup()
+    dx = cg.solve(bd, 6, dx=dx)             # replayed against the refilled one
+    xo = oracle.pcg(b.dims, b.idx, b.t, b.factors, "ls", lam, [-v for v in g], 6)
+    for d in range(3):
+        assert rel(host(dx[d]), xo[d]) <= CG_TOL["f64"]
