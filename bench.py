@@ -157,6 +157,8 @@ def run_ours(args):
     from paper_1910_02371_gb300 import drivers, tc
 
     w = synth.WORKLOADS[args.workload]
+    if args.nnz:
+        w = synth.scaled(w, args.nnz)
     # independent replicas: each rank its own seeded batch of the same shape
     seed, idx_h, planted_h, start_h = make_inputs(w, seed_offset=rank)
     m = w.nnz
@@ -222,6 +224,14 @@ def run_ours(args):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         total_ms = tt.item()
     value = world * m * args.steps / (total_ms / 1e3)
+    if args.quick:      # timed steps only (for profiler runs)
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": "nnz/s",
+                              "ms_per_step": total_ms / args.steps, "gpu_launches": int(launches),
+                              "config": {"workload": w.name, "nnz": w.nnz}}), flush=True)
+        if world > 1:
+            dist.destroy_process_group()
+        return
 
     # ---- per-kernel breakdown (same inputs, events around each call)
     def timed(fn, reps=5):
@@ -461,6 +471,10 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true",
+                    help="setup, warm-up and the timed steps only (for profiler runs)")
+    ap.add_argument("--nnz", type=int, default=0,
+                    help="use the first NNZ coordinates of the workload (smaller profiling case)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

@@ -11,17 +11,21 @@ namespace tc {
 // device scalars of one solve
 enum { S_RZ = 0, S_PAP = 1, S_RZNEW = 2, S_STOP = 3, S_COUNT = 8 };
 
-// mode == 0: z = P^-1 r and scal[acc] += r.z  (start of the iteration)
+// mode == 0: z = P^-1 r and scal[acc] += r.z   (scal may be null: no dot)
 // mode == 1: alpha = rz / pAp; x += alpha p; r -= alpha Ap; z = P^-1 r; scal[acc] += r.z
-// One warp per row (grid-stride); chol == null means P = I.
-template <typename T>
+// P^-1 is the stored per-row inverse of the diagonal block (pinv, I x R x R);
+// pinv == null means P = I.  LR lanes own one row (LR a power of two >= R/2,
+// at most 32), each lane one or two of its entries; a warp takes 32/LR rows
+// at a time.
+template <typename T, int LR>
 __global__ void __launch_bounds__(256) cg_update_kernel(int mode, int64_t I, int R,
-                                                        const double *__restrict__ chol, T *x, T *r,
+                                                        const T *__restrict__ pinv, T *x, T *r,
                                                         const T *__restrict__ p,
                                                         const T *__restrict__ Ap, T *z,
                                                         double *scal, int acc, int *status) {
-    __shared__ double sb[8][TC_MAX_RANK];
+    constexpr int RPW = 32 / LR;           // rows per warp
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int l = lane % LR, slot = lane / LR, base_lane = slot * LR;
     double alpha = 0.0;
     if (mode == 1) {
         const double rz = scal[S_RZ], pap = scal[S_PAP];
@@ -35,45 +39,52 @@ __global__ void __launch_bounds__(256) cg_update_kernel(int mode, int64_t I, int
         }
     }
     double dot = 0.0;
-    double *bv = sb[wib];
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib; i < I; i += nwarps) {
-        const int64_t off = i * (int64_t)R;
-        for (int q = lane; q < R; q += 32) {
-            T rv = r[off + q];
+    const int64_t groups = (I + RPW - 1) / RPW;
+    for (int64_t gi = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib; gi < groups; gi += nwarps) {
+        const int64_t i = gi * RPW + slot;
+        const bool row_ok = i < I;
+        const int64_t off = (row_ok ? i : 0) * (int64_t)R;
+        // this lane's entries e0 = l and e1 = l + LR of the row
+        const int e0 = l, e1 = l + LR;
+        T r0 = T(0), r1 = T(0);
+        if (row_ok && e0 < R) {
+            r0 = r[off + e0];
             if (mode == 1) {
-                x[off + q] = (T)((double)x[off + q] + alpha * (double)p[off + q]);
-                rv = (T)((double)rv - alpha * (double)Ap[off + q]);
-                r[off + q] = rv;
-            }
-            bv[q] = (double)rv;
-        }
-        __syncwarp();
-        if (chol) {
-            const double *Lo = chol + i * (int64_t)R * R;
-            for (int j = 0; j < R; ++j) {
-                const double yj = bv[j] / Lo[j * R + j];
-                __syncwarp();
-                for (int q = j + 1 + lane; q < R; q += 32) bv[q] -= Lo[q * R + j] * yj;
-                if (lane == 0) bv[j] = yj;
-                __syncwarp();
-            }
-            for (int j = R - 1; j >= 0; --j) {
-                const double xj = bv[j] / Lo[j * R + j];
-                __syncwarp();
-                for (int q = lane; q < j; q += 32) bv[q] -= Lo[j * R + q] * xj;
-                if (lane == 0) bv[j] = xj;
-                __syncwarp();
+                x[off + e0] = (T)((double)x[off + e0] + alpha * (double)p[off + e0]);
+                r0 = (T)((double)r0 - alpha * (double)Ap[off + e0]);
+                r[off + e0] = r0;
             }
         }
-        for (int q = lane; q < R; q += 32) {
-            const T zv = (T)bv[q];
-            z[off + q] = zv;
-            dot += (double)r[off + q] * (double)zv;
+        if (row_ok && e1 < R) {
+            r1 = r[off + e1];
+            if (mode == 1) {
+                x[off + e1] = (T)((double)x[off + e1] + alpha * (double)p[off + e1]);
+                r1 = (T)((double)r1 - alpha * (double)Ap[off + e1]);
+                r[off + e1] = r1;
+            }
         }
-        __syncwarp();
+        T z0 = r0, z1 = r1;
+        if (pinv) {
+            const T *Pi = pinv + (row_ok ? i : 0) * (int64_t)R * R;
+            z0 = T(0);
+            z1 = T(0);
+            for (int c = 0; c < R; ++c) {
+                const T rc = __shfl_sync(0xffffffffu, c < LR ? r0 : r1, base_lane + (c % LR));
+                if (row_ok && e0 < R) z0 += Pi[e0 * R + c] * rc;
+                if (row_ok && e1 < R) z1 += Pi[e1 * R + c] * rc;
+            }
+        }
+        if (row_ok && e0 < R) {
+            z[off + e0] = z0;
+            dot += (double)r0 * (double)z0;
+        }
+        if (row_ok && e1 < R) {
+            z[off + e1] = z1;
+            dot += (double)r1 * (double)z1;
+        }
     }
-    block_add(dot, scal + acc);
+    if (scal) block_add(dot, scal + acc);
 }
 
 // p = z + beta p with beta = rz_new / rz
@@ -124,7 +135,7 @@ struct tc_cg {
     void *A[TC_ORDER] = {nullptr, nullptr, nullptr};
     double lambda = 0.0;
     int precond = 1;
-    double *chol[TC_ORDER] = {nullptr, nullptr, nullptr};
+    void *pinv[TC_ORDER] = {nullptr, nullptr, nullptr};
     void *r[TC_ORDER] = {}, *z[TC_ORDER] = {}, *pv[TC_ORDER] = {}, *Ap[TC_ORDER] = {};
     void *grad[TC_ORDER] = {}, *dx[TC_ORDER] = {};
     double *scal = nullptr;
@@ -147,19 +158,39 @@ static int sms() {
     return n > 0 ? n : 1;
 }
 
+template <typename T, int LR>
+static void launch_update_lr(int mode, int64_t I, int R, const void *pinv, void *x, void *r,
+                             const void *p, const void *Ap, void *z, double *scal, int acc,
+                             int *status, cudaStream_t st) {
+    constexpr int RPW = 32 / LR;
+    const int64_t groups = (I + RPW - 1) / RPW;
+    int64_t blocks = (groups + 7) / 8;
+    if (blocks > 4LL * sms()) blocks = 4LL * sms();
+    if (blocks < 1) blocks = 1;
+    cg_update_kernel<T, LR><<<(unsigned)blocks, 256, 0, st>>>(
+        mode, I, R, (const T *)pinv, (T *)x, (T *)r, (const T *)p, (const T *)Ap, (T *)z, scal, acc,
+        status);
+    count_launch();
+}
+
+template <typename T>
+static void launch_update(int mode, int64_t I, int R, const void *pinv, void *x, void *r,
+                          const void *p, const void *Ap, void *z, double *scal, int acc,
+                          int *status, cudaStream_t st) {
+    if (R <= 2) launch_update_lr<T, 1>(mode, I, R, pinv, x, r, p, Ap, z, scal, acc, status, st);
+    else if (R <= 4) launch_update_lr<T, 2>(mode, I, R, pinv, x, r, p, Ap, z, scal, acc, status, st);
+    else if (R <= 8) launch_update_lr<T, 4>(mode, I, R, pinv, x, r, p, Ap, z, scal, acc, status, st);
+    else if (R <= 16) launch_update_lr<T, 8>(mode, I, R, pinv, x, r, p, Ap, z, scal, acc, status, st);
+    else if (R <= 32) launch_update_lr<T, 16>(mode, I, R, pinv, x, r, p, Ap, z, scal, acc, status, st);
+    else launch_update_lr<T, 32>(mode, I, R, pinv, x, r, p, Ap, z, scal, acc, status, st);
+}
+
 template <typename T>
 static void enqueue_update(tc_cg *cg, int mode, int acc, cudaStream_t st) {
     const tc_pattern *p = cg->p;
-    for (int d = 0; d < TC_ORDER; ++d) {
-        const int64_t I = p->dims[d];
-        int64_t blocks = (I + 7) / 8;
-        if (blocks > 4LL * sms()) blocks = 4LL * sms();
-        if (blocks < 1) blocks = 1;
-        cg_update_kernel<T><<<(unsigned)blocks, 256, 0, st>>>(
-            mode, I, cg->R, cg->precond ? cg->chol[d] : nullptr, (T *)cg->dx[d], (T *)cg->r[d],
-            (const T *)cg->pv[d], (const T *)cg->Ap[d], (T *)cg->z[d], cg->scal, acc, p->status);
-        count_launch();
-    }
+    for (int d = 0; d < TC_ORDER; ++d)
+        launch_update<T>(mode, p->dims[d], cg->R, cg->precond ? cg->pinv[d] : nullptr, cg->dx[d],
+                         cg->r[d], cg->pv[d], cg->Ap[d], cg->z[d], cg->scal, acc, p->status, st);
 }
 
 template <typename T>
@@ -214,7 +245,7 @@ static tc_status enqueue_solve(tc_cg *cg, const void *const *b, void *const *dx,
 static void free_cg(tc_cg *cg) {
     if (!cg) return;
     for (int d = 0; d < TC_ORDER; ++d) {
-        cudaFree(cg->chol[d]);
+        cudaFree(cg->pinv[d]);
         cudaFree(cg->r[d]);
         cudaFree(cg->z[d]);
         cudaFree(cg->pv[d]);
@@ -260,8 +291,7 @@ tc_status tc_cg_create(const tc_pattern *p, tc_loss loss, int R, const void *con
         ok = ok && cudaMalloc(&cg->grad[d], bytes) == cudaSuccess;
         ok = ok && cudaMalloc(&cg->dx[d], bytes) == cudaSuccess;
         if (cg->precond)
-            ok = ok && cudaMalloc((void **)&cg->chol[d], sizeof(double) * p->dims[d] * R * R) ==
-                           cudaSuccess;
+            ok = ok && cudaMalloc(&cg->pinv[d], es * p->dims[d] * R * R) == cudaSuccess;
     }
     ok = ok && cudaMalloc((void **)&cg->scal, sizeof(double) * S_COUNT) == cudaSuccess;
     ok = ok && cudaStreamCreateWithFlags(&cg->own, cudaStreamNonBlocking) == cudaSuccess;
@@ -289,7 +319,7 @@ tc_status tc_cg_setup(tc_cg *cg, tc_stream_t stream) {
         tc_status rc = launch_solve_factor(cg->p, TC_W_ONE, nullptr, cg->R,
                                            (const void *const *)cg->A, d, nullptr,
                                            2.0 * cg->lambda, nullptr, nullptr, 1, cg->loss,
-                                           cg->chol[d], (cudaStream_t)stream);
+                                           cg->pinv[d], (cudaStream_t)stream);
         if (rc != TC_OK) return rc;
     }
     return cudaGetLastError() == cudaSuccess ? TC_OK : TC_ERR_CUDA;
@@ -298,17 +328,16 @@ tc_status tc_cg_setup(tc_cg *cg, tc_stream_t stream) {
 tc_status tc_cg_precond_apply(tc_cg *cg, const void *const *r, void *const *z,
                               tc_stream_t stream) {
     if (!cg || !r || !z) return TC_ERR_ARG;
-    const size_t es = tsize(cg->p->dtype);
+    const tc_pattern *p = cg->p;
     for (int d = 0; d < TC_ORDER; ++d) {
         if (!r[d] || !z[d]) return TC_ERR_ARG;
-        if (cg->precond) {
-            tc_status rc = launch_chol_apply(cg->p, cg->R, d, cg->chol[d], r[d], z[d],
-                                             (cudaStream_t)stream);
-            if (rc != TC_OK) return rc;
-        } else if (r[d] != z[d]) {
-            TC_CUDA(cudaMemcpyAsync(z[d], r[d], (size_t)cg->p->dims[d] * cg->R * es,
-                                    cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
-        }
+        const void *pinv = cg->precond ? cg->pinv[d] : nullptr;
+        if (p->dtype == TC_F64)
+            launch_update<double>(0, p->dims[d], cg->R, pinv, nullptr, const_cast<void *>(r[d]),
+                                  nullptr, nullptr, z[d], nullptr, 0, p->status, (cudaStream_t)stream);
+        else
+            launch_update<float>(0, p->dims[d], cg->R, pinv, nullptr, const_cast<void *>(r[d]),
+                                 nullptr, nullptr, z[d], nullptr, 0, p->status, (cudaStream_t)stream);
     }
     return cudaGetLastError() == cudaSuccess ? TC_OK : TC_ERR_CUDA;
 }

@@ -105,14 +105,13 @@ tc_status launch_loss_grad(const tc_pattern *p, tc_loss loss, int R, const void 
 tc_status launch_ggn_matvec(const tc_pattern *p, tc_loss loss, int R, const void *const *A,
                             const void *const *x, double lambda, void *const *y,
                             double *dot_out, cudaStream_t st);
-// Gram + Cholesky per row.  If chol_out != null the (lower) Cholesky factors are
-// stored (FP64, I_d x R x R) instead of solving.
+// Gram + FP64 Cholesky per row.  If pinv_out != null the inverse of each row
+// system, (G_i + lambda I)^-1, is formed in FP64 from the factor and stored
+// (pattern dtype, I_d x R x R) instead of solving.
 tc_status launch_solve_factor(const tc_pattern *p, tc_weights w, const void *s, int R,
                               const void *const *A, int mode, const void *rhs, double lambda,
                               void *out, int8_t *row_status, int use_loss_d2, tc_loss loss,
-                              double *chol_out, cudaStream_t st);
-tc_status launch_chol_apply(const tc_pattern *p, int R, int mode, const double *chol,
-                            const void *r, void *z, cudaStream_t st);
+                              void *pinv_out, cudaStream_t st);
 tc_status build_pattern_impl(int order, const int64_t *dims, int64_t nnz,
                              const int32_t *const *idx, const void *vals, tc_dtype dtype,
                              unsigned flags, cudaStream_t st, tc_pattern **out);
@@ -223,6 +222,26 @@ __device__ __forceinline__ int64_t search_le(const int64_t *__restrict__ a, int6
         else hi = mid - 1;
     }
     return lo;
+}
+
+// The same with 32-bit positions in the array (row counts fit in int32).
+__device__ __forceinline__ int search_le32(const int64_t *__restrict__ a, int lo, int hi,
+                                          int64_t key) {
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(a + mid) <= key) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Sum of v over the NG groups of a warp (lanes with equal lane % G), every
+// lane receiving the total of its own slice.
+template <int G, typename T>
+__device__ __forceinline__ T across_groups(T v) {
+#pragma unroll
+    for (int o = G; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
 }
 
 // Weight s_e of the nonzero at sorted position q of the current traversal.

@@ -25,7 +25,7 @@ struct SolveParams {
     const T *Ad, *A1, *A2;
     const T *rhs;                 // I_d x R (solve mode)
     T *out;                       // I_d x R (solve mode)
-    double *chol;                 // I_d x R x R lower factors (factor mode) or null
+    T *pinv;                      // I_d x R x R inverses (preconditioner mode) or null
     int8_t *row_status;
     double lambda;
     int R;
@@ -44,11 +44,13 @@ struct GramLay {
 template <typename T, int RT>
 struct SolveSmem {
     static constexpr int NG = Lay<T, RT>::NG;
-    // per warp: h buffer, weights, FP64 system, FP64 right-hand side
+    // per warp: h buffer, weights, FP64 system, FP64 right-hand side; the
+    // preconditioner variant also holds the FP64 inverse
     static constexpr size_t h_bytes = sizeof(T) * NG * RT;
     static constexpr size_t w_bytes = sizeof(T) * NG;
     static constexpr size_t s_off = ((h_bytes + w_bytes + 15) / 16) * 16;
     static constexpr size_t per_warp = s_off + sizeof(double) * (RT * RT + RT);
+    static constexpr size_t per_warp_inv = per_warp + sizeof(double) * RT * RT;
 };
 
 template <typename T, int RT, bool VEC>
@@ -63,7 +65,7 @@ __global__ void solve_kernel(const SolveParams<T> P) {
     const int wib = threadIdx.x >> 5;
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (i >= P.I) return;
-    unsigned char *wbase = smem_raw + (size_t)wib * SM::per_warp;
+    unsigned char *wbase = smem_raw + (size_t)wib * (P.pinv ? SM::per_warp_inv : SM::per_warp);
     T *hs = reinterpret_cast<T *>(wbase);
     T *ws = hs + NG * RT;
     double *S = reinterpret_cast<double *>(wbase + SM::s_off);
@@ -133,7 +135,7 @@ __global__ void solve_kernel(const SolveParams<T> P) {
     __syncwarp();
     for (int r = lane; r < R; r += 32) {
         S[r * RT + r] += P.lambda;
-        if (!P.chol) bv[r] = (double)P.rhs[i * (int64_t)R + r];
+        if (!P.pinv) bv[r] = (double)P.rhs[i * (int64_t)R + r];
     }
     __syncwarp();
 
@@ -162,20 +164,32 @@ __global__ void solve_kernel(const SolveParams<T> P) {
             record_error(P.status, TC_ERR_NOT_SPD);
             if (P.row_status) P.row_status[i] = 1;
         }
-        if (P.chol) {  // an identity factor keeps the preconditioner defined
-            double *Lo = P.chol + i * (int64_t)R * R;
-            for (int q = lane; q < R * R; q += 32) Lo[q] = (q / R == q % R) ? 1.0 : 0.0;
+        if (P.pinv) {  // an identity block keeps the preconditioner defined
+            T *Po = P.pinv + i * (int64_t)R * R;
+            for (int q = lane; q < R * R; q += 32) Po[q] = (q / R == q % R) ? T(1) : T(0);
         }
         return;
     }
     if (lane == 0 && P.row_status) P.row_status[i] = 0;
 
-    if (P.chol) {
-        double *Lo = P.chol + i * (int64_t)R * R;
-        for (int q = lane; q < R * R; q += 32) {
-            const int r = q / R, c = q % R;
-            Lo[q] = c <= r ? S[r * RT + c] : 0.0;
+    if (P.pinv) {
+        // (L L^T)^-1 column by column in FP64: lane c solves L L^T y = e_c
+        double *Y = bv + RT;
+        for (int c = lane; c < R; c += 32) {
+            for (int r = 0; r < R; ++r) {
+                double v = (r == c) ? 1.0 : 0.0;
+                for (int k = c; k < r; ++k) v -= S[r * RT + k] * Y[k * RT + c];
+                Y[r * RT + c] = r < c ? 0.0 : v / S[r * RT + r];
+            }
+            for (int r = R - 1; r >= 0; --r) {
+                double v = Y[r * RT + c];
+                for (int k = r + 1; k < R; ++k) v -= S[k * RT + r] * Y[k * RT + c];
+                Y[r * RT + c] = v / S[r * RT + r];
+            }
         }
+        __syncwarp();
+        T *Po = P.pinv + i * (int64_t)R * R;
+        for (int q = lane; q < R * R; q += 32) Po[q] = (T)Y[(q / R) * RT + q % R];
         return;
     }
     // L y = b, then L^T x = y
@@ -196,40 +210,11 @@ __global__ void solve_kernel(const SolveParams<T> P) {
     for (int r = lane; r < R; r += 32) P.out[i * (int64_t)R + r] = (T)bv[r];
 }
 
-// z_i = (L_i L_i^T)^-1 r_i with the stored FP64 factors; one warp per row.
-template <typename T>
-__global__ void chol_apply_kernel(const double *__restrict__ chol, const T *__restrict__ r,
-                                  T *__restrict__ z, int64_t I, int R) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (i >= I) return;
-    double *bv = reinterpret_cast<double *>(smem_raw) + wib * TC_MAX_RANK;
-    const double *Lo = chol + i * (int64_t)R * R;
-    for (int q = lane; q < R; q += 32) bv[q] = (double)r[i * (int64_t)R + q];
-    __syncwarp();
-    for (int j = 0; j < R; ++j) {
-        const double yj = bv[j] / Lo[j * R + j];
-        __syncwarp();
-        for (int q = j + 1 + lane; q < R; q += 32) bv[q] -= Lo[q * R + j] * yj;
-        if (lane == 0) bv[j] = yj;
-        __syncwarp();
-    }
-    for (int j = R - 1; j >= 0; --j) {
-        const double xj = bv[j] / Lo[j * R + j];
-        __syncwarp();
-        for (int q = lane; q < j; q += 32) bv[q] -= Lo[j * R + q] * xj;
-        if (lane == 0) bv[j] = xj;
-        __syncwarp();
-    }
-    for (int q = lane; q < R; q += 32) z[i * (int64_t)R + q] = (T)bv[q];
-}
-
 template <typename T, int RT, bool VEC>
 static tc_status launch_solve_rt(const SolveParams<T> &P, cudaStream_t st) {
     using SM = SolveSmem<T, RT>;
     const int warps = RT >= 64 ? 2 : 4;
-    const size_t smem = SM::per_warp * warps;
+    const size_t smem = (P.pinv ? SM::per_warp_inv : SM::per_warp) * warps;
     auto kern = solve_kernel<T, RT, VEC>;
     if (smem > 48 * 1024) TC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                        (int)smem));
@@ -242,7 +227,7 @@ static tc_status launch_solve_rt(const SolveParams<T> &P, cudaStream_t st) {
 template <typename T>
 static tc_status solve_t(const tc_pattern *p, tc_weights w, const void *s, int R,
                          const void *const *A, int mode, const void *rhs, double lambda,
-                         void *out, int8_t *row_status, int use_d2, tc_loss loss, double *chol,
+                         void *out, int8_t *row_status, int use_d2, tc_loss loss, void *pinv,
                          cudaStream_t st) {
     const ModeData &md = p->md[mode];
     int o1, o2;
@@ -260,7 +245,7 @@ static tc_status solve_t(const tc_pattern *p, tc_weights w, const void *s, int R
     P.A2 = (const T *)A[o2];
     P.rhs = (const T *)rhs;
     P.out = (T *)out;
-    P.chol = chol;
+    P.pinv = (T *)pinv;
     P.row_status = row_status;
     P.lambda = lambda;
     P.R = R;
@@ -289,28 +274,12 @@ static tc_status solve_t(const tc_pattern *p, tc_weights w, const void *s, int R
 tc_status launch_solve_factor(const tc_pattern *p, tc_weights w, const void *s, int R,
                               const void *const *A, int mode, const void *rhs, double lambda,
                               void *out, int8_t *row_status, int use_loss_d2, tc_loss loss,
-                              double *chol_out, cudaStream_t st) {
+                              void *pinv_out, cudaStream_t st) {
     if (p->dtype == TC_F64)
         return solve_t<double>(p, w, s, R, A, mode, rhs, lambda, out, row_status, use_loss_d2,
-                               loss, chol_out, st);
+                               loss, pinv_out, st);
     return solve_t<float>(p, w, s, R, A, mode, rhs, lambda, out, row_status, use_loss_d2, loss,
-                          chol_out, st);
-}
-
-tc_status launch_chol_apply(const tc_pattern *p, int R, int mode, const double *chol,
-                            const void *r, void *z, cudaStream_t st) {
-    const int64_t I = p->dims[mode];
-    const int warps = 4;
-    const int64_t blocks = (I + warps - 1) / warps;
-    const size_t smem = sizeof(double) * TC_MAX_RANK * warps;
-    if (p->dtype == TC_F64)
-        chol_apply_kernel<double><<<(unsigned)blocks, warps * 32, smem, st>>>(
-            chol, (const double *)r, (double *)z, I, R);
-    else
-        chol_apply_kernel<float><<<(unsigned)blocks, warps * 32, smem, st>>>(
-            chol, (const float *)r, (float *)z, I, R);
-    count_launch();
-    return TC_OK;
+                          pinv_out, st);
 }
 
 }  // namespace tc

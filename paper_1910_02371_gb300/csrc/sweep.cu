@@ -36,11 +36,85 @@ struct SweepParams {
     int *status;
 };
 
+// Per-step inputs of one nonzero group, loaded one step ahead.
+template <typename T>
+struct StepIn {
+    int32_t j, k;
+    T t, s;
+};
+
+template <typename T, int OP>
+__device__ __forceinline__ StepIn<T> load_step(const SweepParams<T> &P, int64_t qq) {
+    StepIn<T> in;
+    in.j = __ldcs(P.c1 + qq);
+    in.k = __ldcs(P.c2 + qq);
+    if constexpr (OP == OP_MTTKRP) {
+        in.s = weight_at(P.w, qq);
+        in.t = T(0);
+    } else {
+        in.s = T(0);
+        in.t = (OP == OP_GGN && P.loss == TC_LOSS_LS) ? T(0) : __ldcs(P.t + qq);
+    }
+    return in;
+}
+
+// Contribution of one nonzero to its row of the output (one lane's V entries).
+// a / xa: this mode's factor / direction rows of the nonzero's row.
+template <typename T, int V, int G, bool VEC, int OP>
+__device__ __forceinline__ void contribution(const SweepParams<T> &P, const StepIn<T> &in,
+                                             const T (&a)[V], const T (&xa)[V], int lg, bool valid,
+                                             T (&c)[V], double &lacc, bool &dom_ok) {
+    const int R = P.R;
+    T b[V], e[V];
+    load_slice<T, V, VEC>(b, P.A1, in.j, R, lg);
+    load_slice<T, V, VEC>(e, P.A2, in.k, R, lg);
+    if constexpr (OP == OP_MTTKRP) {
+#pragma unroll
+        for (int t = 0; t < V; ++t) c[t] = in.s * b[t] * e[t];
+    } else if constexpr (OP == OP_GRAD) {
+        T part = T(0);
+#pragma unroll
+        for (int t = 0; t < V; ++t) part += a[t] * b[t] * e[t];
+        const T m = group_sum<G>(part);
+        T phi, d1, d2;
+        loss_terms(P.loss, in.t, m, phi, d1, d2, dom_ok);
+#pragma unroll
+        for (int t = 0; t < V; ++t) c[t] = d1 * b[t] * e[t];
+        if (lg == 0 && valid) lacc += (double)phi;
+    } else {
+        T xb[V], xc[V];
+        load_slice<T, V, VEC>(xb, P.X1, in.j, R, lg);
+        load_slice<T, V, VEC>(xc, P.X2, in.k, R, lg);
+        T zp = T(0), part = T(0);
+#pragma unroll
+        for (int t = 0; t < V; ++t) {
+            const T be = b[t] * e[t];
+            zp += xa[t] * be + a[t] * (xb[t] * e[t] + b[t] * xc[t]);
+            part += a[t] * be;
+        }
+        const T z = group_sum<G>(zp);
+        T d2 = T(2);
+        if (P.loss != TC_LOSS_LS) {
+            const T m = group_sum<G>(part);
+            T phi, d1;
+            loss_terms(P.loss, in.t, m, phi, d1, d2, dom_ok);
+        }
+        const T wz = d2 * z;
+#pragma unroll
+        for (int t = 0; t < V; ++t) c[t] = wz * b[t] * e[t];
+    }
+    if (!valid) {
+#pragma unroll
+        for (int t = 0; t < V; ++t) c[t] = T(0);
+    }
+}
+
 template <typename T, int RT, bool VEC, int OP>
 __global__ void __launch_bounds__(256) sweep_kernel(const SweepParams<T> P) {
     using L = Lay<T, RT>;
     constexpr int V = L::V, G = L::G, NG = L::NG;
     constexpr unsigned FULL = 0xffffffffu;
+    constexpr bool OWN = OP != OP_MTTKRP;     // needs this mode's own factor row
     const int lane = threadIdx.x & 31, g = lane / G, lg = lane % G;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t c0 = warp * P.chunk;
@@ -48,22 +122,23 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepParams<T> P) {
     const int64_t cend = active ? min(c0 + P.chunk, P.nnz) : c0;
     const int64_t *__restrict__ nzp = P.nz_ptr;
     const int R = P.R;
-    const int64_t n_ne = active ? __ldg(P.n_ne_dev) : 1;
+    const int n_ne = active ? (int)__ldg(P.n_ne_dev) : 1;
 
-    int64_t cur = active ? search_le(nzp, 0, n_ne - 1, c0) : 0;
-    const int64_t first_cr = cur;
+    int cur = active ? search_le32(nzp, 0, n_ne - 1, c0) : 0;
+    const int first_cr = cur;
     const bool first_shared = active && __ldg(nzp + cur) < c0;
-    const int64_t last_cr = active ? search_le(nzp, cur, n_ne - 1, cend - 1) : 0;
+    const int last_cr = active ? search_le32(nzp, cur, n_ne - 1, cend - 1) : 0;
     const bool last_shared = active && __ldg(nzp + last_cr + 1) > cend;
+    int64_t row_end = active ? __ldg(nzp + cur + 1) : 0;
 
-    T carry[V];
+    T acc[V], a[V], xa[V];
 #pragma unroll
-    for (int t = 0; t < V; ++t) carry[t] = T(0);
-    int64_t carry_cr = -1;
+    for (int t = 0; t < V; ++t) acc[t] = a[t] = xa[t] = T(0);
+    int own_cr = -1;
     double lacc = 0.0, dacc = 0.0;
     bool dom_ok = true;
 
-    auto flush = [&](int64_t cr, const T(&v)[V]) {
+    auto flush = [&](int cr, const T(&v)[V]) {
         if (!P.out) return;
         const int64_t row = __ldg(P.nz_rows + cr);
         if ((cr == first_cr && first_shared) || (cr == last_cr && last_shared)) {
@@ -84,81 +159,63 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepParams<T> P) {
             for (int t = 0; t < V; ++t) dacc += (double)dw[t] * (double)v[t];
         }
     };
+    auto load_own = [&](int cr) {
+        const int64_t row = __ldg(P.nz_rows + cr);
+        load_slice<T, V, VEC>(a, P.Ad, row, R, lg);
+        if constexpr (OP == OP_GGN) load_slice<T, V, VEC>(xa, P.Xd, row, R, lg);
+    };
 
+    StepIn<T> nxt;
+    if (active) nxt = load_step<T, OP>(P, min(c0 + g, cend - 1));
     for (int64_t base = c0; base < cend; base += NG) {
-        const int64_t q = base + g;
-        const bool valid = q < cend;
+        const StepIn<T> in = nxt;
         const int64_t lastpos = min(base + NG, cend) - 1;
-        int64_t cr;
-        if (__ldg(nzp + cur + 1) > lastpos) cr = cur;   // the whole step lies in one row
-        else cr = search_le(nzp, cur, min(cur + NG - 1, n_ne - 1), valid ? q : lastpos);
-
-        // Tail lanes of the last step read the last valid position and their
-        // contribution is dropped, so every lane takes part in the shuffles.
-        const int64_t qq = valid ? q : lastpos;
+        const bool valid = base + g < cend;
+        if (base + NG < cend) nxt = load_step<T, OP>(P, min(base + NG + g, cend - 1));
         T c[V];
-        {
-            const int32_t j = __ldcs(P.c1 + qq), k = __ldcs(P.c2 + qq);
-            T b[V], e[V];
-            load_slice<T, V, VEC>(b, P.A1, j, R, lg);
-            load_slice<T, V, VEC>(e, P.A2, k, R, lg);
-            if constexpr (OP == OP_MTTKRP) {
-                const T s = weight_at(P.w, qq);
-#pragma unroll
-                for (int t = 0; t < V; ++t) c[t] = s * b[t] * e[t];
-            } else {
-                const int32_t row = __ldg(P.nz_rows + cr);
-                T a[V];
-                load_slice<T, V, VEC>(a, P.Ad, row, R, lg);
-                const T tv = __ldcs(P.t + qq);
-                T part = T(0);
-#pragma unroll
-                for (int t = 0; t < V; ++t) part += a[t] * b[t] * e[t];
-                if constexpr (OP == OP_GRAD) {
-                    const T m = group_sum<G>(part);
-                    T phi, d1, d2;
-                    loss_terms(P.loss, tv, m, phi, d1, d2, dom_ok);
-#pragma unroll
-                    for (int t = 0; t < V; ++t) c[t] = d1 * b[t] * e[t];
-                    if (lg == 0 && valid) lacc += (double)phi;
-                } else {
-                    T xa[V], xb[V], xc[V];
-                    load_slice<T, V, VEC>(xa, P.Xd, row, R, lg);
-                    load_slice<T, V, VEC>(xb, P.X1, j, R, lg);
-                    load_slice<T, V, VEC>(xc, P.X2, k, R, lg);
-                    T zp = T(0);
-#pragma unroll
-                    for (int t = 0; t < V; ++t)
-                        zp += xa[t] * b[t] * e[t] + a[t] * xb[t] * e[t] + a[t] * b[t] * xc[t];
-                    const T z = group_sum<G>(zp);
-                    T d2 = T(2);
-                    if (P.loss != TC_LOSS_LS) {
-                        const T m = group_sum<G>(part);
-                        T phi, d1;
-                        loss_terms(P.loss, tv, m, phi, d1, d2, dom_ok);
-                    }
-                    const T wz = d2 * z;
-#pragma unroll
-                    for (int t = 0; t < V; ++t) c[t] = wz * b[t] * e[t];
+        if (row_end > lastpos) {
+            // fast path: the whole step lies in row `cur`
+            if constexpr (OWN) {
+                if (own_cr != cur) {
+                    load_own(cur);
+                    own_cr = cur;
                 }
             }
-        }
-        if (!valid) {
+            contribution<T, V, G, VEC, OP>(P, in, a, xa, lg, valid, c, lacc, dom_ok);
 #pragma unroll
-            for (int t = 0; t < V; ++t) c[t] = T(0);
+            for (int t = 0; t < V; ++t) acc[t] += c[t];
+            continue;
         }
-        if (!valid) cr = -1;
-
-        // a carried row that does not continue into this step is complete
-        const int64_t cr0 = __shfl_sync(FULL, cr, 0);
-        if (carry_cr >= 0 && carry_cr != cr0) {
-            if (g == 0) flush(carry_cr, carry);
-            carry_cr = -1;
+        // slow path: row boundaries inside this step
+        const int64_t qq = valid ? base + g : lastpos;
+        // `cur` holds position base - 1 or base, so the step spans rows cur .. cur + NG
+        const int cr = search_le32(nzp, cur, min(cur + NG, n_ne - 1), qq);
+        if constexpr (OWN) {
+            load_own(cr);
+            own_cr = cr;
         }
-        // segmented inclusive scan over the NG groups of this step
+        contribution<T, V, G, VEC, OP>(P, in, a, xa, lg, valid, c, lacc, dom_ok);
+        if (cr == cur) {
+#pragma unroll
+            for (int t = 0; t < V; ++t) {
+                acc[t] += c[t];
+                c[t] = T(0);
+            }
+        }
+        // row `cur` ends inside this step: reduce the private partial sums
+        {
+            T tot[V];
+#pragma unroll
+            for (int t = 0; t < V; ++t) tot[t] = across_groups<G>(acc[t]);
+            if (g == 0) flush(cur, tot);
+        }
+        T craw[V];
+#pragma unroll
+        for (int t = 0; t < V; ++t) craw[t] = c[t];
+        // rows after `cur`: segmented inclusive scan over the groups
 #pragma unroll
         for (int d = 1; d < NG; d <<= 1) {
-            const int64_t ocr = __shfl_up_sync(FULL, cr, d * G);
+            const int ocr = __shfl_up_sync(FULL, cr, d * G);
             T o[V];
 #pragma unroll
             for (int t = 0; t < V; ++t) o[t] = __shfl_up_sync(FULL, c[t], d * G);
@@ -167,19 +224,22 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepParams<T> P) {
                 for (int t = 0; t < V; ++t) c[t] += o[t];
             }
         }
-        if (carry_cr >= 0 && cr == carry_cr) {
+        const int ncr = __shfl_down_sync(FULL, cr, G);
+        const int lcr = __shfl_sync(FULL, cr, (NG - 1) * G);
+        const bool tail = (g == NG - 1) || (ncr != cr);
+        if (tail && cr != cur && cr != lcr) flush(cr, c);       // rows wholly inside the step
 #pragma unroll
-            for (int t = 0; t < V; ++t) c[t] += carry[t];
-        }
-        const int64_t ncr = __shfl_down_sync(FULL, cr, G);
-        if (valid && g < NG - 1 && ncr != cr) flush(cr, c);
-        const int64_t lcr = __shfl_sync(FULL, cr, (NG - 1) * G);
-#pragma unroll
-        for (int t = 0; t < V; ++t) carry[t] = __shfl_sync(FULL, c[t], (NG - 1) * G + lg);
-        carry_cr = lcr;
-        if (base + NG < cend) cur = lcr + ((__ldg(nzp + lcr + 1) <= base + NG) ? 1 : 0);
+        for (int t = 0; t < V; ++t) acc[t] = (cr == lcr) ? craw[t] : T(0);
+        cur = lcr;
+        row_end = __ldg(nzp + cur + 1);
+        if constexpr (OWN) own_cr = (own_cr == cur) ? cur : -1;
     }
-    if (carry_cr >= 0 && g == 0) flush(carry_cr, carry);
+    if (active) {
+        T tot[V];
+#pragma unroll
+        for (int t = 0; t < V; ++t) tot[t] = across_groups<G>(acc[t]);
+        if (g == 0) flush(cur, tot);
+    }
 
     if constexpr (OP != OP_MTTKRP) {
         if (!dom_ok) record_error(P.status, TC_ERR_DOMAIN);

@@ -437,9 +437,11 @@ def test_pattern_refill_range_error_is_recorded(tc):
 
 
 def test_refill_keeps_captured_cg_graph_valid(tc):
+    import torch
     a = problem("f64_r16")
     b = make_problem("refill_cg", a.dims, a.nnz, a.R, "f64", seed=515)
-    p = tc.build_pattern(idx_dev(a.idx), a.dims, to_dev(a.t, "f64"), refillable=True)
+    p = tc.build_pattern(idx_dev(a.idx), a.dims, to_dev(a.t, "f64"), dtype=torch.float64,
+                         refillable=True)
     A = dev_factors(b)
     lam = 0.05
     cg = tc.CG(p, A, "ls", lam)
