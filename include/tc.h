@@ -218,6 +218,37 @@ tc_status tc_cg_solve(tc_cg *cg, const void *const *b, void *const *dx, int iter
  * loss_out (device double, may be NULL) receives f before the step. */
 tc_status tc_ggn_step(tc_cg *cg, int iters, double *loss_out, tc_stream_t stream);
 
+/* ------------------------------------------------------------------ allocation-free sort */
+
+/* Largest nnz that tc_sort_mode_noalloc accepts. */
+#define TC_SORT_NOALLOC_MAX_NNZ (1 << 20)
+
+/* The per-mode sort of tc_build_pattern for one index array, without any
+ * device allocation.  The paper has no counterpart: this is a service of the
+ * library for callers that may not call cudaMalloc -- a process that handed all
+ * device memory to another allocator's pool, a server that forbids new
+ * allocations once it is serving so that no request can fail for lack of
+ * memory, or a host thread that must not stall: a device allocation can make
+ * the CUDA runtime synchronize work across streams.
+ *   key      device int32[nnz]: mode indices in input order.
+ *   I        the mode's dimension, 1 <= I <= 2^31 - 1.
+ *   perm     device int64[nnz] output: sorted position -> input position,
+ *            equal keys in input order (the same as tc_pattern_view's perm).
+ *   row_ptr  device int64[I + 1] output, as tc_pattern_view's row_ptr.
+ *   status   device int or NULL: set to 0, then to TC_ERR_RANGE if a key lies
+ *            outside [0, I) (perm is then still a permutation, row_ptr is not
+ *            meaningful).
+ * Work space is one array of about 16.5 MB compiled into the library; every
+ * GPU that loads the library holds it until the process exits.  The first call
+ * on each device looks up the array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  All calls share the array
+ * and a call leaves its contents behind: calls whose GPU work overlaps (other
+ * streams, other host threads) race and give wrong answers, so serialize them.
+ * nnz > TC_SORT_NOALLOC_MAX_NNZ returns TC_ERR_UNSUPPORTED and launches
+ * nothing.  Asynchronous on `stream`. */
+tc_status tc_sort_mode_noalloc(int64_t nnz, const int32_t *key, int64_t I, int64_t *perm,
+                               int64_t *row_ptr, int *status, tc_stream_t stream);
+
 /* ------------------------------------------------------------------ misc */
 
 /* Number of kernel launches this library has issued in the calling process

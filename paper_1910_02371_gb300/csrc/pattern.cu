@@ -545,3 +545,97 @@ tc_status refill_pattern_impl(tc_pattern *p, const int32_t *const *idx, const vo
 }
 
 }  // namespace tc
+
+// ------------------------------------------------------------------ allocation-free mode sort
+// tc_sort_mode_noalloc runs the same radix-sort pipeline as the pattern
+// builder, but its work space is one fixed array compiled into the library
+// instead of device allocations.
+#include <mutex>
+
+namespace tc {
+namespace noalloc {
+
+constexpr int64_t kMaxNnz = TC_SORT_NOALLOC_MAX_NNZ;
+constexpr int64_t kTiles = (kMaxNnz + kTile - 1) / kTile;
+constexpr int64_t kHist = (int64_t)kDigits * kTiles;
+
+constexpr int64_t scan_elems(int64_t n) {
+    int64_t total = 0;
+    while (n > kScanTile) {
+        n = (n + kScanTile - 1) / kScanTile;
+        total += n;
+    }
+    return total;
+}
+
+// byte offsets of the pieces (all multiples of 256)
+constexpr size_t round256(size_t b) { return (b + 255) / 256 * 256; }
+constexpr size_t kOffKtmp = 0;
+constexpr size_t kOffKout = kOffKtmp + round256(sizeof(int32_t) * kMaxNnz);
+constexpr size_t kOffVtmp = kOffKout + round256(sizeof(int32_t) * kMaxNnz);
+constexpr size_t kOffHist = kOffVtmp + round256(sizeof(int64_t) * kMaxNnz);
+constexpr size_t kOffScan = kOffHist + round256(sizeof(int64_t) * kHist);
+constexpr size_t kOffStatus = kOffScan + round256(sizeof(int64_t) * (scan_elems(kHist) + 1));
+constexpr size_t kBytes = kOffStatus + 256;
+
+// The work space: each GPU that loads this library holds it (about 16.5 MB)
+// until the process exits.  Only host code below needs its device address.
+static __device__ __align__(256) unsigned char g_sort_scratch[kBytes];
+
+constexpr int kMaxDevices = 64;
+static std::mutex g_mu;
+static void *g_addr[kMaxDevices] = {};
+
+// Device address of g_sort_scratch on the current device, looked up once per
+// device with that device current.
+static tc_status scratch_address(void **out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return TC_ERR_CUDA;
+    if (dev < 0 || dev >= kMaxDevices) return TC_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!g_addr[dev]) {
+        void *ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_sort_scratch) != cudaSuccess || !ptr) return TC_ERR_CUDA;
+        g_addr[dev] = ptr;
+    }
+    *out = g_addr[dev];
+    return TC_OK;
+}
+
+}  // namespace noalloc
+}  // namespace tc
+
+extern "C" tc_status tc_sort_mode_noalloc(int64_t nnz, const int32_t *key, int64_t I,
+                                          int64_t *perm, int64_t *row_ptr, int *status,
+                                          tc_stream_t stream) {
+    using namespace tc;
+    if (nnz < 0 || I < 1 || I > INT32_MAX || !row_ptr || (nnz > 0 && (!key || !perm)))
+        return TC_ERR_ARG;
+    if (nnz > noalloc::kMaxNnz) return TC_ERR_UNSUPPORTED;
+    void *base = nullptr;
+    tc_status rc = noalloc::scratch_address(&base);
+    if (rc != TC_OK) return rc;
+    unsigned char *b = static_cast<unsigned char *>(base);
+    int32_t *ktmp = reinterpret_cast<int32_t *>(b + noalloc::kOffKtmp);
+    int32_t *kout = reinterpret_cast<int32_t *>(b + noalloc::kOffKout);
+    int64_t *vtmp = reinterpret_cast<int64_t *>(b + noalloc::kOffVtmp);
+    int64_t *hist = reinterpret_cast<int64_t *>(b + noalloc::kOffHist);
+    int64_t *scan = reinterpret_cast<int64_t *>(b + noalloc::kOffScan);
+    int *st_word = status ? status : reinterpret_cast<int *>(b + noalloc::kOffStatus);
+    cudaStream_t st = (cudaStream_t)stream;
+    // Every scratch word a call reads was written earlier in the same call
+    // (histograms are rewritten in full each pass), so only the status word
+    // needs clearing.
+    if (cudaMemsetAsync(st_word, 0, sizeof(int), st) != cudaSuccess) return TC_ERR_CUDA;
+    if (nnz > 0) {
+        range_check_kernel<<<grid_for(nnz, 256, 4096), 256, 0, st>>>(key, nnz, I, st_word);
+        count_launch();
+    }
+    radix_sort(key, nullptr, nnz, I - 1, kout, perm, ktmp, vtmp, hist, scan, st);
+    if (cudaMemsetAsync(row_ptr, 0, sizeof(int64_t) * (I + 1), st) != cudaSuccess) return TC_ERR_CUDA;
+    if (nnz > 0) {
+        row_ptr_kernel<<<grid_for(nnz, 256), 256, 0, st>>>(kout, nnz, I, row_ptr);
+        count_launch();
+    }
+    return cudaGetLastError() == cudaSuccess ? TC_OK : TC_ERR_CUDA;
+}

@@ -51,6 +51,7 @@ _SIGS = {
     "tc_cg_precond_apply": [_P, _P, _P, _P],
     "tc_cg_solve": [_P, _P, _P, _I, _P, _P],
     "tc_ggn_step": [_P, _I, _P, _P],
+    "tc_sort_mode_noalloc": [_I64, _P, _I64, _P, _P, _P, _P],
 }
 for _name, _args in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -294,3 +295,20 @@ class CG:
     def ggn_step(self, iters: int, loss_out=None, stream=None):
         _check(_lib.tc_ggn_step(self.handle, int(iters), _ptr(loss_out), _stream(stream)),
                "tc_ggn_step")
+
+
+SORT_NOALLOC_MAX_NNZ = 1 << 20
+
+
+def sort_mode_noalloc(key: torch.Tensor, I: int, perm=None, row_ptr=None, status=None,
+                      stream=None):
+    """tc_sort_mode_noalloc: the stable per-mode sort without device
+    allocations in the library (the output tensors are the caller's)."""
+    n = int(key.numel())
+    if perm is None:
+        perm = torch.empty(n, dtype=torch.int64, device=key.device)
+    if row_ptr is None:
+        row_ptr = torch.empty(int(I) + 1, dtype=torch.int64, device=key.device)
+    _check(_lib.tc_sort_mode_noalloc(n, _ptr(key), int(I), _ptr(perm), _ptr(row_ptr), _ptr(status),
+                                     _stream(stream)), "tc_sort_mode_noalloc")
+    return perm, row_ptr
