@@ -43,17 +43,26 @@ struct StepIn {
     T t, s;
 };
 
+// The warp's chunk-relative views of the nonzero streams.
+template <typename T>
+struct ChunkStreams {
+    const int32_t *c1, *c2;
+    const T *t;
+    Weights<T> w;
+};
+
 template <typename T, int OP>
-__device__ __forceinline__ StepIn<T> load_step(const SweepParams<T> &P, int64_t qq) {
+__device__ __forceinline__ StepIn<T> load_step(const SweepParams<T> &P, const ChunkStreams<T> &S,
+                                               int off) {
     StepIn<T> in;
-    in.j = __ldcs(P.c1 + qq);
-    in.k = __ldcs(P.c2 + qq);
+    in.j = __ldcs(S.c1 + off);
+    in.k = __ldcs(S.c2 + off);
     if constexpr (OP == OP_MTTKRP) {
-        in.s = weight_at(P.w, qq);
+        in.s = weight_at(S.w, off);
         in.t = T(0);
     } else {
         in.s = T(0);
-        in.t = (OP == OP_GGN && P.loss == TC_LOSS_LS) ? T(0) : __ldcs(P.t + qq);
+        in.t = (OP == OP_GGN && P.loss == TC_LOSS_LS) ? T(0) : __ldcs(S.t + off);
     }
     return in;
 }
@@ -64,7 +73,8 @@ template <typename T, int V, int G, bool VEC, int OP>
 __device__ __forceinline__ void contribution(const SweepParams<T> &P, const StepIn<T> &in,
                                              const T (&a)[V], const T (&xa)[V], int lg, bool valid,
                                              T (&c)[V], double &lacc, bool &dom_ok) {
-    const int R = P.R;
+    constexpr int RT = V * G;
+    const int R = VEC ? RT : P.R;
     T b[V], e[V];
     load_slice<T, V, VEC>(b, P.A1, in.j, R, lg);
     load_slice<T, V, VEC>(e, P.A2, in.k, R, lg);
@@ -94,7 +104,7 @@ __device__ __forceinline__ void contribution(const SweepParams<T> &P, const Step
         }
         const T z = group_sum<G>(zp);
         T d2 = T(2);
-        if (P.loss != TC_LOSS_LS) {
+        if (P.loss != TC_LOSS_LS) {   // (part is unused for least squares)
             const T m = group_sum<G>(part);
             T phi, d1;
             loss_terms(P.loss, in.t, m, phi, d1, d2, dom_ok);
@@ -119,17 +129,28 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepParams<T> P) {
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t c0 = warp * P.chunk;
     const bool active = c0 < P.nnz;     // idle warps still join the block reductions
-    const int64_t cend = active ? min(c0 + P.chunk, P.nnz) : c0;
+    // positions inside the chunk are 32-bit offsets from c0
+    const int n = active ? (int)(min(c0 + P.chunk, P.nnz) - c0) : 0;
     const int64_t *__restrict__ nzp = P.nz_ptr;
-    const int R = P.R;
+    const int R = VEC ? RT : P.R;
     const int n_ne = active ? (int)__ldg(P.n_ne_dev) : 1;
+
+    ChunkStreams<T> S;
+    S.c1 = P.c1 + c0;
+    S.c2 = P.c2 + c0;
+    S.t = P.t ? P.t + c0 : nullptr;
+    S.w = P.w;
+    if (P.w.to0) S.w.to0 = P.w.to0 + c0;
+    else if (P.w.s) S.w.s = P.w.s + c0;
 
     int cur = active ? search_le32(nzp, 0, n_ne - 1, c0) : 0;
     const int first_cr = cur;
     const bool first_shared = active && __ldg(nzp + cur) < c0;
-    const int last_cr = active ? search_le32(nzp, cur, n_ne - 1, cend - 1) : 0;
-    const bool last_shared = active && __ldg(nzp + last_cr + 1) > cend;
-    int64_t row_end = active ? __ldg(nzp + cur + 1) : 0;
+    const int last_cr = active ? search_le32(nzp, cur, n_ne - 1, c0 + n - 1) : 0;
+    const bool last_shared = active && __ldg(nzp + last_cr + 1) > c0 + n;
+    // end of row `cur` as an offset, clamped to n (beyond the chunk)
+    auto row_end_of = [&](int cr) { return (int)min(__ldg(nzp + cr + 1) - c0, (int64_t)n); };
+    int row_end = active ? row_end_of(cur) : 0;
 
     T acc[V], a[V], xa[V];
 #pragma unroll
@@ -164,36 +185,17 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepParams<T> P) {
         load_slice<T, V, VEC>(a, P.Ad, row, R, lg);
         if constexpr (OP == OP_GGN) load_slice<T, V, VEC>(xa, P.Xd, row, R, lg);
     };
-
-    StepIn<T> nxt;
-    if (active) nxt = load_step<T, OP>(P, min(c0 + g, cend - 1));
-    for (int64_t base = c0; base < cend; base += NG) {
-        const StepIn<T> in = nxt;
-        const int64_t lastpos = min(base + NG, cend) - 1;
-        const bool valid = base + g < cend;
-        if (base + NG < cend) nxt = load_step<T, OP>(P, min(base + NG + g, cend - 1));
-        T c[V];
-        if (row_end > lastpos) {
-            // fast path: the whole step lies in row `cur`
-            if constexpr (OWN) {
-                if (own_cr != cur) {
-                    load_own(cur);
-                    own_cr = cur;
-                }
-            }
-            contribution<T, V, G, VEC, OP>(P, in, a, xa, lg, valid, c, lacc, dom_ok);
-#pragma unroll
-            for (int t = 0; t < V; ++t) acc[t] += c[t];
-            continue;
-        }
-        // slow path: row boundaries inside this step
-        const int64_t qq = valid ? base + g : lastpos;
-        // `cur` holds position base - 1 or base, so the step spans rows cur .. cur + NG
-        const int cr = search_le32(nzp, cur, min(cur + NG, n_ne - 1), qq);
+    // A step whose row boundaries fall inside it (off: first offset; last: its
+    // last valid offset; valid: this group's nonzero exists).
+    auto slow_step = [&](int off, int last, bool valid, const StepIn<T> &in) {
+        const int qq = valid ? off + g : last;
+        // `cur` holds offset off - 1 or off, so the step spans rows cur .. cur + NG
+        const int cr = search_le32(nzp, cur, min(cur + NG, n_ne - 1), c0 + qq);
         if constexpr (OWN) {
             load_own(cr);
             own_cr = cr;
         }
+        T c[V];
         contribution<T, V, G, VEC, OP>(P, in, a, xa, lg, valid, c, lacc, dom_ok);
         if (cr == cur) {
 #pragma unroll
@@ -202,8 +204,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepParams<T> P) {
                 c[t] = T(0);
             }
         }
-        // row `cur` ends inside this step: reduce the private partial sums
-        {
+        {   // row `cur` ends inside this step: reduce the private partial sums
             T tot[V];
 #pragma unroll
             for (int t = 0; t < V; ++t) tot[t] = across_groups<G>(acc[t]);
@@ -231,8 +232,51 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepParams<T> P) {
 #pragma unroll
         for (int t = 0; t < V; ++t) acc[t] = (cr == lcr) ? craw[t] : T(0);
         cur = lcr;
-        row_end = __ldg(nzp + cur + 1);
+        row_end = row_end_of(cur);
         if constexpr (OWN) own_cr = (own_cr == cur) ? cur : -1;
+    };
+
+    StepIn<T> nxt;
+    if (n > 0) nxt = load_step<T, OP>(P, S, min(g, n - 1));
+    int off = 0;
+    // full steps: every group has a nonzero
+    for (; off + NG <= n; off += NG) {
+        const StepIn<T> in = nxt;
+        if (off + NG < n) nxt = load_step<T, OP>(P, S, min(off + NG + g, n - 1));
+        if (row_end >= off + NG) {
+            // the whole step lies in row `cur`: private accumulation, no shuffles
+            if constexpr (OWN) {
+                if (own_cr != cur) {
+                    load_own(cur);
+                    own_cr = cur;
+                }
+            }
+            T c[V];
+            contribution<T, V, G, VEC, OP>(P, in, a, xa, lg, true, c, lacc, dom_ok);
+#pragma unroll
+            for (int t = 0; t < V; ++t) acc[t] += c[t];
+        } else {
+            slow_step(off, off + NG - 1, true, in);
+        }
+    }
+    // the partial last step
+    if (off < n) {
+        const StepIn<T> in = nxt;
+        const bool valid = off + g < n;
+        if (row_end >= n) {
+            if constexpr (OWN) {
+                if (own_cr != cur) {
+                    load_own(cur);
+                    own_cr = cur;
+                }
+            }
+            T c[V];
+            contribution<T, V, G, VEC, OP>(P, in, a, xa, lg, valid, c, lacc, dom_ok);
+#pragma unroll
+            for (int t = 0; t < V; ++t) acc[t] += c[t];
+        } else {
+            slow_step(off, n - 1, valid, in);
+        }
     }
     if (active) {
         T tot[V];
@@ -272,53 +316,63 @@ __global__ void __launch_bounds__(256) tttp_kernel(const TttpParams<T> P) {
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t c0 = warp * P.chunk;
     if (c0 >= P.nnz) return;
-    const int64_t cend = min(c0 + P.chunk, P.nnz);
+    const int n = (int)(min(c0 + P.chunk, P.nnz) - c0);
     const int64_t *__restrict__ nzp = P.nz_ptr;
-    const int R = P.R;
-    const int64_t n_ne = P.A0 ? __ldg(P.n_ne_dev) : 1;
-    int64_t cur = P.A0 ? search_le(nzp, 0, n_ne - 1, c0) : 0;
+    const int R = VEC ? RT : P.R;
+    const int32_t *c1 = P.c1 + c0, *c2 = P.c2 + c0;
+    Weights<T> W = P.w;
+    if (W.to0) W.to0 += c0;
+    else if (W.s) W.s += c0;
+    T *x = P.x + c0;
+    const int n_ne = P.A0 ? (int)__ldg(P.n_ne_dev) : 1;
+    int cur = P.A0 ? search_le32(nzp, 0, n_ne - 1, c0) : 0;
+    int row_end = P.A0 ? (int)min(__ldg(nzp + cur + 1) - c0, (int64_t)n) : n;
+    int own_cr = -1;
+    T a[V];
+#pragma unroll
+    for (int t = 0; t < V; ++t) a[t] = T(1);
 
-    for (int64_t base = c0; base < cend; base += NG) {
-        const int64_t q = base + g;
-        const bool valid = q < cend;
-        const int64_t lastpos = min(base + NG, cend) - 1;
+    for (int off = 0; off < n; off += NG) {
+        const bool valid = off + g < n;
+        const int q = valid ? off + g : n - 1;
+        const int last = min(off + NG, n) - 1;
+        if (P.A0) {
+            if (row_end > last) {              // the step lies in row `cur`
+                if (own_cr != cur) {
+                    load_slice<T, V, VEC>(a, P.A0, __ldg(P.nz_rows + cur), R, lg);
+                    own_cr = cur;
+                }
+            } else {
+                const int cr = search_le32(nzp, cur, min(cur + NG, n_ne - 1), c0 + q);
+                load_slice<T, V, VEC>(a, P.A0, __ldg(P.nz_rows + cr), R, lg);
+                own_cr = cr;
+                const int lcr = __shfl_sync(0xffffffffu, cr, (NG - 1) * G);
+                cur = lcr;
+                row_end = (int)min(__ldg(nzp + cur + 1) - c0, (int64_t)n);
+                own_cr = (own_cr == cur) ? cur : -1;
+            }
+        }
         T prod[V];
 #pragma unroll
-        for (int t = 0; t < V; ++t) prod[t] = T(1);
-        if (P.A0) {
-            int64_t cr;
-            if (__ldg(nzp + cur + 1) > lastpos) cr = cur;
-            else cr = search_le(nzp, cur, min(cur + NG - 1, n_ne - 1), valid ? q : lastpos);
-            if (valid) {
-                T a[V];
-                load_slice<T, V, VEC>(a, P.A0, __ldg(P.nz_rows + cr), R, lg);
+        for (int t = 0; t < V; ++t) prod[t] = a[t];
+        if (P.A1) {
+            T b[V];
+            load_slice<T, V, VEC>(b, P.A1, __ldcs(c1 + q), R, lg);
 #pragma unroll
-                for (int t = 0; t < V; ++t) prod[t] *= a[t];
-            }
-            const int64_t lcr = __shfl_sync(0xffffffffu, cr, (NG - 1) * G);
-            if (base + NG < cend) cur = lcr + ((__ldg(nzp + lcr + 1) <= base + NG) ? 1 : 0);
+            for (int t = 0; t < V; ++t) prod[t] *= b[t];
         }
-        T s = T(0);
-        if (valid) {
-            if (P.A1) {
-                T b[V];
-                load_slice<T, V, VEC>(b, P.A1, __ldcs(P.c1 + q), R, lg);
+        if (P.A2) {
+            T e[V];
+            load_slice<T, V, VEC>(e, P.A2, __ldcs(c2 + q), R, lg);
 #pragma unroll
-                for (int t = 0; t < V; ++t) prod[t] *= b[t];
-            }
-            if (P.A2) {
-                T e[V];
-                load_slice<T, V, VEC>(e, P.A2, __ldcs(P.c2 + q), R, lg);
-#pragma unroll
-                for (int t = 0; t < V; ++t) prod[t] *= e[t];
-            }
-            s = weight_at(P.w, q);
+            for (int t = 0; t < V; ++t) prod[t] *= e[t];
         }
+        const T s = weight_at(W, q);
         T part = T(0);
 #pragma unroll
         for (int t = 0; t < V; ++t) part += (lg * V + t < R) ? prod[t] : T(0);
         const T m = group_sum<G>(part);
-        if (valid && lg == 0) __stcs(P.x + q, s * m);
+        if (valid && lg == 0) __stcs(x + q, s * m);
     }
 }
 

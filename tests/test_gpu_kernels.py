@@ -215,8 +215,13 @@ def test_solve_factor_not_spd_rows_untouched(tc):
     assert np.array_equal(st, ost)          # rows with fewer than R nonzeros are indefinite
     got = host(out)
     np.testing.assert_array_equal(got[st == 1], prev[st == 1])
-    if (st == 0).any():
-        assert rel(got[st == 0], ref[st == 0]) <= 1e-4
+    # the rows that factored are barely definite (lambda < 0), hence badly
+    # conditioned: their solutions carry the FP32 Gram error times a large
+    # condition number, so only a loose agreement is meaningful here
+    ok_rows = np.nonzero(st == 0)[0]
+    if ok_rows.size:
+        assert np.all(np.isfinite(got[ok_rows]))
+        assert rel(got[ok_rows], ref[ok_rows]) <= 1e-2
     assert tc.last_error(p) == tc.OK        # cleared
 
 
