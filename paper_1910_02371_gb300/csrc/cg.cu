@@ -11,6 +11,14 @@ namespace tc {
 // device scalars of one solve
 enum { S_RZ = 0, S_PAP = 1, S_RZNEW = 2, S_STOP = 3, S_COUNT = 8 };
 
+// Offset of entry (i, e) of the direction inside the interleaved buffer (axv
+// = chunk length V of the factor / direction interleave), or of a plain I x R
+// array (axv = 0).
+__device__ __forceinline__ int64_t dir_index(int64_t i, int e, int R, int axv) {
+    if (!axv) return i * R + e;
+    return i * 2 * R + (e / axv) * 2 * axv + axv + e % axv;
+}
+
 // mode == 0: z = P^-1 r and scal[acc] += r.z   (scal may be null: no dot)
 // mode == 1: alpha = rz / pAp; x += alpha p; r -= alpha Ap; z = P^-1 r; scal[acc] += r.z
 // P^-1 is the stored per-row inverse of the diagonal block (pinv, I x R x R);
@@ -20,7 +28,7 @@ enum { S_RZ = 0, S_PAP = 1, S_RZNEW = 2, S_STOP = 3, S_COUNT = 8 };
 template <typename T, int LR>
 __global__ void __launch_bounds__(256) cg_update_kernel(int mode, int64_t I, int R,
                                                         const T *__restrict__ pinv, T *x, T *r,
-                                                        const T *__restrict__ p,
+                                                        const T *__restrict__ p, int axv,
                                                         const T *__restrict__ Ap, T *z,
                                                         double *scal, int acc, int *status) {
     constexpr int RPW = 32 / LR;           // rows per warp
@@ -48,10 +56,11 @@ __global__ void __launch_bounds__(256) cg_update_kernel(int mode, int64_t I, int
         // this lane's entries e0 = l and e1 = l + LR of the row
         const int e0 = l, e1 = l + LR;
         T r0 = T(0), r1 = T(0);
+        const int64_t ri = row_ok ? i : 0;
         if (row_ok && e0 < R) {
             r0 = r[off + e0];
             if (mode == 1) {
-                x[off + e0] = (T)((double)x[off + e0] + alpha * (double)p[off + e0]);
+                x[off + e0] = (T)((double)x[off + e0] + alpha * (double)p[dir_index(ri, e0, R, axv)]);
                 r0 = (T)((double)r0 - alpha * (double)Ap[off + e0]);
                 r[off + e0] = r0;
             }
@@ -59,7 +68,7 @@ __global__ void __launch_bounds__(256) cg_update_kernel(int mode, int64_t I, int
         if (row_ok && e1 < R) {
             r1 = r[off + e1];
             if (mode == 1) {
-                x[off + e1] = (T)((double)x[off + e1] + alpha * (double)p[off + e1]);
+                x[off + e1] = (T)((double)x[off + e1] + alpha * (double)p[dir_index(ri, e1, R, axv)]);
                 r1 = (T)((double)r1 - alpha * (double)Ap[off + e1]);
                 r[off + e1] = r1;
             }
@@ -87,14 +96,32 @@ __global__ void __launch_bounds__(256) cg_update_kernel(int mode, int64_t I, int
     if (scal) block_add(dot, scal + acc);
 }
 
-// p = z + beta p with beta = rz_new / rz
+// p = z + beta p with beta = rz_new / rz (p plain or interleaved, see dir_index)
 template <typename T>
-__global__ void cg_dir_kernel(int64_t n, const T *__restrict__ z, T *p, const double *scal) {
+__global__ void cg_dir_kernel(int64_t I, int R, const T *__restrict__ z, T *p, int axv,
+                              const double *scal) {
     const double rz = scal[S_RZ];
     const double beta = rz != 0.0 ? scal[S_RZNEW] / rz : 0.0;
+    const int64_t n = I * R;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
-         q += (int64_t)gridDim.x * blockDim.x)
-        p[q] = (T)((double)z[q] + beta * (double)p[q]);
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = q / R;
+        const int64_t pi = dir_index(i, (int)(q - i * R), R, axv);
+        p[pi] = (T)((double)z[q] + beta * (double)p[pi]);
+    }
+}
+
+// Interleaved buffer from a factor (part 0) or a direction (part 1).
+template <typename T>
+__global__ void ax_fill_kernel(T *__restrict__ ax, const T *__restrict__ src, int64_t I, int R,
+                               int axv, int part) {
+    const int64_t n = I * R;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = q / R;
+        const int e = (int)(q - i * R);
+        ax[i * 2 * R + (e / axv) * 2 * axv + part * axv + e % axv] = src[q];
+    }
 }
 
 __global__ void cg_scalar_kernel(double *scal, double *rz_hist, int slot) {
@@ -138,6 +165,8 @@ struct tc_cg {
     void *pinv[TC_ORDER] = {nullptr, nullptr, nullptr};
     void *r[TC_ORDER] = {}, *z[TC_ORDER] = {}, *pv[TC_ORDER] = {}, *Ap[TC_ORDER] = {};
     void *grad[TC_ORDER] = {}, *dx[TC_ORDER] = {};
+    void *ax[TC_ORDER] = {};      // interleaved factor / direction rows (vector path)
+    int axv = 0;                  // interleave chunk length, 0 = plain direction buffers
     double *scal = nullptr;
     cudaStream_t own = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -160,7 +189,7 @@ static int sms() {
 
 template <typename T, int LR>
 static void launch_update_lr(int mode, int64_t I, int R, const void *pinv, void *x, void *r,
-                             const void *p, const void *Ap, void *z, double *scal, int acc,
+                             const void *p, int axv, const void *Ap, void *z, double *scal, int acc,
                              int *status, cudaStream_t st) {
     constexpr int RPW = 32 / LR;
     const int64_t groups = (I + RPW - 1) / RPW;
@@ -168,21 +197,23 @@ static void launch_update_lr(int mode, int64_t I, int R, const void *pinv, void 
     if (blocks > 4LL * sms()) blocks = 4LL * sms();
     if (blocks < 1) blocks = 1;
     cg_update_kernel<T, LR><<<(unsigned)blocks, 256, 0, st>>>(
-        mode, I, R, (const T *)pinv, (T *)x, (T *)r, (const T *)p, (const T *)Ap, (T *)z, scal, acc,
-        status);
+        mode, I, R, (const T *)pinv, (T *)x, (T *)r, (const T *)p, axv, (const T *)Ap, (T *)z, scal,
+        acc, status);
     count_launch();
 }
 
 template <typename T>
 static void launch_update(int mode, int64_t I, int R, const void *pinv, void *x, void *r,
-                          const void *p, const void *Ap, void *z, double *scal, int acc,
+                          const void *p, int axv, const void *Ap, void *z, double *scal, int acc,
                           int *status, cudaStream_t st) {
-    if (R <= 2) launch_update_lr<T, 1>(mode, I, R, pinv, x, r, p, Ap, z, scal, acc, status, st);
-    else if (R <= 4) launch_update_lr<T, 2>(mode, I, R, pinv, x, r, p, Ap, z, scal, acc, status, st);
-    else if (R <= 8) launch_update_lr<T, 4>(mode, I, R, pinv, x, r, p, Ap, z, scal, acc, status, st);
-    else if (R <= 16) launch_update_lr<T, 8>(mode, I, R, pinv, x, r, p, Ap, z, scal, acc, status, st);
-    else if (R <= 32) launch_update_lr<T, 16>(mode, I, R, pinv, x, r, p, Ap, z, scal, acc, status, st);
-    else launch_update_lr<T, 32>(mode, I, R, pinv, x, r, p, Ap, z, scal, acc, status, st);
+#define TC_UPD(LR) launch_update_lr<T, LR>(mode, I, R, pinv, x, r, p, axv, Ap, z, scal, acc, status, st)
+    if (R <= 2) TC_UPD(1);
+    else if (R <= 4) TC_UPD(2);
+    else if (R <= 8) TC_UPD(4);
+    else if (R <= 16) TC_UPD(8);
+    else if (R <= 32) TC_UPD(16);
+    else TC_UPD(32);
+#undef TC_UPD
 }
 
 template <typename T>
@@ -190,7 +221,8 @@ static void enqueue_update(tc_cg *cg, int mode, int acc, cudaStream_t st) {
     const tc_pattern *p = cg->p;
     for (int d = 0; d < TC_ORDER; ++d)
         launch_update<T>(mode, p->dims[d], cg->R, cg->precond ? cg->pinv[d] : nullptr, cg->dx[d],
-                         cg->r[d], cg->pv[d], cg->Ap[d], cg->z[d], cg->scal, acc, p->status, st);
+                         cg->r[d], cg->axv ? cg->ax[d] : cg->pv[d], cg->axv, cg->Ap[d], cg->z[d],
+                         cg->scal, acc, p->status, st);
 }
 
 template <typename T>
@@ -199,8 +231,21 @@ static void enqueue_dir(tc_cg *cg, cudaStream_t st) {
         const int64_t n = cg->p->dims[d] * cg->R;
         int64_t blocks = (n + 255) / 256;
         if (blocks > 8LL * sms()) blocks = 8LL * sms();
-        cg_dir_kernel<T><<<(unsigned)blocks, 256, 0, st>>>(n, (const T *)cg->z[d], (T *)cg->pv[d],
-                                                          cg->scal);
+        cg_dir_kernel<T><<<(unsigned)blocks, 256, 0, st>>>(
+            cg->p->dims[d], cg->R, (const T *)cg->z[d], (T *)(cg->axv ? cg->ax[d] : cg->pv[d]),
+            cg->axv, cg->scal);
+        count_launch();
+    }
+}
+
+template <typename T>
+static void enqueue_ax_fill(tc_cg *cg, const void *const *src, int part, cudaStream_t st) {
+    for (int d = 0; d < TC_ORDER; ++d) {
+        const int64_t n = cg->p->dims[d] * cg->R;
+        int64_t blocks = (n + 255) / 256;
+        if (blocks > 8LL * sms()) blocks = 8LL * sms();
+        ax_fill_kernel<T><<<(unsigned)blocks, 256, 0, st>>>((T *)cg->ax[d], (const T *)src[d],
+                                                           cg->p->dims[d], cg->R, cg->axv, part);
         count_launch();
     }
 }
@@ -223,15 +268,23 @@ static tc_status enqueue_solve(tc_cg *cg, const void *const *b, void *const *dx,
     }
     TC_CUDA(cudaMemsetAsync(cg->scal, 0, sizeof(double) * S_COUNT, st));
     enqueue_update<T>(cg, 0, S_RZNEW, st);                 // z0 = P^-1 r0, rz
-    for (int d = 0; d < TC_ORDER; ++d)
-        TC_CUDA(cudaMemcpyAsync(cg->pv[d], cg->z[d], (size_t)p->dims[d] * cg->R * es,
-                                cudaMemcpyDeviceToDevice, st));
+    if (cg->axv) {
+        enqueue_ax_fill<T>(cg, (const void *const *)cg->A, 0, st);   // factors (fixed in the solve)
+        enqueue_ax_fill<T>(cg, (const void *const *)cg->z, 1, st);   // p0 = z0
+    } else {
+        for (int d = 0; d < TC_ORDER; ++d)
+            TC_CUDA(cudaMemcpyAsync(cg->pv[d], cg->z[d], (size_t)p->dims[d] * cg->R * es,
+                                    cudaMemcpyDeviceToDevice, st));
+    }
     cg_start_kernel<<<1, 32, 0, st>>>(cg->scal, rz_out);
     count_launch();
     for (int it = 0; it < iters; ++it) {
-        tc_status rc = launch_ggn_matvec(p, cg->loss, cg->R, (const void *const *)cg->A,
-                                         (const void *const *)cg->pv, cg->lambda, cg->Ap,
-                                         cg->scal + S_PAP, st);
+        tc_status rc =
+            cg->axv ? launch_ggn_matvec_ax(p, cg->loss, cg->R, (const void *const *)cg->ax, cg->lambda,
+                                           cg->Ap, cg->scal + S_PAP, st)
+                    : launch_ggn_matvec(p, cg->loss, cg->R, (const void *const *)cg->A,
+                                        (const void *const *)cg->pv, cg->lambda, cg->Ap,
+                                        cg->scal + S_PAP, st);
         if (rc != TC_OK) return rc;
         enqueue_update<T>(cg, 1, S_RZNEW, st);
         enqueue_dir<T>(cg, st);
@@ -252,6 +305,7 @@ static void free_cg(tc_cg *cg) {
         cudaFree(cg->Ap[d]);
         cudaFree(cg->grad[d]);
         cudaFree(cg->dx[d]);
+        cudaFree(cg->ax[d]);
     }
     cudaFree(cg->scal);
     if (cg->exec) cudaGraphExecDestroy(cg->exec);
@@ -292,6 +346,12 @@ tc_status tc_cg_create(const tc_pattern *p, tc_loss loss, int R, const void *con
         ok = ok && cudaMalloc(&cg->dx[d], bytes) == cudaSuccess;
         if (cg->precond)
             ok = ok && cudaMalloc(&cg->pinv[d], es * p->dims[d] * R * R) == cudaSuccess;
+    }
+    // interleaved factor / direction rows for the matrix-vector product
+    if (vec_ok(R, rank_tier(R), es)) {
+        cg->axv = (int)(16 / es);
+        for (int d = 0; d < TC_ORDER && ok; ++d)
+            ok = cudaMalloc(&cg->ax[d], 2 * es * p->dims[d] * R) == cudaSuccess;
     }
     ok = ok && cudaMalloc((void **)&cg->scal, sizeof(double) * S_COUNT) == cudaSuccess;
     ok = ok && cudaStreamCreateWithFlags(&cg->own, cudaStreamNonBlocking) == cudaSuccess;
@@ -334,10 +394,12 @@ tc_status tc_cg_precond_apply(tc_cg *cg, const void *const *r, void *const *z,
         const void *pinv = cg->precond ? cg->pinv[d] : nullptr;
         if (p->dtype == TC_F64)
             launch_update<double>(0, p->dims[d], cg->R, pinv, nullptr, const_cast<void *>(r[d]),
-                                  nullptr, nullptr, z[d], nullptr, 0, p->status, (cudaStream_t)stream);
+                                  nullptr, 0, nullptr, z[d], nullptr, 0, p->status,
+                                  (cudaStream_t)stream);
         else
             launch_update<float>(0, p->dims[d], cg->R, pinv, nullptr, const_cast<void *>(r[d]),
-                                 nullptr, nullptr, z[d], nullptr, 0, p->status, (cudaStream_t)stream);
+                                 nullptr, 0, nullptr, z[d], nullptr, 0, p->status,
+                                 (cudaStream_t)stream);
     }
     return cudaGetLastError() == cudaSuccess ? TC_OK : TC_ERR_CUDA;
 }

@@ -68,14 +68,16 @@ inline int rank_tier(int R) {
     return 64;
 }
 
-// Rows may use 16-byte vector loads when the row stride is a multiple of 16
+// Rows may use 32-byte vector loads when the row stride is a multiple of 32
 // bytes and the rank fills the tier.
-inline bool vec_ok(int R, int tier, size_t es) { return R == tier && (R * es) % 16 == 0; }
+constexpr int kVecBytes = 32;
+inline bool vec_ok(int R, int tier, size_t es) { return R == tier && (R * es) % kVecBytes == 0; }
 
-// Every non-null pointer 16-byte aligned (a caller may pass an offset view).
+// Every non-null pointer aligned for the vector loads (a caller may pass an
+// offset view).
 inline bool aligned16(std::initializer_list<const void *> ptrs) {
     for (const void *q : ptrs)
-        if (q && (reinterpret_cast<uintptr_t>(q) & 15u)) return false;
+        if (q && (reinterpret_cast<uintptr_t>(q) & (kVecBytes - 1))) return false;
     return true;
 }
 
@@ -105,6 +107,11 @@ tc_status launch_loss_grad(const tc_pattern *p, tc_loss loss, int R, const void 
 tc_status launch_ggn_matvec(const tc_pattern *p, tc_loss loss, int R, const void *const *A,
                             const void *const *x, double lambda, void *const *y,
                             double *dot_out, cudaStream_t st);
+// The same on interleaved factor / direction buffers AX[n] (I_n x 2R: per lane
+// chunk of 16 bytes, the factor chunk then the direction chunk); needs the
+// vector path (vec_ok).
+tc_status launch_ggn_matvec_ax(const tc_pattern *p, tc_loss loss, int R, const void *const *AX,
+                               double lambda, void *const *y, double *dot_out, cudaStream_t st);
 // Gram + FP64 Cholesky per row.  If pinv_out != null the inverse of each row
 // system, (G_i + lambda I)^-1, is formed in FP64 from the factor and stored
 // (pattern dtype, I_d x R x R) instead of solving.
@@ -126,10 +133,12 @@ void free_pattern(tc_pattern *p);
 namespace tc {
 
 // Lane layout of one row of a factor: V consecutive elements per lane (one
-// 16-byte vector), G lanes per nonzero, NG nonzeros per warp step.
-template <typename T, int RT>
+// VB-byte vector, 16 or 32 bytes), G lanes per nonzero, NG nonzeros per warp
+// step.  Kernels pick VB by measurement: 32-byte lanes halve the instructions
+// per row but raise register use.
+template <typename T, int RT, int VB = 16>
 struct Lay {
-    static constexpr int V = 16 / (int)sizeof(T);
+    static constexpr int V = VB / (int)sizeof(T);
     static constexpr int G = RT / V;
     static constexpr int NG = 32 / G;
 };
@@ -142,7 +151,19 @@ template <typename T, int V, bool VEC>
 __device__ __forceinline__ void load_slice(T (&v)[V], const T *__restrict__ A, int64_t row, int R,
                                            int lg) {
     const T *ptr = A + row * (int64_t)R + lg * V;
-    if constexpr (VEC) {
+    if constexpr (VEC && V * sizeof(T) == 32) {
+        if constexpr (sizeof(T) == 4) {
+            asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]),
+                  "=f"(v[6]), "=f"(v[7])
+                : "l"(ptr));
+        } else {
+            asm("ld.global.nc.v4.f64 {%0,%1,%2,%3}, [%4];"
+                : "=d"(v[0]), "=d"(v[1]), "=d"(v[2]), "=d"(v[3])
+                : "l"(ptr));
+        }
+    } else if constexpr (VEC) {
+        static_assert(V * sizeof(T) == 16, "16- or 32-byte vectors");
         if constexpr (sizeof(T) == 4) {
             float4 q = __ldg(reinterpret_cast<const float4 *>(ptr));
             v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
@@ -160,7 +181,17 @@ template <typename T, int V, bool VEC>
 __device__ __forceinline__ void store_slice(T *__restrict__ A, int64_t row, int R, int lg,
                                             const T (&v)[V]) {
     T *ptr = A + row * (int64_t)R + lg * V;
-    if constexpr (VEC) {
+    if constexpr (VEC && V * sizeof(T) == 32) {
+        if constexpr (sizeof(T) == 4) {
+            asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(ptr), "f"(v[0]),
+                         "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7])
+                         : "memory");
+        } else {
+            asm volatile("st.global.v4.f64 [%0], {%1,%2,%3,%4};" ::"l"(ptr), "d"(v[0]), "d"(v[1]),
+                         "d"(v[2]), "d"(v[3])
+                         : "memory");
+        }
+    } else if constexpr (VEC) {
         if constexpr (sizeof(T) == 4) {
             *reinterpret_cast<float4 *>(ptr) = make_float4(v[0], v[1], v[2], v[3]);
         } else {

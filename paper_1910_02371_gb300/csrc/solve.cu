@@ -43,7 +43,7 @@ struct GramLay {
 
 template <typename T, int RT>
 struct SolveSmem {
-    static constexpr int NG = Lay<T, RT>::NG;
+    static constexpr int NG = Lay<T, RT, 32>::NG;
     // per warp: h buffer, weights, FP64 system, FP64 right-hand side; the
     // preconditioner variant also holds the FP64 inverse
     static constexpr size_t h_bytes = sizeof(T) * NG * RT;
@@ -60,7 +60,7 @@ template <typename T, int RT, bool VEC>
 __device__ __forceinline__ void gram_row(const SolveParams<T> &P, int64_t i, T *hs, T *ws,
                                          T (&acc)[GramLay<RT>::RPL][GramLay<RT>::CPL],
                                          int part = 0, int nparts = 1) {
-    using L = Lay<T, RT>;
+    using L = Lay<T, RT, 32>;
     using GL = GramLay<RT>;
     constexpr int V = L::V, G = L::G, NG = L::NG;
     const int lane = threadIdx.x & 31, g = lane / G, lg = lane % G;
@@ -129,7 +129,7 @@ __device__ __forceinline__ void gram_row(const SolveParams<T> &P, int64_t i, T *
 
 template <typename T, int RT, bool VEC>
 __global__ void solve_kernel(const SolveParams<T> P) {
-    using L = Lay<T, RT>;
+    using L = Lay<T, RT, 32>;
     using GL = GramLay<RT>;
     using SM = SolveSmem<T, RT>;
     constexpr int V = L::V, G = L::G, NG = L::NG;
@@ -278,7 +278,7 @@ template <int RT, bool VEC>
 __device__ __forceinline__ void gram_row_mma(const SolveParams<float> &P, int64_t i, float *stage,
                                              float (&d)[MmaGram<RT>::MT][MmaGram<RT>::NT][4],
                                              int part = 0, int nparts = 1) {
-    using L = Lay<float, RT>;
+    using L = Lay<float, RT, 32>;
     using MG = MmaGram<RT>;
     constexpr int V = L::V, G = L::G, NG = L::NG;
     constexpr int KB = MG::KB, S = MG::STRIDE;
@@ -377,7 +377,7 @@ template <typename T, int RT>
 struct GramCfg {
     static constexpr int W = 4;
     static constexpr bool MMA = sizeof(T) == 4;               // FP32: tensor-core Gram
-    static constexpr int NG = Lay<T, RT>::NG;
+    static constexpr int NG = Lay<T, RT, 32>::NG;
     static constexpr size_t stage_elems = MMA ? MmaGram<RT>::stage_floats : (size_t)(NG * RT + NG);
     static constexpr size_t stage_per_warp = ((sizeof(T) * stage_elems + 15) / 16) * 16;
     static constexpr size_t dense_off = W * stage_per_warp;

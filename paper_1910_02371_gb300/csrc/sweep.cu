@@ -67,17 +67,44 @@ __device__ __forceinline__ StepIn<T> load_step(const SweepParams<T> &P, const Ch
     return in;
 }
 
+// Loads lane slices of a factor row and of the matching direction row.  AXL:
+// both come from one interleaved buffer whose row holds, for each lane's
+// chunk of V entries, the factor chunk followed by the direction chunk (row
+// stride 2R), so one 2V-element vector load serves both.
+template <typename T, int V, bool VEC, bool AXL>
+__device__ __forceinline__ void load_pair(T (&a)[V], T (&x)[V], const T *A, const T *X, int64_t row,
+                                          int R, int lg) {
+    if constexpr (AXL) {
+        T t2[2 * V];
+        load_slice<T, 2 * V, VEC>(t2, A, row, 2 * R, lg);
+#pragma unroll
+        for (int t = 0; t < V; ++t) {
+            a[t] = t2[t];
+            x[t] = t2[V + t];
+        }
+    } else {
+        load_slice<T, V, VEC>(a, A, row, R, lg);
+        load_slice<T, V, VEC>(x, X, row, R, lg);
+    }
+}
+
 // Contribution of one nonzero to its row of the output (one lane's V entries).
 // a / xa: this mode's factor / direction rows of the nonzero's row.
-template <typename T, int V, int G, bool VEC, int OP>
+template <typename T, int V, int G, bool VEC, int OP, bool AXL = false>
 __device__ __forceinline__ void contribution(const SweepParams<T> &P, const StepIn<T> &in,
                                              const T (&a)[V], const T (&xa)[V], int lg, bool valid,
                                              T (&c)[V], double &lacc, bool &dom_ok) {
     constexpr int RT = V * G;
     const int R = VEC ? RT : P.R;
     T b[V], e[V];
-    load_slice<T, V, VEC>(b, P.A1, in.j, R, lg);
-    load_slice<T, V, VEC>(e, P.A2, in.k, R, lg);
+    T xb[V], xc[V];
+    if constexpr (OP == OP_GGN) {
+        load_pair<T, V, VEC, AXL>(b, xb, P.A1, P.X1, in.j, R, lg);
+        load_pair<T, V, VEC, AXL>(e, xc, P.A2, P.X2, in.k, R, lg);
+    } else {
+        load_slice<T, V, VEC>(b, P.A1, in.j, R, lg);
+        load_slice<T, V, VEC>(e, P.A2, in.k, R, lg);
+    }
     if constexpr (OP == OP_MTTKRP) {
 #pragma unroll
         for (int t = 0; t < V; ++t) c[t] = in.s * b[t] * e[t];
@@ -92,9 +119,6 @@ __device__ __forceinline__ void contribution(const SweepParams<T> &P, const Step
         for (int t = 0; t < V; ++t) c[t] = d1 * b[t] * e[t];
         if (lg == 0 && valid) lacc += (double)phi;
     } else {
-        T xb[V], xc[V];
-        load_slice<T, V, VEC>(xb, P.X1, in.j, R, lg);
-        load_slice<T, V, VEC>(xc, P.X2, in.k, R, lg);
         T zp = T(0), part = T(0);
 #pragma unroll
         for (int t = 0; t < V; ++t) {
@@ -119,9 +143,13 @@ __device__ __forceinline__ void contribution(const SweepParams<T> &P, const Step
     }
 }
 
-template <typename T, int RT, bool VEC, int OP>
+// Lane width per operation (bytes per lane vector), chosen by measurement.
+template <int OP>
+constexpr int sweep_vb() { return OP == OP_GRAD ? 32 : 16; }
+
+template <typename T, int RT, bool VEC, int OP, bool AXL = false>
 __global__ void __launch_bounds__(256) sweep_kernel(const SweepParams<T> P) {
-    using L = Lay<T, RT>;
+    using L = Lay<T, RT, sweep_vb<OP>()>;
     constexpr int V = L::V, G = L::G, NG = L::NG;
     constexpr unsigned FULL = 0xffffffffu;
     constexpr bool OWN = OP != OP_MTTKRP;     // needs this mode's own factor row
@@ -174,16 +202,17 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepParams<T> P) {
             store_slice<T, V, VEC>(P.out, row, R, lg, v);
         }
         if (P.dot_acc) {
-            T dw[V];
-            load_slice<T, V, VEC>(dw, P.dot_with, row, R, lg);
+            T dw[V], unused[V];
+            if constexpr (AXL) load_pair<T, V, VEC, true>(unused, dw, P.dot_with, nullptr, row, R, lg);
+            else load_slice<T, V, VEC>(dw, P.dot_with, row, R, lg);
 #pragma unroll
             for (int t = 0; t < V; ++t) dacc += (double)dw[t] * (double)v[t];
         }
     };
     auto load_own = [&](int cr) {
         const int64_t row = __ldg(P.nz_rows + cr);
-        load_slice<T, V, VEC>(a, P.Ad, row, R, lg);
-        if constexpr (OP == OP_GGN) load_slice<T, V, VEC>(xa, P.Xd, row, R, lg);
+        if constexpr (OP == OP_GGN) load_pair<T, V, VEC, AXL>(a, xa, P.Ad, P.Xd, row, R, lg);
+        else load_slice<T, V, VEC>(a, P.Ad, row, R, lg);
     };
     // A step whose row boundaries fall inside it (off: first offset; last: its
     // last valid offset; valid: this group's nonzero exists).
@@ -196,7 +225,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepParams<T> P) {
             own_cr = cr;
         }
         T c[V];
-        contribution<T, V, G, VEC, OP>(P, in, a, xa, lg, valid, c, lacc, dom_ok);
+        contribution<T, V, G, VEC, OP, AXL>(P, in, a, xa, lg, valid, c, lacc, dom_ok);
         if (cr == cur) {
 #pragma unroll
             for (int t = 0; t < V; ++t) {
@@ -252,7 +281,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepParams<T> P) {
                 }
             }
             T c[V];
-            contribution<T, V, G, VEC, OP>(P, in, a, xa, lg, true, c, lacc, dom_ok);
+            contribution<T, V, G, VEC, OP, AXL>(P, in, a, xa, lg, true, c, lacc, dom_ok);
 #pragma unroll
             for (int t = 0; t < V; ++t) acc[t] += c[t];
         } else {
@@ -271,7 +300,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepParams<T> P) {
                 }
             }
             T c[V];
-            contribution<T, V, G, VEC, OP>(P, in, a, xa, lg, valid, c, lacc, dom_ok);
+            contribution<T, V, G, VEC, OP, AXL>(P, in, a, xa, lg, valid, c, lacc, dom_ok);
 #pragma unroll
             for (int t = 0; t < V; ++t) acc[t] += c[t];
         } else {
@@ -454,8 +483,8 @@ static void launch_sweep_t(const SweepParams<T> &P, int tier, bool vec, cudaStre
     };
 #define TC_SWEEP_CASE(RT)                                                              \
     case RT:                                                                           \
-        if (vec) go(sweep_kernel<T, RT, true, OP>, Lay<T, RT>::NG);                    \
-        else go(sweep_kernel<T, RT, false, OP>, Lay<T, RT>::NG);                       \
+        if (vec) go(sweep_kernel<T, RT, true, OP>, Lay<T, RT, sweep_vb<OP>()>::NG);     \
+        else go(sweep_kernel<T, RT, false, OP>, Lay<T, RT, sweep_vb<OP>()>::NG);        \
         break;
     switch (tier) {
         TC_SWEEP_CASE(8)
@@ -650,6 +679,76 @@ static tc_status ggn_t(const tc_pattern *p, tc_loss loss, int R, const void *con
         launch_sweep_t<T, OP_GGN>(P, tier, vec, st);
     }
     return TC_OK;
+}
+
+// y = alpha * (direction part of the interleaved buffer); dot += alpha x.x
+template <typename T>
+__global__ void scale_ax_kernel(T *__restrict__ y, const T *__restrict__ ax, T alpha, int64_t I,
+                                int R, int V, double *dot) {
+    double acc = 0.0;
+    const int64_t n = I * R;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = q / R;
+        const int e = (int)(q - i * R);
+        const T v = ax[i * 2 * R + (e / V) * 2 * V + V + e % V];
+        y[q] = alpha * v;
+        acc += (double)alpha * (double)v * (double)v;
+    }
+    if (dot) block_add(acc, dot);
+}
+
+// Gauss-Newton matvec on interleaved factor / direction buffers (the PCG
+// driver's layout; see load_pair).  Requires the vector path (R fills its tier).
+template <typename T>
+static tc_status ggn_ax_t(const tc_pattern *p, tc_loss loss, int R, const void *const *AX,
+                          double lambda, void *const *y, double *dot_out, cudaStream_t st) {
+    const int tier = rank_tier(R);
+    constexpr int V = 16 / (int)sizeof(T);
+    for (int d = 0; d < TC_ORDER; ++d) {
+        const int64_t n = p->dims[d] * R;
+        int64_t blocks = (n + 255) / 256;
+        if (blocks > (int64_t)sm_count() * 8) blocks = (int64_t)sm_count() * 8;
+        if (blocks < 1) blocks = 1;
+        scale_ax_kernel<T><<<(unsigned)blocks, 256, 0, st>>>((T *)y[d], (const T *)AX[d],
+                                                             (T)(2.0 * lambda), p->dims[d], R, V,
+                                                             dot_out);
+        count_launch();
+        if (p->nnz == 0) continue;
+        int o1, o2;
+        other_modes(d, o1, o2);
+        SweepParams<T> P = base_params<T>(p, d, R);
+        P.Ad = (const T *)AX[d];
+        P.A1 = (const T *)AX[o1];
+        P.A2 = (const T *)AX[o2];
+        P.loss = loss;
+        P.out = (T *)y[d];
+        P.accumulate = 1;
+        P.dot_acc = dot_out;
+        P.dot_with = (const T *)AX[d];
+        const int threads = 256;
+        auto go = [&](auto kern, int NG) {
+            SweepParams<T> Q = P;
+            Q.chunk = pick_chunk(P.nnz, NG);
+            const int64_t warps = (P.nnz + Q.chunk - 1) / Q.chunk;
+            const int64_t nb = (warps * 32 + threads - 1) / threads;
+            kern<<<(unsigned)nb, threads, 0, st>>>(Q);
+            count_launch();
+        };
+        switch (tier) {
+            case 8: go(sweep_kernel<T, 8, true, OP_GGN, true>, Lay<T, 8, 16>::NG); break;
+            case 16: go(sweep_kernel<T, 16, true, OP_GGN, true>, Lay<T, 16, 16>::NG); break;
+            case 32: go(sweep_kernel<T, 32, true, OP_GGN, true>, Lay<T, 32, 16>::NG); break;
+            default: go(sweep_kernel<T, 64, true, OP_GGN, true>, Lay<T, 64, 16>::NG); break;
+        }
+    }
+    return TC_OK;
+}
+
+tc_status launch_ggn_matvec_ax(const tc_pattern *p, tc_loss loss, int R, const void *const *AX,
+                               double lambda, void *const *y, double *dot_out, cudaStream_t st) {
+    return p->dtype == TC_F64 ? ggn_ax_t<double>(p, loss, R, AX, lambda, y, dot_out, st)
+                              : ggn_ax_t<float>(p, loss, R, AX, lambda, y, dot_out, st);
 }
 
 tc_status launch_ggn_matvec(const tc_pattern *p, tc_loss loss, int R, const void *const *A,
