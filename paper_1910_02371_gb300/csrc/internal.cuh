@@ -25,9 +25,10 @@ struct ModeData {
 
 // Work space of the builder, kept when the pattern may be refilled.
 struct PatternScratch {
-    int32_t *kbuf = nullptr, *ktmp = nullptr, *dk = nullptr;
+    int32_t *kbuf = nullptr, *ktmp = nullptr, *dk = nullptr, *c1tmp = nullptr, *c2tmp = nullptr;
     int64_t *vtmp = nullptr, *inv0 = nullptr, *hist = nullptr, *scan = nullptr, *flags = nullptr,
             *dp = nullptr;
+    void *valtmp = nullptr;
 };
 
 struct tc_pattern {
@@ -41,6 +42,7 @@ struct tc_pattern {
     ModeData md[TC_ORDER];
     int *status = nullptr;        // device word: first error recorded, 0 if none
     int64_t *counts = nullptr;    // device: nonempty rows per mode
+    int to0_valid = 0;            // md[d].to0 built (on first use) for the current contents
     PatternScratch work;
     double *dscratch = nullptr;   // device doubles for reductions (kScratchDoubles)
 };
@@ -124,6 +126,9 @@ tc_status build_pattern_impl(int order, const int64_t *dims, int64_t nnz,
                              unsigned flags, cudaStream_t st, tc_pattern **out);
 tc_status refill_pattern_impl(tc_pattern *p, const int32_t *const *idx, const void *vals,
                               cudaStream_t st);
+// Builds the mode-d -> mode-0 position maps (for caller weight arrays in
+// pattern order) if the current contents do not have them yet.
+tc_status ensure_to0(const tc_pattern *p, cudaStream_t st);
 void free_pattern(tc_pattern *p);
 
 }  // namespace tc

@@ -12,6 +12,7 @@
 
 #include <algorithm>
 #include <new>
+#include <type_traits>
 
 namespace tc {
 
@@ -228,6 +229,205 @@ static void radix_sort(const int32_t *keys_in, const int64_t *vals_in, int64_t n
     }
 }
 
+// ------------------------------------------------------------------ payload sort
+// The pattern builder's sort carries, with each key, the input position, the
+// other two modes' indices and the value, so one pass writes the final sorted
+// copies (no random gathers afterwards).  Each tile of kTileP elements is
+// ranked as above, staged in shared memory in its sorted order, and written
+// out digit run by digit run, so consecutive threads write consecutive
+// addresses.
+constexpr int kTileP = 2048;
+constexpr int kItemsP = kTileP / kSortThreads;
+static_assert(kDigits == kSortThreads, "one thread per digit in the tile scan");
+
+struct SortSide {
+    int32_t *key;
+    int64_t *perm;   // null on the first pass: the input position
+    int32_t *c1, *c2;
+    void *val;
+};
+
+__global__ void radix_hist_p_kernel(const int32_t *__restrict__ keys, int64_t n, int shift,
+                                    int64_t num_tiles, int64_t *__restrict__ hist) {
+    __shared__ int h[kDigits];
+    for (int d = threadIdx.x; d < kDigits; d += blockDim.x) h[d] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kTileP;
+    for (int k = 0; k < kItemsP; ++k) {
+        const int64_t q = base + (int64_t)k * kSortThreads + threadIdx.x;
+        if (q < n) atomicAdd(&h[(keys[q] >> shift) & (kDigits - 1)], 1);
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < kDigits; d += blockDim.x)
+        hist[(int64_t)d * num_tiles + blockIdx.x] = h[d];
+}
+
+__device__ __forceinline__ int32_t clamp_index(int32_t v, int64_t I) {
+    return v < 0 ? 0 : ((int64_t)v >= I ? (int32_t)(I - 1) : v);
+}
+
+// VB: value bytes (0, 4 or 8).  first: src.perm is the input position and the
+// index payload is clamped into [0, I1) / [0, I2) (out-of-range indices are
+// already recorded as TC_ERR_RANGE; clamping keeps later factor reads in bounds).
+template <int VB>
+__global__ void __launch_bounds__(kSortThreads)
+radix_scatter_p_kernel(SortSide src, SortSide dst, int64_t n, int shift, int64_t num_tiles,
+                       const int64_t *__restrict__ offs, int64_t I1, int64_t I2, int first) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    int64_t *perm_s = reinterpret_cast<int64_t *>(smem_raw);
+    int32_t *key_s = reinterpret_cast<int32_t *>(perm_s + kTileP);
+    int32_t *c1_s = key_s + kTileP;
+    int32_t *c2_s = c1_s + kTileP;
+    unsigned char *val_s = reinterpret_cast<unsigned char *>(c2_s + kTileP);
+    __shared__ int wcnt[kSortWarps][kDigits];
+    __shared__ int toff[kDigits];
+    __shared__ int64_t goff[kDigits];
+    __shared__ int wsum[kSortWarps];
+    using VT = typename std::conditional<VB == 8, double, float>::type;
+
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int d = lane; d < kDigits; d += 32) wcnt[w][d] = 0;
+    __syncwarp();
+    const int64_t tile0 = (int64_t)blockIdx.x * kTileP;
+    const int64_t base = tile0 + (int64_t)w * 32 * kItemsP;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    int32_t key[kItemsP], c1[kItemsP], c2[kItemsP];
+    int64_t prm[kItemsP];
+    VT val[kItemsP];
+    int pos[kItemsP];
+#pragma unroll
+    for (int r = 0; r < kItemsP; ++r) {
+        const int64_t q = base + (int64_t)r * 32 + lane;
+        const bool valid = q < n;
+        key[r] = valid ? src.key[q] : 0;
+        if (valid) {
+            if (first) {
+                prm[r] = q;
+                c1[r] = clamp_index(src.c1[q], I1);
+                c2[r] = clamp_index(src.c2[q], I2);
+            } else {
+                prm[r] = src.perm[q];
+                c1[r] = src.c1[q];
+                c2[r] = src.c2[q];
+            }
+            if constexpr (VB > 0) val[r] = reinterpret_cast<const VT *>(src.val)[q];
+        }
+        const int dig = valid ? ((key[r] >> shift) & (kDigits - 1)) : kDigits;
+        const unsigned peers = __match_any_sync(0xffffffffu, dig);
+        const int rank = __popc(peers & lt_mask);
+        const int cnt0 = valid ? wcnt[w][dig] : 0;
+        pos[r] = cnt0 + rank;
+        __syncwarp();
+        if (valid && rank == 0) wcnt[w][dig] = cnt0 + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    {   // digit d = thread: prefix over the warps, the tile's digit offsets and the global ones
+        const int d = threadIdx.x;
+        int tot = 0;
+        for (int k = 0; k < kSortWarps; ++k) {
+            const int c = wcnt[k][d];
+            wcnt[k][d] = tot;
+            tot += c;
+        }
+        int inc = tot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) wsum[w] = inc;
+        __syncthreads();
+        int wpre = 0;
+        for (int k = 0; k < w; ++k) wpre += wsum[k];
+        toff[d] = wpre + inc - tot;
+        goff[d] = offs[(int64_t)d * num_tiles + blockIdx.x];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kItemsP; ++r) {
+        const int64_t q = base + (int64_t)r * 32 + lane;
+        if (q < n) {
+            const int dig = (key[r] >> shift) & (kDigits - 1);
+            const int l = toff[dig] + wcnt[w][dig] + pos[r];
+            key_s[l] = key[r];
+            perm_s[l] = prm[r];
+            c1_s[l] = c1[r];
+            c2_s[l] = c2[r];
+            if constexpr (VB > 0) reinterpret_cast<VT *>(val_s)[l] = val[r];
+        }
+    }
+    __syncthreads();
+    const int tile_n = (int)min((int64_t)kTileP, n - tile0);
+    for (int j = threadIdx.x; j < tile_n; j += kSortThreads) {
+        const int32_t k = key_s[j];
+        const int dig = (k >> shift) & (kDigits - 1);
+        const int64_t o = goff[dig] + (j - toff[dig]);
+        dst.key[o] = k;
+        dst.perm[o] = perm_s[j];
+        dst.c1[o] = c1_s[j];
+        dst.c2[o] = c2_s[j];
+        if constexpr (VB > 0) reinterpret_cast<VT *>(dst.val)[o] = reinterpret_cast<const VT *>(val_s)[j];
+    }
+}
+
+// A key range of one value (no sort needed): copy with the positions.
+template <int VB>
+__global__ void copy_p_kernel(SortSide src, SortSide dst, int64_t n, int64_t I1, int64_t I2) {
+    using VT = typename std::conditional<VB == 8, double, float>::type;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        dst.key[q] = src.key[q];
+        dst.perm[q] = q;
+        dst.c1[q] = clamp_index(src.c1[q], I1);
+        dst.c2[q] = clamp_index(src.c2[q], I2);
+        if constexpr (VB > 0) reinterpret_cast<VT *>(dst.val)[q] = reinterpret_cast<const VT *>(src.val)[q];
+    }
+}
+
+static int64_t sort_tiles_p(int64_t n) { return (n + kTileP - 1) / kTileP; }
+static size_t scatter_p_smem(int vb) { return (size_t)kTileP * (8 + 4 + 4 + 4 + vb); }
+
+template <int VB>
+static void radix_sort_p_t(const SortSide &in, const SortSide &out, const SortSide &tmp, int64_t n,
+                           int64_t max_key, int64_t I1, int64_t I2, int64_t *hist, int64_t *scan,
+                           cudaStream_t st) {
+    int bits = 0;
+    while (bits < 31 && (max_key >> bits) > 0) ++bits;
+    const int passes = (bits + kRadixBits - 1) / kRadixBits;
+    if (n == 0) return;
+    if (passes == 0) {
+        copy_p_kernel<VB><<<grid_for(n, 256), 256, 0, st>>>(in, out, n, I1, I2);
+        count_launch();
+        return;
+    }
+    const size_t smem = scatter_p_smem(VB);
+    cudaFuncSetAttribute(radix_scatter_p_kernel<VB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    const int64_t num_tiles = sort_tiles_p(n);
+    SortSide src = in;
+    for (int p = 0; p < passes; ++p) {
+        const SortSide &dst = ((passes - 1 - p) % 2 == 0) ? out : tmp;
+        const int shift = p * kRadixBits;
+        radix_hist_p_kernel<<<(unsigned)num_tiles, kSortThreads, 0, st>>>(src.key, n, shift, num_tiles,
+                                                                         hist);
+        count_launch();
+        scan_exclusive(hist, hist, kDigits * num_tiles, scan, st);
+        radix_scatter_p_kernel<VB><<<(unsigned)num_tiles, kSortThreads, smem, st>>>(
+            src, dst, n, shift, num_tiles, hist, I1, I2, p == 0 ? 1 : 0);
+        count_launch();
+        src = dst;
+    }
+}
+
+static void radix_sort_p(int vb, const SortSide &in, const SortSide &out, const SortSide &tmp,
+                         int64_t n, int64_t max_key, int64_t I1, int64_t I2, int64_t *hist,
+                         int64_t *scan, cudaStream_t st) {
+    if (vb == 8) radix_sort_p_t<8>(in, out, tmp, n, max_key, I1, I2, hist, scan, st);
+    else if (vb == 4) radix_sort_p_t<4>(in, out, tmp, n, max_key, I1, I2, hist, scan, st);
+    else radix_sort_p_t<0>(in, out, tmp, n, max_key, I1, I2, hist, scan, st);
+}
+
 // ------------------------------------------------------------------ pattern kernels
 __global__ void range_check_kernel(const int32_t *__restrict__ idx, int64_t n, int64_t I,
                                    int *status) {
@@ -332,6 +532,8 @@ __global__ void dup_check_kernel(const int32_t *__restrict__ i0, const int32_t *
 }
 
 // ------------------------------------------------------------------ builder
+static void free_scratch(tc_pattern *p);
+
 void free_pattern(tc_pattern *p) {
     if (!p) return;
     for (int d = 0; d < TC_ORDER; ++d) {
@@ -345,16 +547,7 @@ void free_pattern(tc_pattern *p) {
         cudaFree(m.cols[1]);
         cudaFree(m.vals);
     }
-    PatternScratch &w = p->work;
-    cudaFree(w.kbuf);
-    cudaFree(w.ktmp);
-    cudaFree(w.vtmp);
-    cudaFree(w.inv0);
-    cudaFree(w.hist);
-    cudaFree(w.scan);
-    cudaFree(w.flags);
-    cudaFree(w.dk);
-    cudaFree(w.dp);
+    free_scratch(p);
     cudaFree(p->status);
     cudaFree(p->counts);
     cudaFree(p->dscratch);
@@ -376,6 +569,9 @@ static void free_scratch(tc_pattern *p) {
     cudaFree(w.flags);
     cudaFree(w.dk);
     cudaFree(w.dp);
+    cudaFree(w.c1tmp);
+    cudaFree(w.c2tmp);
+    cudaFree(w.valtmp);
     w = PatternScratch();
 }
 
@@ -384,7 +580,7 @@ static tc_status alloc_scratch(tc_pattern *p) {
     const int64_t n = p->nnz;
     int64_t maxI = 0;
     for (int d = 0; d < TC_ORDER; ++d) maxI = p->dims[d] > maxI ? p->dims[d] : maxI;
-    const int64_t hist_n = (int64_t)kDigits * sort_tiles(n);
+    const int64_t hist_n = (int64_t)kDigits * std::max(sort_tiles(n), sort_tiles_p(n));
     int64_t scan_n = scan_scratch_elems(hist_n);
     const int64_t s2 = scan_scratch_elems(maxI);
     if (s2 > scan_n) scan_n = s2;
@@ -394,7 +590,10 @@ static tc_status alloc_scratch(tc_pattern *p) {
               dalloc((void **)&w.inv0, sizeof(int64_t) * n) &&
               dalloc((void **)&w.hist, sizeof(int64_t) * hist_n) &&
               dalloc((void **)&w.scan, sizeof(int64_t) * (scan_n + 1)) &&
-              dalloc((void **)&w.flags, sizeof(int64_t) * maxI);
+              dalloc((void **)&w.flags, sizeof(int64_t) * maxI) &&
+              dalloc((void **)&w.c1tmp, sizeof(int32_t) * n) &&
+              dalloc((void **)&w.c2tmp, sizeof(int32_t) * n) &&
+              (!p->has_vals || dalloc(&w.valtmp, tsize(p->dtype) * n));
     if (ok && (p->flags & TC_PATTERN_CHECK_DUPLICATES))
         ok = dalloc((void **)&w.dk, sizeof(int32_t) * n) && dalloc((void **)&w.dp, sizeof(int64_t) * n);
     return ok ? TC_OK : TC_ERR_OOM;
@@ -442,7 +641,14 @@ static void fill_pattern(tc_pattern *p, const int32_t *const *idx, const void *v
         const int64_t I = p->dims[d];
         // keys outside [0, I) still sort into a permutation of [0, n): digits
         // are taken from the low bits, so no write leaves the arrays
-        radix_sort(idx[d], nullptr, n, I - 1, w.kbuf, m.perm, w.ktmp, w.vtmp, w.hist, w.scan, st);
+        int o1, o2;
+        other_modes(d, o1, o2);
+        SortSide in{const_cast<int32_t *>(idx[d]), nullptr, const_cast<int32_t *>(idx[o1]),
+                    const_cast<int32_t *>(idx[o2]), const_cast<void *>(vals)};
+        SortSide out{w.kbuf, m.perm, m.cols[0], m.cols[1], m.vals};
+        SortSide tmp{w.ktmp, w.vtmp, w.c1tmp, w.c2tmp, w.valtmp};
+        radix_sort_p(p->has_vals ? (int)tsize(p->dtype) : 0, in, out, tmp, n, I - 1, p->dims[o1],
+                     p->dims[o2], w.hist, w.scan, st);
         cudaMemsetAsync(m.row_ptr, 0, sizeof(int64_t) * (I + 1), st);
         if (n > 0) {
             row_ptr_kernel<<<grid_for(n, 256), 256, 0, st>>>(w.kbuf, n, I, m.row_ptr);
@@ -454,32 +660,9 @@ static void fill_pattern(tc_pattern *p, const int32_t *const *idx, const void *v
         nonempty_fill_kernel<<<grid_for(I, 256), 256, 0, st>>>(m.row_ptr, I, w.flags, n, m.nz_rows,
                                                                m.nz_ptr, m.n_ne_dev);
         count_launch();
-        int o1, o2;
-        other_modes(d, o1, o2);
-        if (n > 0) {
-            gather_i32_kernel<<<grid_for(n, 256), 256, 0, st>>>(idx[o1], m.perm, n, p->dims[o1], m.cols[0]);
-            gather_i32_kernel<<<grid_for(n, 256), 256, 0, st>>>(idx[o2], m.perm, n, p->dims[o2], m.cols[1]);
-            count_launch(2);
-            if (p->has_vals) {
-                if (p->dtype == TC_F64)
-                    gather_val_kernel<double><<<grid_for(n, 256), 256, 0, st>>>(
-                        (const double *)vals, m.perm, n, (double *)m.vals);
-                else
-                    gather_val_kernel<float><<<grid_for(n, 256), 256, 0, st>>>(
-                        (const float *)vals, m.perm, n, (float *)m.vals);
-                count_launch();
-            }
-        }
     }
-    // mode-d position -> mode-0 position, for caller arrays in pattern order
-    if (n > 0) {
-        invert_perm_kernel<<<grid_for(n, 256), 256, 0, st>>>(p->md[0].perm, n, w.inv0);
-        count_launch();
-        for (int d = 1; d < TC_ORDER; ++d) {
-            compose_kernel<<<grid_for(n, 256), 256, 0, st>>>(w.inv0, p->md[d].perm, n, p->md[d].to0);
-            count_launch();
-        }
-    }
+    // the mode-d -> mode-0 maps are rebuilt on first use (ensure_to0)
+    p->to0_valid = 0;
     if ((p->flags & TC_PATTERN_CHECK_DUPLICATES) && n > 1) {
         // lexicographic order by (i_0, i_1, i_2): stable sorts by i_2, then i_1, then i_0
         int64_t *cur = nullptr;
@@ -534,6 +717,24 @@ tc_status build_pattern_impl(int order, const int64_t *dims, int64_t nnz,
     }
     if (!(flags & TC_PATTERN_REFILLABLE)) free_scratch(p);
     *out = p;
+    return TC_OK;
+}
+
+tc_status ensure_to0(const tc_pattern *pc, cudaStream_t st) {
+    tc_pattern *p = const_cast<tc_pattern *>(pc);
+    if (p->to0_valid || p->nnz == 0) return TC_OK;
+    const int64_t n = p->nnz;
+    int64_t *inv0 = p->work.inv0;
+    const bool temp = inv0 == nullptr;
+    if (temp) TC_CUDA(cudaMallocAsync((void **)&inv0, sizeof(int64_t) * n, st));
+    invert_perm_kernel<<<grid_for(n, 256), 256, 0, st>>>(p->md[0].perm, n, inv0);
+    count_launch();
+    for (int d = 1; d < TC_ORDER; ++d) {
+        compose_kernel<<<grid_for(n, 256), 256, 0, st>>>(inv0, p->md[d].perm, n, p->md[d].to0);
+        count_launch();
+    }
+    if (temp) TC_CUDA(cudaFreeAsync(inv0, st));
+    p->to0_valid = 1;
     return TC_OK;
 }
 

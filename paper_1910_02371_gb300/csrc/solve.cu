@@ -599,7 +599,11 @@ static tc_status solve_t(const tc_pattern *p, tc_weights w, const void *s, int R
         if (w == TC_W_VALUES) P.w.s = (const T *)md.vals;
         else if (w == TC_W_ARRAY) {
             P.w.s = (const T *)s;
-            if (mode != 0) P.w.to0 = md.to0;
+            if (mode != 0) {
+                tc_status rc = ensure_to0(p, st);
+                if (rc != TC_OK) return rc;
+                P.w.to0 = md.to0;
+            }
         }
     }
     const int tier = rank_tier(R);

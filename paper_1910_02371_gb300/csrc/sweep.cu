@@ -590,6 +590,10 @@ static tc_status mttkrp_t(const tc_pattern *p, tc_weights w, const void *s, int 
         TC_CUDA(cudaMemsetAsync(out, 0, bytes, st));
     }
     if (p->nnz == 0) return TC_OK;
+    if (w == TC_W_ARRAY && mode != 0) {
+        tc_status rc = ensure_to0(p, st);
+        if (rc != TC_OK) return rc;
+    }
     int o1, o2;
     other_modes(mode, o1, o2);
     SweepParams<T> P = base_params<T>(p, mode, R);
