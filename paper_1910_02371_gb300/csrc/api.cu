@@ -189,7 +189,7 @@ tc_status tc_ggn_matvec(const tc_pattern *p, tc_loss loss, int R, const void *co
         for (int m = 0; m < TC_ORDER; ++m)
             if (y[n] == x[m]) return TC_ERR_ARG;
     }
-    tc_status rc = launch_ggn_matvec(p, loss, R, factors, x, lambda, y, nullptr,
+    tc_status rc = launch_ggn_matvec(p, loss, R, factors, x, lambda, y, nullptr, 1,
                                      (cudaStream_t)stream);
     return rc != TC_OK ? rc : launch_status();
 }

@@ -9,7 +9,7 @@
 namespace tc {
 
 // device scalars of one solve
-enum { S_RZ = 0, S_PAP = 1, S_RZNEW = 2, S_STOP = 3, S_COUNT = 8 };
+enum { S_RZ = 0, S_PAP = 1, S_RZNEW = 2, S_STOP = 3, S_BETA = 4, S_COUNT = 8 };
 
 // Offset of entry (i, e) of the direction inside the interleaved buffer (axv
 // = chunk length V of the factor / direction interleave), or of a plain I x R
@@ -19,17 +19,29 @@ __device__ __forceinline__ int64_t dir_index(int64_t i, int e, int R, int axv) {
     return i * 2 * R + (e / axv) * 2 * axv + axv + e % axv;
 }
 
+// The per-mode vectors of one solve; the rows of the three modes are numbered
+// consecutively (mode d owns rows rows[d] .. rows[d+1]-1) so that one launch
+// covers all modes.
+template <typename T>
+struct CGModes {
+    const T *pinv[TC_ORDER];
+    T *x[TC_ORDER], *r[TC_ORDER], *z[TC_ORDER], *p[TC_ORDER], *Ap[TC_ORDER];
+    int64_t rows[TC_ORDER + 1];
+    int axv;
+};
+
+__device__ __forceinline__ int mode_of(const int64_t (&rows)[TC_ORDER + 1], int64_t g) {
+    return (g >= rows[1]) + (g >= rows[2]);
+}
+
 // mode == 0: z = P^-1 r and scal[acc] += r.z   (scal may be null: no dot)
 // mode == 1: alpha = rz / pAp; x += alpha p; r -= alpha Ap; z = P^-1 r; scal[acc] += r.z
-// P^-1 is the stored per-row inverse of the diagonal block (pinv, I x R x R);
-// pinv == null means P = I.  LR lanes own one row (LR a power of two >= R/2,
-// at most 32), each lane one or two of its entries; a warp takes 32/LR rows
-// at a time.
+// P^-1 is the stored per-row inverse of the diagonal block (pinv, R x R per
+// row); pinv == null means P = I.  LR lanes own one row (LR a power of two
+// >= R/2, at most 32), each lane one or two of its entries; a warp takes 32/LR
+// rows at a time.
 template <typename T, int LR>
-__global__ void __launch_bounds__(256) cg_update_kernel(int mode, int64_t I, int R,
-                                                        const T *__restrict__ pinv, T *x, T *r,
-                                                        const T *__restrict__ p, int axv,
-                                                        const T *__restrict__ Ap, T *z,
+__global__ void __launch_bounds__(256) cg_update_kernel(int mode, int R, const CGModes<T> M,
                                                         double *scal, int acc, int *status) {
     constexpr int RPW = 32 / LR;           // rows per warp
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -47,20 +59,24 @@ __global__ void __launch_bounds__(256) cg_update_kernel(int mode, int64_t I, int
         }
     }
     double dot = 0.0;
+    const int64_t total = M.rows[TC_ORDER];
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    const int64_t groups = (I + RPW - 1) / RPW;
+    const int64_t groups = (total + RPW - 1) / RPW;
     for (int64_t gi = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib; gi < groups; gi += nwarps) {
-        const int64_t i = gi * RPW + slot;
-        const bool row_ok = i < I;
-        const int64_t off = (row_ok ? i : 0) * (int64_t)R;
+        const int64_t grow = gi * RPW + slot;
+        const bool row_ok = grow < total;
+        const int d = row_ok ? mode_of(M.rows, grow) : 0;
+        const int64_t i = row_ok ? grow - M.rows[d] : 0;
+        const int64_t off = i * (int64_t)R;
+        T *x = M.x[d], *r = M.r[d], *z = M.z[d];
+        const T *p = M.p[d], *Ap = M.Ap[d];
         // this lane's entries e0 = l and e1 = l + LR of the row
         const int e0 = l, e1 = l + LR;
         T r0 = T(0), r1 = T(0);
-        const int64_t ri = row_ok ? i : 0;
         if (row_ok && e0 < R) {
             r0 = r[off + e0];
             if (mode == 1) {
-                x[off + e0] = (T)((double)x[off + e0] + alpha * (double)p[dir_index(ri, e0, R, axv)]);
+                x[off + e0] = (T)((double)x[off + e0] + alpha * (double)p[dir_index(i, e0, R, M.axv)]);
                 r0 = (T)((double)r0 - alpha * (double)Ap[off + e0]);
                 r[off + e0] = r0;
             }
@@ -68,14 +84,15 @@ __global__ void __launch_bounds__(256) cg_update_kernel(int mode, int64_t I, int
         if (row_ok && e1 < R) {
             r1 = r[off + e1];
             if (mode == 1) {
-                x[off + e1] = (T)((double)x[off + e1] + alpha * (double)p[dir_index(ri, e1, R, axv)]);
+                x[off + e1] = (T)((double)x[off + e1] + alpha * (double)p[dir_index(i, e1, R, M.axv)]);
                 r1 = (T)((double)r1 - alpha * (double)Ap[off + e1]);
                 r[off + e1] = r1;
             }
         }
         T z0 = r0, z1 = r1;
+        const T *pinv = M.pinv[d];
         if (pinv) {
-            const T *Pi = pinv + (row_ok ? i : 0) * (int64_t)R * R;
+            const T *Pi = pinv + i * (int64_t)R * R;
             z0 = T(0);
             z1 = T(0);
             for (int c = 0; c < R; ++c) {
@@ -96,19 +113,50 @@ __global__ void __launch_bounds__(256) cg_update_kernel(int mode, int64_t I, int
     if (scal) block_add(dot, scal + acc);
 }
 
-// p = z + beta p with beta = rz_new / rz (p plain or interleaved, see dir_index)
+// p = z + beta p (beta from the scalars; beta == 0 takes p = z) and the start
+// of the next product: Ap = 2 lambda p, scal[S_PAP] += 2 lambda p.p
 template <typename T>
-__global__ void cg_dir_kernel(int64_t I, int R, const T *__restrict__ z, T *p, int axv,
-                              const double *scal) {
-    const double rz = scal[S_RZ];
-    const double beta = rz != 0.0 ? scal[S_RZNEW] / rz : 0.0;
-    const int64_t n = I * R;
+__global__ void cg_dir_kernel(int R, const CGModes<T> M, T two_lambda, double *scal) {
+    const double beta = scal[S_BETA];
+    const int64_t n = M.rows[TC_ORDER] * R;
+    double acc = 0.0;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
          q += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = q / R;
-        const int64_t pi = dir_index(i, (int)(q - i * R), R, axv);
-        p[pi] = (T)((double)z[q] + beta * (double)p[pi]);
+        const int64_t g = q / R;
+        const int e = (int)(q - g * R);
+        const int d = mode_of(M.rows, g);
+        const int64_t i = g - M.rows[d];
+        const int64_t pi = dir_index(i, e, R, M.axv);
+        T *p = M.p[d];
+        const T zv = M.z[d][i * R + e];
+        const T pn = beta != 0.0 ? (T)((double)zv + beta * (double)p[pi]) : zv;
+        p[pi] = pn;
+        const T y = two_lambda * pn;
+        M.Ap[d][i * R + e] = y;
+        acc += (double)y * (double)pn;
     }
+    block_add(acc, scal + S_PAP);
+}
+
+// Between iterations: record r.z, beta = rz_new / rz, rz = rz_new, clear the sums.
+__global__ void cg_scalar_kernel(double *scal, double *rz_hist, int slot, int first) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        const double rz_new = scal[S_RZNEW], rz = scal[S_RZ];
+        if (rz_hist) rz_hist[slot] = rz_new;
+        scal[S_BETA] = (!first && rz != 0.0) ? rz_new / rz : 0.0;
+        scal[S_RZ] = rz_new;
+        scal[S_PAP] = 0.0;
+        scal[S_RZNEW] = 0.0;
+        if (first) scal[S_STOP] = 0.0;
+    }
+}
+
+// y = a x + b y (elementwise)
+template <typename T>
+__global__ void axpby_kernel(int64_t n, T a, const T *__restrict__ x, T b, T *y) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+         q += (int64_t)gridDim.x * blockDim.x)
+        y[q] = a * x[q] + b * y[q];
 }
 
 // Interleaved buffer from a factor (part 0) or a direction (part 1).
@@ -122,33 +170,6 @@ __global__ void ax_fill_kernel(T *__restrict__ ax, const T *__restrict__ src, in
         const int e = (int)(q - i * R);
         ax[i * 2 * R + (e / axv) * 2 * axv + part * axv + e % axv] = src[q];
     }
-}
-
-__global__ void cg_scalar_kernel(double *scal, double *rz_hist, int slot) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        if (rz_hist) rz_hist[slot] = scal[S_RZNEW];
-        scal[S_RZ] = scal[S_RZNEW];
-        scal[S_PAP] = 0.0;
-        scal[S_RZNEW] = 0.0;
-    }
-}
-
-__global__ void cg_start_kernel(double *scal, double *rz_hist) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        if (rz_hist) rz_hist[0] = scal[S_RZNEW];
-        scal[S_RZ] = scal[S_RZNEW];
-        scal[S_PAP] = 0.0;
-        scal[S_RZNEW] = 0.0;
-        scal[S_STOP] = 0.0;
-    }
-}
-
-// y = a x + b y (elementwise)
-template <typename T>
-__global__ void axpby_kernel(int64_t n, T a, const T *__restrict__ x, T b, T *y) {
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
-         q += (int64_t)gridDim.x * blockDim.x)
-        y[q] = a * x[q] + b * y[q];
 }
 
 }  // namespace tc
@@ -187,55 +208,54 @@ static int sms() {
     return n > 0 ? n : 1;
 }
 
+template <typename T>
+static CGModes<T> cg_modes(tc_cg *cg) {
+    CGModes<T> M;
+    M.rows[0] = 0;
+    for (int d = 0; d < TC_ORDER; ++d) {
+        M.pinv[d] = cg->precond ? (const T *)cg->pinv[d] : nullptr;
+        M.x[d] = (T *)cg->dx[d];
+        M.r[d] = (T *)cg->r[d];
+        M.z[d] = (T *)cg->z[d];
+        M.p[d] = (T *)(cg->axv ? cg->ax[d] : cg->pv[d]);
+        M.Ap[d] = (T *)cg->Ap[d];
+        M.rows[d + 1] = M.rows[d] + cg->p->dims[d];
+    }
+    M.axv = cg->axv;
+    return M;
+}
+
 template <typename T, int LR>
-static void launch_update_lr(int mode, int64_t I, int R, const void *pinv, void *x, void *r,
-                             const void *p, int axv, const void *Ap, void *z, double *scal, int acc,
+static void launch_update_lr(int mode, int R, const CGModes<T> &M, double *scal, int acc,
                              int *status, cudaStream_t st) {
     constexpr int RPW = 32 / LR;
-    const int64_t groups = (I + RPW - 1) / RPW;
+    const int64_t groups = (M.rows[TC_ORDER] + RPW - 1) / RPW;
     int64_t blocks = (groups + 7) / 8;
     if (blocks > 4LL * sms()) blocks = 4LL * sms();
     if (blocks < 1) blocks = 1;
-    cg_update_kernel<T, LR><<<(unsigned)blocks, 256, 0, st>>>(
-        mode, I, R, (const T *)pinv, (T *)x, (T *)r, (const T *)p, axv, (const T *)Ap, (T *)z, scal,
-        acc, status);
+    cg_update_kernel<T, LR><<<(unsigned)blocks, 256, 0, st>>>(mode, R, M, scal, acc, status);
     count_launch();
 }
 
 template <typename T>
-static void launch_update(int mode, int64_t I, int R, const void *pinv, void *x, void *r,
-                          const void *p, int axv, const void *Ap, void *z, double *scal, int acc,
-                          int *status, cudaStream_t st) {
-#define TC_UPD(LR) launch_update_lr<T, LR>(mode, I, R, pinv, x, r, p, axv, Ap, z, scal, acc, status, st)
-    if (R <= 2) TC_UPD(1);
-    else if (R <= 4) TC_UPD(2);
-    else if (R <= 8) TC_UPD(4);
-    else if (R <= 16) TC_UPD(8);
-    else if (R <= 32) TC_UPD(16);
-    else TC_UPD(32);
-#undef TC_UPD
+static void launch_update(int mode, int R, const CGModes<T> &M, double *scal, int acc, int *status,
+                          cudaStream_t st) {
+    if (R <= 2) launch_update_lr<T, 1>(mode, R, M, scal, acc, status, st);
+    else if (R <= 4) launch_update_lr<T, 2>(mode, R, M, scal, acc, status, st);
+    else if (R <= 8) launch_update_lr<T, 4>(mode, R, M, scal, acc, status, st);
+    else if (R <= 16) launch_update_lr<T, 8>(mode, R, M, scal, acc, status, st);
+    else if (R <= 32) launch_update_lr<T, 16>(mode, R, M, scal, acc, status, st);
+    else launch_update_lr<T, 32>(mode, R, M, scal, acc, status, st);
 }
 
 template <typename T>
-static void enqueue_update(tc_cg *cg, int mode, int acc, cudaStream_t st) {
-    const tc_pattern *p = cg->p;
-    for (int d = 0; d < TC_ORDER; ++d)
-        launch_update<T>(mode, p->dims[d], cg->R, cg->precond ? cg->pinv[d] : nullptr, cg->dx[d],
-                         cg->r[d], cg->axv ? cg->ax[d] : cg->pv[d], cg->axv, cg->Ap[d], cg->z[d],
-                         cg->scal, acc, p->status, st);
-}
-
-template <typename T>
-static void enqueue_dir(tc_cg *cg, cudaStream_t st) {
-    for (int d = 0; d < TC_ORDER; ++d) {
-        const int64_t n = cg->p->dims[d] * cg->R;
-        int64_t blocks = (n + 255) / 256;
-        if (blocks > 8LL * sms()) blocks = 8LL * sms();
-        cg_dir_kernel<T><<<(unsigned)blocks, 256, 0, st>>>(
-            cg->p->dims[d], cg->R, (const T *)cg->z[d], (T *)(cg->axv ? cg->ax[d] : cg->pv[d]),
-            cg->axv, cg->scal);
-        count_launch();
-    }
+static void launch_dir(tc_cg *cg, const CGModes<T> &M, cudaStream_t st) {
+    const int64_t n = M.rows[TC_ORDER] * cg->R;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 8LL * sms()) blocks = 8LL * sms();
+    if (blocks < 1) blocks = 1;
+    cg_dir_kernel<T><<<(unsigned)blocks, 256, 0, st>>>(cg->R, M, (T)(2.0 * cg->lambda), cg->scal);
+    count_launch();
 }
 
 template <typename T>
@@ -244,6 +264,7 @@ static void enqueue_ax_fill(tc_cg *cg, const void *const *src, int part, cudaStr
         const int64_t n = cg->p->dims[d] * cg->R;
         int64_t blocks = (n + 255) / 256;
         if (blocks > 8LL * sms()) blocks = 8LL * sms();
+        if (blocks < 1) blocks = 1;
         ax_fill_kernel<T><<<(unsigned)blocks, 256, 0, st>>>((T *)cg->ax[d], (const T *)src[d],
                                                            cg->p->dims[d], cg->R, cg->axv, part);
         count_launch();
@@ -251,8 +272,9 @@ static void enqueue_ax_fill(tc_cg *cg, const void *const *src, int part, cudaStr
 }
 
 // Enqueues a full solve of `iters` iterations on st (graph-capturable: no
-// host synchronization, no allocation).  cg->dx receives the solution; the
-// right-hand side is in b.
+// host synchronization, no allocation).  dx receives the solution; the
+// right-hand side is in b.  Per iteration: the three mode passes of the
+// product, one update launch, one scalar launch, one direction launch.
 template <typename T>
 static tc_status enqueue_solve(tc_cg *cg, const void *const *b, void *const *dx, int iters,
                                double *rz_out, cudaStream_t st) {
@@ -266,32 +288,27 @@ static tc_status enqueue_solve(tc_cg *cg, const void *const *b, void *const *dx,
         TC_CUDA(cudaMemsetAsync(dx[d], 0, bytes, st));
         TC_CUDA(cudaMemcpyAsync(cg->r[d], b[d], bytes, cudaMemcpyDeviceToDevice, st));
     }
+    const CGModes<T> M = cg_modes<T>(cg);
+    for (int d = 0; d < TC_ORDER; ++d) cg->dx[d] = save_dx[d];
     TC_CUDA(cudaMemsetAsync(cg->scal, 0, sizeof(double) * S_COUNT, st));
-    enqueue_update<T>(cg, 0, S_RZNEW, st);                 // z0 = P^-1 r0, rz
-    if (cg->axv) {
-        enqueue_ax_fill<T>(cg, (const void *const *)cg->A, 0, st);   // factors (fixed in the solve)
-        enqueue_ax_fill<T>(cg, (const void *const *)cg->z, 1, st);   // p0 = z0
-    } else {
-        for (int d = 0; d < TC_ORDER; ++d)
-            TC_CUDA(cudaMemcpyAsync(cg->pv[d], cg->z[d], (size_t)p->dims[d] * cg->R * es,
-                                    cudaMemcpyDeviceToDevice, st));
-    }
-    cg_start_kernel<<<1, 32, 0, st>>>(cg->scal, rz_out);
+    if (cg->axv) enqueue_ax_fill<T>(cg, (const void *const *)cg->A, 0, st);  // fixed during the solve
+    launch_update<T>(0, cg->R, M, cg->scal, S_RZNEW, p->status, st);          // z0 = P^-1 r0, r0.z0
+    cg_scalar_kernel<<<1, 32, 0, st>>>(cg->scal, rz_out, 0, 1);               // beta = 0
     count_launch();
+    launch_dir<T>(cg, M, st);                                                 // p0 = z0, Ap = 2 lambda p0
     for (int it = 0; it < iters; ++it) {
         tc_status rc =
             cg->axv ? launch_ggn_matvec_ax(p, cg->loss, cg->R, (const void *const *)cg->ax, cg->lambda,
-                                           cg->Ap, cg->scal + S_PAP, st)
+                                           cg->Ap, cg->scal + S_PAP, 0, st)
                     : launch_ggn_matvec(p, cg->loss, cg->R, (const void *const *)cg->A,
                                         (const void *const *)cg->pv, cg->lambda, cg->Ap,
-                                        cg->scal + S_PAP, st);
+                                        cg->scal + S_PAP, 0, st);
         if (rc != TC_OK) return rc;
-        enqueue_update<T>(cg, 1, S_RZNEW, st);
-        enqueue_dir<T>(cg, st);
-        cg_scalar_kernel<<<1, 32, 0, st>>>(cg->scal, rz_out, it + 1);
+        launch_update<T>(1, cg->R, M, cg->scal, S_RZNEW, p->status, st);
+        cg_scalar_kernel<<<1, 32, 0, st>>>(cg->scal, rz_out, it + 1, 0);
         count_launch();
+        if (it + 1 < iters) launch_dir<T>(cg, M, st);
     }
-    for (int d = 0; d < TC_ORDER; ++d) cg->dx[d] = save_dx[d];
     return TC_OK;
 }
 
@@ -389,17 +406,22 @@ tc_status tc_cg_precond_apply(tc_cg *cg, const void *const *r, void *const *z,
                               tc_stream_t stream) {
     if (!cg || !r || !z) return TC_ERR_ARG;
     const tc_pattern *p = cg->p;
-    for (int d = 0; d < TC_ORDER; ++d) {
+    for (int d = 0; d < TC_ORDER; ++d)
         if (!r[d] || !z[d]) return TC_ERR_ARG;
-        const void *pinv = cg->precond ? cg->pinv[d] : nullptr;
-        if (p->dtype == TC_F64)
-            launch_update<double>(0, p->dims[d], cg->R, pinv, nullptr, const_cast<void *>(r[d]),
-                                  nullptr, 0, nullptr, z[d], nullptr, 0, p->status,
-                                  (cudaStream_t)stream);
-        else
-            launch_update<float>(0, p->dims[d], cg->R, pinv, nullptr, const_cast<void *>(r[d]),
-                                 nullptr, 0, nullptr, z[d], nullptr, 0, p->status,
-                                 (cudaStream_t)stream);
+    if (p->dtype == TC_F64) {
+        CGModes<double> M = cg_modes<double>(cg);
+        for (int d = 0; d < TC_ORDER; ++d) {
+            M.r[d] = (double *)const_cast<void *>(r[d]);
+            M.z[d] = (double *)z[d];
+        }
+        launch_update<double>(0, cg->R, M, nullptr, 0, p->status, (cudaStream_t)stream);
+    } else {
+        CGModes<float> M = cg_modes<float>(cg);
+        for (int d = 0; d < TC_ORDER; ++d) {
+            M.r[d] = (float *)const_cast<void *>(r[d]);
+            M.z[d] = (float *)z[d];
+        }
+        launch_update<float>(0, cg->R, M, nullptr, 0, p->status, (cudaStream_t)stream);
     }
     return cudaGetLastError() == cudaSuccess ? TC_OK : TC_ERR_CUDA;
 }

@@ -658,13 +658,14 @@ tc_status launch_loss_grad(const tc_pattern *p, tc_loss loss, int R, const void 
 template <typename T>
 static tc_status ggn_t(const tc_pattern *p, tc_loss loss, int R, const void *const *A,
                        const void *const *x, double lambda, void *const *y, double *dot_out,
-                       cudaStream_t st) {
+                       int init, cudaStream_t st) {
     const int tier = rank_tier(R);
     const bool vec = vec_ok(R, tier, sizeof(T)) && aligned16({A[0], A[1], A[2]}) &&
                      aligned16({x[0], x[1], x[2]}) && aligned16({y[0], y[1], y[2]});
     for (int d = 0; d < TC_ORDER; ++d) {
-        launch_scale<T>((T *)y[d], (const T *)x[d], (T)(2.0 * lambda), p->dims[d] * R, dot_out,
-                        st);
+        if (init)
+            launch_scale<T>((T *)y[d], (const T *)x[d], (T)(2.0 * lambda), p->dims[d] * R, dot_out,
+                            st);
         if (p->nnz == 0) continue;
         int o1, o2;
         other_modes(d, o1, o2);
@@ -706,7 +707,8 @@ __global__ void scale_ax_kernel(T *__restrict__ y, const T *__restrict__ ax, T a
 // driver's layout; see load_pair).  Requires the vector path (R fills its tier).
 template <typename T>
 static tc_status ggn_ax_t(const tc_pattern *p, tc_loss loss, int R, const void *const *AX,
-                          double lambda, void *const *y, double *dot_out, cudaStream_t st) {
+                          double lambda, void *const *y, double *dot_out, int init,
+                          cudaStream_t st) {
     const int tier = rank_tier(R);
     constexpr int V = 16 / (int)sizeof(T);
     for (int d = 0; d < TC_ORDER; ++d) {
@@ -714,10 +716,12 @@ static tc_status ggn_ax_t(const tc_pattern *p, tc_loss loss, int R, const void *
         int64_t blocks = (n + 255) / 256;
         if (blocks > (int64_t)sm_count() * 8) blocks = (int64_t)sm_count() * 8;
         if (blocks < 1) blocks = 1;
-        scale_ax_kernel<T><<<(unsigned)blocks, 256, 0, st>>>((T *)y[d], (const T *)AX[d],
-                                                             (T)(2.0 * lambda), p->dims[d], R, V,
-                                                             dot_out);
-        count_launch();
+        if (init) {
+            scale_ax_kernel<T><<<(unsigned)blocks, 256, 0, st>>>((T *)y[d], (const T *)AX[d],
+                                                                 (T)(2.0 * lambda), p->dims[d], R,
+                                                                 V, dot_out);
+            count_launch();
+        }
         if (p->nnz == 0) continue;
         int o1, o2;
         other_modes(d, o1, o2);
@@ -750,16 +754,17 @@ static tc_status ggn_ax_t(const tc_pattern *p, tc_loss loss, int R, const void *
 }
 
 tc_status launch_ggn_matvec_ax(const tc_pattern *p, tc_loss loss, int R, const void *const *AX,
-                               double lambda, void *const *y, double *dot_out, cudaStream_t st) {
-    return p->dtype == TC_F64 ? ggn_ax_t<double>(p, loss, R, AX, lambda, y, dot_out, st)
-                              : ggn_ax_t<float>(p, loss, R, AX, lambda, y, dot_out, st);
+                               double lambda, void *const *y, double *dot_out, int init,
+                               cudaStream_t st) {
+    return p->dtype == TC_F64 ? ggn_ax_t<double>(p, loss, R, AX, lambda, y, dot_out, init, st)
+                              : ggn_ax_t<float>(p, loss, R, AX, lambda, y, dot_out, init, st);
 }
 
 tc_status launch_ggn_matvec(const tc_pattern *p, tc_loss loss, int R, const void *const *A,
                             const void *const *x, double lambda, void *const *y,
-                            double *dot_out, cudaStream_t st) {
-    return p->dtype == TC_F64 ? ggn_t<double>(p, loss, R, A, x, lambda, y, dot_out, st)
-                              : ggn_t<float>(p, loss, R, A, x, lambda, y, dot_out, st);
+                            double *dot_out, int init, cudaStream_t st) {
+    return p->dtype == TC_F64 ? ggn_t<double>(p, loss, R, A, x, lambda, y, dot_out, init, st)
+                              : ggn_t<float>(p, loss, R, A, x, lambda, y, dot_out, init, st);
 }
 
 }  // namespace tc
