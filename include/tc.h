@@ -213,6 +213,12 @@ tc_status tc_cg_precond_apply(tc_cg *cg, const void *const *r, void *const *z,
 tc_status tc_cg_solve(tc_cg *cg, const void *const *b, void *const *dx, int iters,
                       double *rz_out, tc_stream_t stream);
 
+/* y = H x with the solver's Gauss-Newton matrix at the current factors (the
+ * product tc_cg_solve iterates with: on the vector path the factor and
+ * direction rows are first interleaved into the solver's own buffers).
+ * x, y: host arrays of `order` device I_n x R blocks; y must not alias x. */
+tc_status tc_cg_matvec(tc_cg *cg, const void *const *x, void *const *y, tc_stream_t stream);
+
 /* One Gauss-Newton step at the current factors: gradient, preconditioner,
  * `iters` PCG iterations on H dx = -grad, then A^(n) += dx^(n) in place.
  * loss_out (device double, may be NULL) receives f before the step. */

@@ -475,6 +475,33 @@ tc_status tc_cg_solve(tc_cg *cg, const void *const *b, void *const *dx, int iter
     return TC_OK;
 }
 
+tc_status tc_cg_matvec(tc_cg *cg, const void *const *x, void *const *y, tc_stream_t stream) {
+    if (!cg || !x || !y) return TC_ERR_ARG;
+    for (int d = 0; d < TC_ORDER; ++d) {
+        if (!x[d] || !y[d]) return TC_ERR_ARG;
+        for (int e = 0; e < TC_ORDER; ++e)
+            if (y[d] == x[e]) return TC_ERR_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    tc_status rc;
+    if (cg->axv) {
+        if (cg->p->dtype == TC_F64) {
+            enqueue_ax_fill<double>(cg, (const void *const *)cg->A, 0, st);
+            enqueue_ax_fill<double>(cg, x, 1, st);
+        } else {
+            enqueue_ax_fill<float>(cg, (const void *const *)cg->A, 0, st);
+            enqueue_ax_fill<float>(cg, x, 1, st);
+        }
+        rc = launch_ggn_matvec_ax(cg->p, cg->loss, cg->R, (const void *const *)cg->ax, cg->lambda, y,
+                                  nullptr, 1, st);
+    } else {
+        rc = launch_ggn_matvec(cg->p, cg->loss, cg->R, (const void *const *)cg->A, x, cg->lambda, y,
+                               nullptr, 1, st);
+    }
+    if (rc != TC_OK) return rc;
+    return cudaGetLastError() == cudaSuccess ? TC_OK : TC_ERR_CUDA;
+}
+
 tc_status tc_ggn_step(tc_cg *cg, int iters, double *loss_out, tc_stream_t stream) {
     if (!cg || iters < 0) return TC_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;

@@ -51,6 +51,7 @@ _SIGS = {
     "tc_cg_precond_apply": [_P, _P, _P, _P],
     "tc_cg_solve": [_P, _P, _P, _I, _P, _P],
     "tc_ggn_step": [_P, _I, _P, _P],
+    "tc_cg_matvec": [_P, _P, _P, _P],
     "tc_sort_mode_noalloc": [_I64, _P, _I64, _P, _P, _P, _P],
 }
 for _name, _args in _SIGS.items():
@@ -291,6 +292,13 @@ class CG:
         _check(_lib.tc_cg_solve(self.handle, _ptrs(b), _ptrs(dx), int(iters), _ptr(rz),
                                 _stream(stream)), "tc_cg_solve")
         return dx
+
+    def matvec(self, x, y=None, stream=None):
+        """tc_cg_matvec: y = H x at the solver's factors (its own layout)."""
+        if y is None:
+            y = [torch.empty_like(v) for v in x]
+        _check(_lib.tc_cg_matvec(self.handle, _ptrs(x), _ptrs(y), _stream(stream)), "tc_cg_matvec")
+        return y
 
     def ggn_step(self, iters: int, loss_out=None, stream=None):
         _check(_lib.tc_ggn_step(self.handle, int(iters), _ptr(loss_out), _stream(stream)),

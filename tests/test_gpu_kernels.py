@@ -350,6 +350,21 @@ def test_cg_solve(tc, name, precond):
     assert tc.last_error(p) == tc.OK
 
 
+@pytest.mark.parametrize("name", ["f32_r16", "f64_r16", "f32_r5", "f64_r5_200cube"])
+def test_cg_matvec(tc, name):
+    prob = problem(name)
+    p = build(prob)
+    cg = tc.CG(p, dev_factors(prob), "ls", 0.05)
+    rng = np.random.default_rng(21)
+    x = [rng.standard_normal((I, prob.R)) for I in prob.dims]
+    if prob.dtype == "f32":
+        x = [v.astype(np.float32).astype(np.float64) for v in x]
+    y = cg.matvec([to_dev(v, prob.dtype) for v in x])
+    yo = oracle.ggn_matvec(prob.dims, prob.idx, prob.t, prob.factors, "ls", 0.05, x)
+    for d in range(3):
+        assert rel(host(y[d]), yo[d]) <= TOL[prob.dtype]
+
+
 @pytest.mark.parametrize("name,loss", [("f64_r16", "ls"), ("f32_r16", "ls")])
 def test_ggn_step(tc, name, loss):
     import torch
