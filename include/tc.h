@@ -79,6 +79,29 @@ typedef enum { TC_LOSS_LS = 0, TC_LOSS_POISSON_LOG = 1, TC_LOSS_POISSON_ID = 2 }
 
 typedef enum { TC_W_ONE = 0, TC_W_VALUES = 1, TC_W_ARRAY = 2 } tc_weights;
 
+/* Precision forms of Solve Factor.  The Cholesky factorization and the
+ * triangular solves are FP64 in every form; the forms differ in how the Gram
+ * G_i is summed and in whether one step of iterative refinement follows:
+ *   TC_PREC_FP32         exact products of the stored factors on the FMA
+ *                        units, partial sums folded into compensated pairs:
+ *                        G_i to a few ulps of the pattern dtype; no refinement.
+ *   TC_PREC_TF32_REFINE  G_i on the tensor cores from TF32-rounded inputs
+ *                        (FP32 accumulation), then one refinement step.
+ *   TC_PREC_BF16_REFINE  the same from BF16-rounded inputs.
+ *   TC_PREC_FP32_REFINE  TC_PREC_FP32, then one refinement step.
+ * The refinement step: res_i = rhs_i - lambda a_i - sum_e s_e h_e (h_e^T a_i),
+ * summed in FP64 over the row's nonzeros with h_e formed in FP64 from the
+ * factors (exactly, for FP32 data), then a_i += (L_i L_i^T)^-1 res_i with the
+ * row's Cholesky factor L_i.  It shrinks the error of a_i by about the
+ * condition number of G_i + lambda I times the unit roundoff of the Gram.
+ * The TF32 / BF16 forms need an FP32 pattern (TC_ERR_UNSUPPORTED otherwise). */
+typedef enum {
+    TC_PREC_FP32 = 0,
+    TC_PREC_TF32_REFINE = 1,
+    TC_PREC_BF16_REFINE = 2,
+    TC_PREC_FP32_REFINE = 3
+} tc_prec;
+
 /* tc_build_pattern flags */
 #define TC_PATTERN_CHECK_DUPLICATES 1u  /* extra sort that rejects repeated coordinates */
 #define TC_PATTERN_REFILLABLE 2u        /* keep the builder's work space for tc_pattern_refill
@@ -155,14 +178,37 @@ tc_status tc_mttkrp(const tc_pattern *p, tc_weights w, const void *s, int R,
  * i of mode `mode`,
  *   G_i = sum_{e in row i} s_e h_e h_e^T,   h_e = hadamard_{n != mode} A^(n)[i_n(e)],
  *   (G_i + lambda I) a_i = rhs_i,
- * solved by an unpivoted FP64 Cholesky of each R x R system (G_i is summed in
- * the pattern's dtype).  rhs, out: device I_mode x R; out may alias rhs or
- * factors[mode].  A row with a pivot <= 0 is left unwritten, gets
- * row_status[i] = 1 (device int8[I_mode], may be NULL; other rows get 0) and
- * records TC_ERR_NOT_SPD.  An empty row solves lambda a_i = rhs_i. */
+ * solved by an unpivoted FP64 Cholesky of each R x R system, with G_i summed
+ * and refined as `prec` says (tc_prec).  Rows of any length are balanced over
+ * the GPU (a row longer than a work chunk is split; see tc_solve_tuning).
+ * rhs, out: device I_mode x R; out may alias rhs or factors[mode].  A row with
+ * a pivot <= 0 is left unwritten, gets row_status[i] = 1 (device
+ * int8[I_mode], may be NULL; other rows get 0) and records TC_ERR_NOT_SPD.
+ * An empty row solves lambda a_i = rhs_i. */
 tc_status tc_solve_factor(const tc_pattern *p, tc_weights w, const void *s, int R,
                           const void *const *factors, int mode, const void *rhs,
-                          double lambda, void *out, int8_t *row_status, tc_stream_t stream);
+                          double lambda, tc_prec prec, void *out, int8_t *row_status,
+                          tc_stream_t stream);
+
+/* Solve Factor tuning.  The Gram kernel walks a mode's sorted nonzeros in
+ * chunks of `chunk_nnz` (rows longer than a chunk are split across blocks and
+ * summed with FP64 atomics), and it forms the Gram triangles of at most
+ * `batch_bytes` of rows before factoring them.  Neither changes what is
+ * computed, only how the work is cut (FP32 sums may round differently).
+ *   chunk_nnz    1 .. 2^30, or 0: automatic (about eight chunks per resident
+ *                block, a power of two in [256, 16384]);
+ *   batch_bytes  >= 0; 0: automatic (1 GiB).  At least one warp's rows are
+ *                taken per batch whatever the value.
+ * Settings are process-wide, per dtype and rank tier (the tier of R: 1..8,
+ * 9..16, 17..32, 33..64; R = 0 sets every tier).  t == NULL restores the
+ * automatic choice.  Not synchronized with calls in flight on other threads. */
+typedef struct {
+    int64_t chunk_nnz;
+    int64_t batch_bytes;
+} tc_solve_tuning;
+
+tc_status tc_set_solve_tuning(tc_dtype dtype, int R, const tc_solve_tuning *t);
+tc_status tc_get_solve_tuning(tc_dtype dtype, int R, tc_solve_tuning *t);
 
 /* Objective and gradient (eq. obj; Table 1; Appendix A):
  *   f = sum_e phi(t_e, m_e) + lambda sum_n ||A^(n)||_F^2,  m_e = sum_r prod_n A^(n)[i_n(e), r]

@@ -395,7 +395,8 @@ tc_status tc_cg_setup(tc_cg *cg, tc_stream_t stream) {
     for (int d = 0; d < TC_ORDER; ++d) {
         tc_status rc = launch_solve_factor(cg->p, TC_W_ONE, nullptr, cg->R,
                                            (const void *const *)cg->A, d, nullptr,
-                                           2.0 * cg->lambda, nullptr, nullptr, 1, cg->loss,
+                                           2.0 * cg->lambda, TC_PREC_FP32, nullptr, nullptr, 1,
+                                           cg->loss,
                                            cg->pinv[d], (cudaStream_t)stream);
         if (rc != TC_OK) return rc;
     }

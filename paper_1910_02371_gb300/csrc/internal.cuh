@@ -122,8 +122,8 @@ tc_status launch_ggn_matvec_ax(const tc_pattern *p, tc_loss loss, int R, const v
 // (pattern dtype, I_d x R x R) instead of solving.
 tc_status launch_solve_factor(const tc_pattern *p, tc_weights w, const void *s, int R,
                               const void *const *A, int mode, const void *rhs, double lambda,
-                              void *out, int8_t *row_status, int use_loss_d2, tc_loss loss,
-                              void *pinv_out, cudaStream_t st);
+                              tc_prec prec, void *out, int8_t *row_status, int use_loss_d2,
+                              tc_loss loss, void *pinv_out, cudaStream_t st);
 tc_status build_pattern_impl(int order, const int64_t *dims, int64_t nnz,
                              const int32_t *const *idx, const void *vals, tc_dtype dtype,
                              unsigned flags, cudaStream_t st, tc_pattern **out);

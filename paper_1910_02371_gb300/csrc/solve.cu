@@ -2,13 +2,27 @@
 // block-diagonal Gauss-Newton preconditioner (Sec. 2.5), which is the same
 // per-row system with weights phi'' and regularization 2 lambda.
 //
-// One warp owns one row i of the mode.  It streams the row's nonzeros in steps
-// of NG, forms h_e = hadamard of the other modes' rows with G lanes per
-// nonzero, stages h_e and its weight in shared memory, and accumulates the
-// R x R Gram sum_e s_e h_e h_e^T in registers (each lane owns a block of
-// entries).  The Gram is then moved to shared memory in FP64, lambda is added
-// to the diagonal, and an unpivoted Cholesky factorization and the two
-// triangular solves run in FP64 with the lanes parallel over rows.
+// Two kernels per batch of rows.
+//
+// Kernel A forms the Gram matrices G_i = sum_e s_e h_e h_e^T.  It walks the
+// mode's sorted nonzeros in fixed-size chunks (a persistent grid; every block
+// takes every gridDim-th chunk), so the work per block is the same whatever
+// the distribution of nonzeros over rows: a power-law row with millions of
+// nonzeros is spread over many blocks, and a chunk may hold many short rows.
+// Inside a chunk the block visits the rows it meets in turn: the block's
+// threads gather h_e = (hadamard of the other modes' rows) and the weight of
+// KB nonzeros into shared memory, then accumulate them with one of the Gram
+// engines below (exact FP32 products on the FMA units by default; tensor-core
+// forms for the refined mixed-precision solves).  At the end of a row's
+// segment the packed lower triangle is written: plainly when the whole row
+// lies in the chunk, otherwise added with FP64 atomics into a zeroed slot
+// owned by the first chunk boundary the row crosses.
+//
+// Kernel B runs the FP64 part: lambda on the diagonal, the unpivoted Cholesky
+// factorization, then the two triangular solves, or the inverse
+// (L L^T)^-1 = L^-T L^-1 for the preconditioner.  For R <= 32 one lane owns
+// one row (every FP64 instruction does a warp of useful work); for R > 32 a
+// warp owns one row and the trailing updates are spread evenly over the lanes.
 #include "internal.cuh"
 
 namespace tc {
@@ -29,229 +43,84 @@ struct SolveParams {
     int8_t *row_status;
     double lambda;
     int R;
+    int refine;                   // one refinement step after the solve
     int *status;
 };
 
-// Gram ownership: LPR lanes share one Gram row, each lane owns RPL rows and
-// CPL consecutive columns.
-template <int RT>
-struct GramLay {
-    static constexpr int LPR = RT >= 32 ? 1 : 32 / RT;
-    static constexpr int RPL = RT >= 32 ? RT / 32 : 1;
-    static constexpr int CPL = RT / LPR;
+// Rows [row0, row0 + nrows) of the mode and the chunks of ch nonzeros that
+// cover them, starting at the batch's first nonzero nb = row_ptr[row0].
+template <typename T>
+struct Batch {
+    int64_t row0, nrows;
+    int64_t ch;
+    T *light;        // nrows x TRI packed triangles of rows that lie within one chunk
+                     // (with refinement: then every row's Cholesky factor)
+    double *cut;     // one TRI slot per chunk boundary, for rows that cross one
+    double *res;     // refinement: nrows x R residual sums (zeroed), or null
 };
 
-template <typename T, int RT>
-struct SolveSmem {
-    static constexpr int NG = Lay<T, RT, 32>::NG;
-    // per warp: h buffer, weights, FP64 system, FP64 right-hand side; the
-    // preconditioner variant also holds the FP64 inverse
-    static constexpr size_t h_bytes = sizeof(T) * NG * RT;
-    static constexpr size_t w_bytes = sizeof(T) * NG;
-    static constexpr size_t s_off = ((h_bytes + w_bytes + 15) / 16) * 16;
-    static constexpr size_t per_warp = s_off + sizeof(double) * (RT * RT + RT);
-    static constexpr size_t per_warp_inv = per_warp + sizeof(double) * RT * RT;
-};
+// Packed lower-triangle index of (r, c), c <= r.
+__host__ __device__ __forceinline__ int tri_idx(int r, int c) { return r * (r + 1) / 2 + c; }
 
-// Accumulates row i's Gram sum_e s_e h_e h_e^T into the lane's block `acc`
-// (GramLay ownership).  hs / ws: this warp's staging buffer (NG x RT values,
-// NG weights).  The next step's indices are loaded one step ahead.
-template <typename T, int RT, bool VEC>
-__device__ __forceinline__ void gram_row(const SolveParams<T> &P, int64_t i, T *hs, T *ws,
-                                         T (&acc)[GramLay<RT>::RPL][GramLay<RT>::CPL],
-                                         int part = 0, int nparts = 1) {
-    using L = Lay<T, RT, 32>;
-    using GL = GramLay<RT>;
-    constexpr int V = L::V, G = L::G, NG = L::NG;
-    const int lane = threadIdx.x & 31, g = lane / G, lg = lane % G;
-    const int R = P.R;
-    const int r0 = (lane / GL::LPR) * GL::RPL;
-    const int cb = (lane % GL::LPR) * GL::CPL;
-#pragma unroll
-    for (int a = 0; a < GL::RPL; ++a)
-#pragma unroll
-        for (int b = 0; b < GL::CPL; ++b) acc[a][b] = T(0);
-    const int64_t rs = __ldg(P.row_ptr + i), re = __ldg(P.row_ptr + i + 1);
-    if (rs + (int64_t)part * NG >= re) return;
-    T arow[V];
-    if (P.use_d2) load_slice<T, V, VEC>(arow, P.Ad, i, R, lg);
-    const int64_t stride = (int64_t)nparts * NG;    // this part takes every nparts-th step
-    int64_t qn = min(rs + (int64_t)part * NG + g, re - 1);
-    int32_t jn = __ldcs(P.c1 + qn), kn = __ldcs(P.c2 + qn);
-    for (int64_t base = rs + (int64_t)part * NG; base < re; base += stride) {
-        const bool valid = base + g < re;
-        const int64_t qq = valid ? base + g : re - 1;
-        const int32_t j = jn, k = kn;
-        if (base + stride < re) {
-            qn = min(base + stride + g, re - 1);
-            jn = __ldcs(P.c1 + qn);
-            kn = __ldcs(P.c2 + qn);
-        }
-        T b[V], e[V];
-        load_slice<T, V, VEC>(b, P.A1, j, R, lg);
-        load_slice<T, V, VEC>(e, P.A2, k, R, lg);
-        T h[V];
-#pragma unroll
-        for (int t = 0; t < V; ++t) h[t] = b[t] * e[t];
-        T s;
-        if (P.use_d2) {
-            T part = T(0);
-#pragma unroll
-            for (int t = 0; t < V; ++t) part += arow[t] * h[t];
-            const T m = group_sum<G>(part);
-            T phi, d1, d2;
-            bool ok = true;
-            loss_terms(P.loss, __ldcs(P.t + qq), m, phi, d1, d2, ok);
-            if (!ok && valid) record_error(P.status, TC_ERR_DOMAIN);
-            s = d2;
-        } else {
-            s = weight_at(P.w, qq);
-        }
-        if (!valid) s = T(0);
-#pragma unroll
-        for (int t = 0; t < V; ++t) hs[g * RT + lg * V + t] = h[t];
-        if (lg == 0) ws[g] = s;
-        __syncwarp();
-#pragma unroll 2
-        for (int gg = 0; gg < NG; ++gg) {
-            const T wgt = ws[gg];
-            const T *hv = hs + gg * RT;
-#pragma unroll
-            for (int a = 0; a < GL::RPL; ++a) {
-                const T hr = wgt * hv[r0 + a];
-#pragma unroll
-                for (int bb = 0; bb < GL::CPL; ++bb) acc[a][bb] += hr * hv[cb + bb];
-            }
-        }
-        __syncwarp();
-    }
+// (r, c) of packed index e.
+__device__ __forceinline__ void tri_rc(int e, int &r, int &c) {
+    r = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+    while (tri_idx(r, 0) > e) --r;
+    while (tri_idx(r + 1, 0) <= e) ++r;
+    c = e - tri_idx(r, 0);
 }
 
-template <typename T, int RT, bool VEC>
-__global__ void solve_kernel(const SolveParams<T> P) {
-    using L = Lay<T, RT, 32>;
-    using GL = GramLay<RT>;
-    using SM = SolveSmem<T, RT>;
-    constexpr int V = L::V, G = L::G, NG = L::NG;
-    constexpr unsigned FULL = 0xffffffffu;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int lane = threadIdx.x & 31, g = lane / G, lg = lane % G;
-    const int wib = threadIdx.x >> 5;
-    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (i >= P.I) return;
-    unsigned char *wbase = smem_raw + (size_t)wib * (P.pinv ? SM::per_warp_inv : SM::per_warp);
-    T *hs = reinterpret_cast<T *>(wbase);
-    T *ws = hs + NG * RT;
-    double *S = reinterpret_cast<double *>(wbase + SM::s_off);
-    double *bv = S + RT * RT;
-    const int R = P.R;
-
-    const int r0 = (lane / GL::LPR) * GL::RPL;
-    const int cb = (lane % GL::LPR) * GL::CPL;
-    T acc[GL::RPL][GL::CPL];
-    gram_row<T, RT, VEC>(P, i, hs, ws, acc);
-
-    // Gram -> FP64 system in shared memory, plus lambda I
-#pragma unroll
-    for (int a = 0; a < GL::RPL; ++a)
-#pragma unroll
-        for (int bb = 0; bb < GL::CPL; ++bb) S[(r0 + a) * RT + cb + bb] = (double)acc[a][bb];
-    __syncwarp();
-    for (int r = lane; r < R; r += 32) {
-        S[r * RT + r] += P.lambda;
-        if (!P.pinv) bv[r] = (double)P.rhs[i * (int64_t)R + r];
-    }
-    __syncwarp();
-
-    // unpivoted Cholesky, right-looking, lanes over rows
-    bool ok = true;
-    for (int j = 0; j < R; ++j) {
-        const double d = S[j * RT + j];
-        if (!(d > 0.0)) {
-            ok = false;
-            break;
-        }
-        const double ljj = sqrt(d);
-        __syncwarp();
-        for (int r = j + 1 + lane; r < R; r += 32) S[r * RT + j] /= ljj;
-        if (lane == 0) S[j * RT + j] = ljj;
-        __syncwarp();
-        for (int r = j + 1 + lane; r < R; r += 32) {
-            const double lrj = S[r * RT + j];
-            for (int k = j + 1; k <= r; ++k) S[r * RT + k] -= lrj * S[k * RT + j];
-        }
-        __syncwarp();
-    }
-    ok = __all_sync(FULL, ok);
-    if (!ok) {
-        if (lane == 0) {
-            record_error(P.status, TC_ERR_NOT_SPD);
-            if (P.row_status) P.row_status[i] = 1;
-        }
-        if (P.pinv) {  // an identity block keeps the preconditioner defined
-            T *Po = P.pinv + i * (int64_t)R * R;
-            for (int q = lane; q < R * R; q += 32) Po[q] = (q / R == q % R) ? T(1) : T(0);
-        }
-        return;
-    }
-    if (lane == 0 && P.row_status) P.row_status[i] = 0;
-
-    if (P.pinv) {
-        // (L L^T)^-1 column by column in FP64: lane c solves L L^T y = e_c
-        double *Y = bv + RT;
-        for (int c = lane; c < R; c += 32) {
-            for (int r = 0; r < R; ++r) {
-                double v = (r == c) ? 1.0 : 0.0;
-                for (int k = c; k < r; ++k) v -= S[r * RT + k] * Y[k * RT + c];
-                Y[r * RT + c] = r < c ? 0.0 : v / S[r * RT + r];
-            }
-            for (int r = R - 1; r >= 0; --r) {
-                double v = Y[r * RT + c];
-                for (int k = r + 1; k < R; ++k) v -= S[k * RT + r] * Y[k * RT + c];
-                Y[r * RT + c] = v / S[r * RT + r];
-            }
-        }
-        __syncwarp();
-        T *Po = P.pinv + i * (int64_t)R * R;
-        for (int q = lane; q < R * R; q += 32) Po[q] = (T)Y[(q / R) * RT + q % R];
-        return;
-    }
-    // L y = b, then L^T x = y
-    for (int j = 0; j < R; ++j) {
-        const double yj = bv[j] / S[j * RT + j];
-        __syncwarp();
-        for (int r = j + 1 + lane; r < R; r += 32) bv[r] -= S[r * RT + j] * yj;
-        if (lane == 0) bv[j] = yj;
-        __syncwarp();
-    }
-    for (int j = R - 1; j >= 0; --j) {
-        const double xj = bv[j] / S[j * RT + j];
-        __syncwarp();
-        for (int r = lane; r < j; r += 32) bv[r] -= S[j * RT + r] * xj;
-        if (lane == 0) bv[j] = xj;
-        __syncwarp();
-    }
-    for (int r = lane; r < R; r += 32) P.out[i * (int64_t)R + r] = (T)bv[r];
+// d^(-1/2) for the Cholesky pivots: two Newton steps y <- y (3 - d y^2) / 2
+// from a single-precision seed (each step doubles the correct bits: about
+// 23 -> 46 -> 53), a handful of FP64 multiply-adds in place of a
+// square root and a division.  Outside the single-precision range the
+// correctly rounded path is taken.
+__device__ __forceinline__ double rsqrt_nr(double d) {
+    if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
+    double y = (double)rsqrtf((float)d);
+    const double h = 0.5 * d;
+    y = y * (1.5 - h * y * y);
+    y = y * (1.5 - h * y * y);
+    return y;
 }
 
-// ------------------------------------------------------------------ tensor-core Gram (FP32)
-// G_i = H^T diag(s) H on the tensor cores with mma.sync m16n8k8 (TF32 inputs,
-// FP32 accumulation).  Each FP32 operand x is split into x_hi = tf32(x) and
-// x_lo = tf32(x - x_hi); the product is formed as hi*hi + hi*lo + lo*hi, which
-// keeps about 22 significant bits per product (the FP32 FFMA path keeps 24),
-// far below the rounding of the FP32 sums themselves.  The h vectors and
-// weights of KB nonzeros are staged in shared memory (row stride padded so the
-// fragment loads hit distinct banks), then consumed 8 nonzeros (one K chunk)
-// at a time.  Output tile (mt, nt) covers Gram rows 16 mt .. 16 mt + 15 and
-// columns 8 nt .. 8 nt + 7.
-template <int RT>
-struct MmaGram {
-    static constexpr int KB = 32;                              // staged nonzeros
-    static constexpr int STRIDE = RT + (RT == 8 ? 0 : 8);      // floats per staged row
-    static constexpr int MT = (RT + 15) / 16;
-    static constexpr int NT = RT / 8;
-    static constexpr size_t stage_floats = KB * STRIDE + KB;
-};
+// Slot of a nonempty row [rs, re) that crosses a chunk boundary: the first
+// boundary after rs (boundary b >= 1 sits at nb + b ch; slot b - 1); -1 when
+// the row lies within one chunk.
+__device__ __forceinline__ int64_t cut_slot(int64_t rs, int64_t re, int64_t nb, int64_t ch) {
+    const int64_t b = (rs - nb) / ch + 1;
+    return nb + b * ch < re ? b - 1 : -1;
+}
+
+template <typename T>
+__global__ void zero_cut_kernel(const int64_t *__restrict__ row_ptr, const Batch<T> B, int tri) {
+    const int64_t nb = __ldg(row_ptr + B.row0), ne = __ldg(row_ptr + B.row0 + B.nrows);
+    const int64_t nch = (ne - nb + B.ch - 1) / B.ch;
+    const int64_t n = (nch > 1 ? nch - 1 : 0) * (int64_t)tri;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+         q += (int64_t)gridDim.x * blockDim.x)
+        B.cut[q] = 0.0;
+}
+
+// ------------------------------------------------------------------ Gram engines
+// How G_i = sum_e s_e h_e h_e^T is summed (the Cholesky is FP64 in every form):
+//   GK_FFMA  exact FP32 (or FP64) products on the FMA units; each thread owns a
+//            4 x 4 tile of the lower triangle and keeps FP32 partial sums of at
+//            most 32 terms, folded into a compensated (TwoSum) FP32 pair, so
+//            the Gram is accurate to a few FP32 ulps whatever the row length;
+//   GK_TF32  tensor cores, mma.sync m16n8k8 with TF32 inputs (11-bit
+//            significands) and FP32 accumulation;
+//   GK_BF16  tensor cores, mma.sync m16n8k16 with BF16 inputs (8-bit
+//            significands) and FP32 accumulation.
+// The tensor-core forms are meant to be followed by a refinement step.
+enum GramKind { GK_FFMA = 0, GK_TF32 = 1, GK_BF16 = 2 };
+
+// s + e = a + b exactly (Knuth's TwoSum; no FMA contraction applies).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
 
 __device__ __forceinline__ uint32_t to_tf32(float x) {
     uint32_t r;
@@ -259,9 +128,12 @@ __device__ __forceinline__ uint32_t to_tf32(float x) {
     return r;
 }
 
-__device__ __forceinline__ void split_tf32(float x, uint32_t &hi, uint32_t &lo) {
-    hi = to_tf32(x);
-    lo = to_tf32(x - __uint_as_float(hi));
+// Two floats as a bf16x2 register: `lo` in the low half (the fragment's
+// element of smaller k), `hi` in the high half.
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    uint32_t r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
 }
 
 __device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
@@ -273,304 +145,1135 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// Accumulates row i's Gram into the warp's mma accumulators d[mt][nt][4].
-template <int RT, bool VEC>
-__device__ __forceinline__ void gram_row_mma(const SolveParams<float> &P, int64_t i, float *stage,
-                                             float (&d)[MmaGram<RT>::MT][MmaGram<RT>::NT][4],
-                                             int part = 0, int nparts = 1) {
-    using L = Lay<float, RT, 32>;
-    using MG = MmaGram<RT>;
-    constexpr int V = L::V, G = L::G, NG = L::NG;
-    constexpr int KB = MG::KB, S = MG::STRIDE;
-    const int lane = threadIdx.x & 31, g = lane / G, lg = lane % G;
-    const int gid = lane >> 2, tig = lane & 3;
-    const int R = VEC ? RT : P.R;
-    float *hs = stage;
-    float *ws = stage + KB * S;
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                         uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// Lower-triangle output tiles of the tensor-core forms: tile (mt, nt) covers
+// rows 16 mt .. 16 mt + 15 and columns 8 nt .. 8 nt + 7.
+template <int RT>
+struct Tiles {
+    static constexpr int MT = (RT + 15) / 16, NT = RT / 8;
+    static constexpr int count() {
+        int n = 0;
+        for (int mt = 0; mt < MT; ++mt)
+            for (int nt = 0; nt < NT; ++nt)
+                if (16 * mt + 15 >= 8 * nt) ++n;
+        return n;
+    }
+    static constexpr int NTL = count();
+};
+
+// (mt, nt) of lower tile t, tiles in row-major order.
+template <int RT>
+__device__ __forceinline__ void tile_at(int t, int &mt, int &nt) {
+    mt = 0;
+    for (;;) {
+        const int in_row = min(Tiles<RT>::NT, (16 * mt + 15) / 8 + 1);
+        if (t < in_row) break;
+        t -= in_row;
+        ++mt;
+    }
+    nt = t;
+}
+
+// Block size and reduction buffer of each form.
+constexpr int pow2_floor(int x) { return x >= 32 ? 32 : x >= 16 ? 16 : x >= 8 ? 8 : x >= 4 ? 4 : x >= 2 ? 2 : 1; }
+
+template <typename T, int RT, int KIND>
+struct GramShape {
+    static constexpr bool MMA = KIND != GK_FFMA;
+    // FFMA: 4 x 4 thread tiles on the lower triangle; KS adjacent lanes share
+    // a tile and split the nonzeros of a stage (reduced by shuffles)
+    static constexpr int TR = RT / 4;
+    static constexpr int NTILE = TR * (TR + 1) / 2;
+    static constexpr int NTH = MMA ? 128 : (RT <= 8 ? 96 : 160);
+    // tensor cores: KS warps share each tile (K split), NGRP tile groups
+    static constexpr int NTL = Tiles<RT>::NTL;
+    static constexpr int KS = MMA ? (RT >= 64 ? 1 : (RT >= 32 ? 2 : 4)) : pow2_floor(NTH / NTILE);
+    static constexpr int NGRP = (NTH / 32) / (MMA ? KS : 1);
+    static constexpr int TPW = (NTL + NGRP - 1) / NGRP;
+    static constexpr int KCH = KIND == GK_BF16 ? 16 : 8;   // nonzeros per mma K step
+    static constexpr bool COMP = !MMA && sizeof(T) == 4;
+    // tensor cores: per-K-group partial tiles, reduced through shared memory
+    static constexpr size_t red_bytes = MMA ? (size_t)KS * RT * RT * sizeof(float) : 0;
+    // nonzero slices each thread gathers per stage (more for small ranks,
+    // whose gathers are short and latency-bound)
+    static constexpr int DEPTH = MMA ? 1 : (RT <= 16 ? 4 : 2);
+    static_assert(!MMA || NGRP * TPW == NTL, "tiles divide evenly between the tile groups");
+    static_assert(MMA || 32 % KS == 0, "a tile's K groups are adjacent lanes of one warp");
+};
+
+// Geometry of kernel A: per stage KB nonzeros gathered by the whole block in
+// NSTEP rounds of NW * NG.
+template <typename T, int RT, int KIND>
+struct GramGeo {
+    using SH = GramShape<T, RT, KIND>;
+    static constexpr int NTH = SH::NTH, NW = NTH / 32;
+    using L = Lay<T, RT, 32>;
+    static constexpr int V = L::V, G = L::G, NG = L::NG;
+    static constexpr int BSTEP = NW * NG;
+    static constexpr int NSTEP0 = (32 + BSTEP - 1) / BSTEP;
+    static constexpr int NSTEP = NSTEP0 > SH::DEPTH ? NSTEP0 : SH::DEPTH;
+    static constexpr int KB = BSTEP * NSTEP;
+    // staged row stride: padded so the fragment / tile loads spread over banks
+    static constexpr int S = SH::MMA ? RT + (RT >= 16 ? 8 : 0) : RT + (sizeof(T) == 4 ? 4 : 0);
+    static constexpr int TRI = RT * (RT + 1) / 2;
+    static constexpr int EPT = (TRI + NTH - 1) / NTH;   // triangle entries per thread at a flush
+    static constexpr size_t stage_bytes = ((sizeof(T) * (KB * S + KB) + 15) / 16) * 16;
+    static constexpr size_t smem = stage_bytes + SH::red_bytes;
+    static_assert(KB % SH::KCH == 0, "whole mma K steps per stage");
+};
+
+// FFMA form.  Thread t owns tile t / KS (if < NTILE) in K group t % KS.
+template <typename T, int RT>
+struct FfmaEngine {
+    using SH = GramShape<T, RT, GK_FFMA>;
+    static constexpr bool DIRECT = true;   // flushes by shuffles, no shared buffer
+    static constexpr int FB = 32;     // FP32 terms per fold
+    int r0, c0, kg, cnt;
+    bool active;
+    T acc[4][4];
+    float hi[4][4], lo[4][4];
+
+    __device__ __forceinline__ void init(int tid) {
+        const int tile = tid / SH::KS;
+        active = tile < SH::NTILE;
+        int a = 0, b = 0;
+        if (active) tri_rc(tile, a, b);
+        r0 = 4 * a;
+        c0 = 4 * b;
+        kg = tid % SH::KS;
+    }
+    __device__ __forceinline__ void zero() {
 #pragma unroll
-    for (int mt = 0; mt < MG::MT; ++mt)
+        for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int nt = 0; nt < MG::NT; ++nt)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) d[mt][nt][q] = 0.f;
-    const int64_t rs = __ldg(P.row_ptr + i), re = __ldg(P.row_ptr + i + 1);
-    if (rs + (int64_t)part * KB >= re) return;
-    float arow[V];
-    if (P.use_d2) load_slice<float, V, VEC>(arow, P.Ad, i, R, lg);
-    // this part takes every nparts-th batch of KB nonzeros
-    for (int64_t base = rs + (int64_t)part * KB; base < re; base += (int64_t)nparts * KB) {
-        // stage KB nonzeros (h and weight), NG per warp step
-#pragma unroll
-        for (int st = 0; st < KB / NG; ++st) {
-            const int slot = st * NG + g;
-            const bool valid = base + slot < re;
-            const int64_t qq = valid ? base + slot : re - 1;
-            float b[V], e[V], h[V];
-            load_slice<float, V, VEC>(b, P.A1, __ldcs(P.c1 + qq), R, lg);
-            load_slice<float, V, VEC>(e, P.A2, __ldcs(P.c2 + qq), R, lg);
-#pragma unroll
-            for (int t = 0; t < V; ++t) h[t] = b[t] * e[t];
-            float sw;
-            if (P.use_d2) {
-                float part = 0.f;
-#pragma unroll
-                for (int t = 0; t < V; ++t) part += arow[t] * h[t];
-                const float m = group_sum<G>(part);
-                float phi, d1, d2;
-                bool ok = true;
-                loss_terms(P.loss, __ldcs(P.t + qq), m, phi, d1, d2, ok);
-                if (!ok && valid) record_error(P.status, TC_ERR_DOMAIN);
-                sw = d2;
-            } else {
-                sw = weight_at(P.w, qq);
+            for (int j = 0; j < 4; ++j) {
+                acc[i][j] = T(0);
+                hi[i][j] = lo[i][j] = 0.f;
             }
-            if (!valid) sw = 0.f;
+        cnt = 0;
+    }
+    __device__ __forceinline__ void fold() {
+        if constexpr (SH::COMP) {
 #pragma unroll
-            for (int t = 0; t < V; ++t) hs[slot * S + lg * V + t] = h[t];
-            if (lg == 0) ws[slot] = sw;
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    float s, e;
+                    two_sum(hi[i][j], acc[i][j], s, e);
+                    hi[i][j] = s;
+                    lo[i][j] += e;
+                    acc[i][j] = 0.f;
+                }
         }
-        __syncwarp();
+    }
+    template <int S>
+    __device__ __forceinline__ void accumulate(const T *hs, const T *ws, int nvalid) {
+        if (!active) return;
+        for (int k = kg; k < nvalid; k += SH::KS) {
+            const T w = ws[k];
+            const T *hk = hs + k * S;
+            T a[4], c[4];
+            if constexpr (sizeof(T) == 4) {
+                const float4 x = *reinterpret_cast<const float4 *>(hk + r0);
+                const float4 y = *reinterpret_cast<const float4 *>(hk + c0);
+                a[0] = x.x; a[1] = x.y; a[2] = x.z; a[3] = x.w;
+                c[0] = y.x; c[1] = y.y; c[2] = y.z; c[3] = y.w;
+            } else {
 #pragma unroll
-        for (int kc = 0; kc < KB / 8; ++kc) {
-            const int k0 = kc * 8 + tig, k1 = k0 + 4;
-            const float w0 = ws[k0], w1 = ws[k1];
-#pragma unroll
-            for (int mt = 0; mt < MG::MT; ++mt) {
-                const int ra = mt * 16 + gid, rb = ra + 8;
-                const float x0 = hs[k0 * S + ra], x2 = hs[k1 * S + ra];
-                const float x1 = rb < RT ? hs[k0 * S + rb] : 0.f;
-                const float x3 = rb < RT ? hs[k1 * S + rb] : 0.f;
-                uint32_t ah[4], al[4];
-                split_tf32(x0, ah[0], al[0]);
-                split_tf32(x1, ah[1], al[1]);
-                split_tf32(x2, ah[2], al[2]);
-                split_tf32(x3, ah[3], al[3]);
-#pragma unroll
-                for (int nt = 0; nt < MG::NT; ++nt) {
-                    const int cn = nt * 8 + gid;
-                    uint32_t bh0, bl0, bh1, bl1;
-                    split_tf32(w0 * hs[k0 * S + cn], bh0, bl0);
-                    split_tf32(w1 * hs[k1 * S + cn], bh1, bl1);
-                    mma_tf32(d[mt][nt], ah, bh0, bh1);
-                    mma_tf32(d[mt][nt], ah, bl0, bl1);
-                    mma_tf32(d[mt][nt], al, bh0, bh1);
+                for (int q = 0; q < 4; ++q) {
+                    a[q] = hk[r0 + q];
+                    c[q] = hk[c0 + q];
                 }
             }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const T wa = w * a[i];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] += wa * c[j];
+            }
+            if constexpr (SH::COMP) {
+                if (++cnt == FB) {
+                    fold();
+                    cnt = 0;
+                }
+            }
+        }
+    }
+    // Sums the tile over its K groups (butterfly shuffles; every lane of the
+    // warp takes part) and writes the lower entries of rows < R: plainly to
+    // lrow or, for a row that crosses a chunk boundary, with FP64 atomics.
+    __device__ __forceinline__ void flush(T *lrow, double *crow, bool whole, int R) {
+        fold();
+        cnt = 0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if constexpr (SH::COMP) {
+                    float H = hi[i][j], Lo = lo[i][j];
+#pragma unroll
+                    for (int o = SH::KS / 2; o > 0; o >>= 1) {
+                        const float H2 = __shfl_xor_sync(0xffffffffu, H, o);
+                        const float L2 = __shfl_xor_sync(0xffffffffu, Lo, o);
+                        float s, e;
+                        two_sum(H, H2, s, e);
+                        H = s;
+                        Lo += L2 + e;
+                    }
+                    hi[i][j] = H;
+                    lo[i][j] = Lo;
+                } else {
+                    T v = acc[i][j];
+#pragma unroll
+                    for (int o = SH::KS / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                    acc[i][j] = v;
+                }
+            }
+        if (!active || kg != 0) return;
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int r = r0 + i, c = c0 + j;
+                if (c > r || r >= R) continue;
+                const int e = tri_idx(r, c);
+                if constexpr (SH::COMP) {
+                    if (whole) lrow[e] = hi[i][j] + lo[i][j];
+                    else atomicAdd(crow + e, (double)hi[i][j] + (double)lo[i][j]);
+                } else {
+                    if (whole) lrow[e] = acc[i][j];
+                    else atomicAdd(crow + e, (double)acc[i][j]);
+                }
+            }
+    }
+};
+
+// Tensor-core forms (FP32 data only).  Warp w owns tiles (w % NGRP) * TPW ..
+// + TPW - 1 for K group w / NGRP.
+template <int RT, int KIND>
+struct MmaEngine {
+    using SH = GramShape<float, RT, KIND>;
+    static constexpr bool DIRECT = false;   // flushes through the shared buffer
+    int kg, gid, tig;
+    int tmt[SH::TPW], tnt[SH::TPW];
+    float d[SH::TPW][4];
+
+    __device__ __forceinline__ void init(int tid) {
+        const int lane = tid & 31, w = tid >> 5;
+        gid = lane >> 2;
+        tig = lane & 3;
+        kg = w / SH::NGRP;
+        const int tg = w % SH::NGRP;
+#pragma unroll
+        for (int u = 0; u < SH::TPW; ++u) tile_at<RT>(tg * SH::TPW + u, tmt[u], tnt[u]);
+    }
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int u = 0; u < SH::TPW; ++u)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) d[u][q] = 0.f;
+    }
+    template <int S>
+    __device__ __forceinline__ void accumulate(const float *hf, const float *wf, int nvalid) {
+        const int nkc = (nvalid + SH::KCH - 1) / SH::KCH;
+        for (int kc = kg; kc < nkc; kc += SH::KS) {
+            if constexpr (KIND == GK_TF32) {
+                const int k0 = kc * 8 + tig, k1 = k0 + 4;
+                const float w0 = wf[k0], w1 = wf[k1];
+                uint32_t a[4];
+#pragma unroll
+                for (int u = 0; u < SH::TPW; ++u) {
+                    if (u == 0 || tmt[u] != tmt[u - 1]) {
+                        const int ra = tmt[u] * 16 + gid, rb = ra + 8;
+                        a[0] = to_tf32(hf[k0 * S + ra]);
+                        a[1] = to_tf32(rb < RT ? hf[k0 * S + rb] : 0.f);
+                        a[2] = to_tf32(hf[k1 * S + ra]);
+                        a[3] = to_tf32(rb < RT ? hf[k1 * S + rb] : 0.f);
+                    }
+                    const int cn = tnt[u] * 8 + gid;
+                    mma_tf32(d[u], a, to_tf32(w0 * hf[k0 * S + cn]), to_tf32(w1 * hf[k1 * S + cn]));
+                }
+            } else {
+                const int k0 = kc * 16 + tig * 2;     // k0, k0 + 1, k0 + 8, k0 + 9
+                const float w0 = wf[k0], w1 = wf[k0 + 1], w8 = wf[k0 + 8], w9 = wf[k0 + 9];
+                uint32_t a[4];
+#pragma unroll
+                for (int u = 0; u < SH::TPW; ++u) {
+                    if (u == 0 || tmt[u] != tmt[u - 1]) {
+                        const int ra = tmt[u] * 16 + gid, rb = ra + 8;
+                        const bool vb = rb < RT;
+                        a[0] = pack_bf16(hf[k0 * S + ra], hf[(k0 + 1) * S + ra]);
+                        a[1] = pack_bf16(vb ? hf[k0 * S + rb] : 0.f, vb ? hf[(k0 + 1) * S + rb] : 0.f);
+                        a[2] = pack_bf16(hf[(k0 + 8) * S + ra], hf[(k0 + 9) * S + ra]);
+                        a[3] = pack_bf16(vb ? hf[(k0 + 8) * S + rb] : 0.f, vb ? hf[(k0 + 9) * S + rb] : 0.f);
+                    }
+                    const int cn = tnt[u] * 8 + gid;
+                    const uint32_t b0 = pack_bf16(w0 * hf[k0 * S + cn], w1 * hf[(k0 + 1) * S + cn]);
+                    const uint32_t b1 = pack_bf16(w8 * hf[(k0 + 8) * S + cn], w9 * hf[(k0 + 9) * S + cn]);
+                    mma_bf16(d[u], a, b0, b1);
+                }
+            }
+        }
+    }
+    __device__ __forceinline__ void to_red(unsigned char *red) {
+        float *mine = reinterpret_cast<float *>(red) + kg * RT * RT;
+#pragma unroll
+        for (int u = 0; u < SH::TPW; ++u)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int r = tmt[u] * 16 + gid + (q >= 2 ? 8 : 0);
+                const int c = tnt[u] * 8 + tig * 2 + (q & 1);
+                if (r < RT) mine[r * RT + c] = d[u][q];
+            }
+    }
+    __device__ __forceinline__ void from_red(const unsigned char *red, int r, int c, double &v,
+                                             float &v32) const {
+        const float *x = reinterpret_cast<const float *>(red);
+        float s = 0.f;
+#pragma unroll
+        for (int k = 0; k < SH::KS; ++k) s += x[(k * RT + r) * RT + c];
+        v = (double)s;
+        v32 = s;
+    }
+};
+
+template <typename T, int RT, int KIND>
+struct EngineOf {
+    using type = FfmaEngine<T, RT>;
+};
+template <int RT>
+struct EngineOf<float, RT, GK_TF32> {
+    using type = MmaEngine<RT, GK_TF32>;
+};
+template <int RT>
+struct EngineOf<float, RT, GK_BF16> {
+    using type = MmaEngine<RT, GK_BF16>;
+};
+
+template <typename T, int RT, bool VEC, int KIND>
+__global__ void __launch_bounds__(GramShape<T, RT, KIND>::NTH, 2)
+    gram_chunk_kernel(const SolveParams<T> P, const Batch<T> B) {
+    using Q = GramGeo<T, RT, KIND>;
+    using E = typename EngineOf<T, RT, KIND>::type;
+    constexpr int V = Q::V, G = Q::G, NG = Q::NG, KB = Q::KB, S = Q::S;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *hs = reinterpret_cast<T *>(smem_raw);
+    T *ws = hs + KB * S;
+    unsigned char *red = smem_raw + Q::stage_bytes;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int g = lane / G, lg = lane % G;
+    const int R = VEC ? RT : P.R;
+    const int tri = R * (R + 1) / 2;
+    const int64_t nb = __ldg(P.row_ptr + B.row0), ne = __ldg(P.row_ptr + B.row0 + B.nrows);
+    const int64_t last = B.row0 + B.nrows - 1;
+
+    // triangle entries this thread writes at a flush
+    constexpr int NE = E::DIRECT ? 1 : Q::EPT;
+    int er[NE], ec[NE];
+    if constexpr (!E::DIRECT) {
+#pragma unroll
+        for (int u = 0; u < NE; ++u) {
+            const int e = tid + u * Q::NTH;
+            if (e < tri) tri_rc(e, er[u], ec[u]);
+            else er[u] = ec[u] = 0;
+        }
+    }
+    E eng;
+    eng.init(tid);
+
+    for (int64_t cs = nb + (int64_t)blockIdx.x * B.ch; cs < ne; cs += (int64_t)gridDim.x * B.ch) {
+        const int64_t ce = min(cs + B.ch, ne);
+        int64_t i = search_le(P.row_ptr, B.row0, last, cs);
+        for (;;) {
+            const int64_t rs = __ldg(P.row_ptr + i), re = __ldg(P.row_ptr + i + 1);
+            const int64_t ss = max(rs, cs), se = min(re, ce);
+            T arow[V];
+            if (P.use_d2) load_slice<T, V, VEC>(arow, P.Ad, i, R, lg);
+            eng.zero();
+            for (int64_t base = ss; base < se; base += KB) {
+                // ---- gather KB nonzeros: h_e and weights
+#pragma unroll
+                for (int st = 0; st < Q::NSTEP; ++st) {
+                    const int slot = st * Q::BSTEP + w * NG + g;
+                    const bool valid = base + slot < se;
+                    const int64_t qq = valid ? base + slot : se - 1;
+                    T b[V], e[V], h[V];
+                    load_slice<T, V, VEC>(b, P.A1, __ldcs(P.c1 + qq), R, lg);
+                    load_slice<T, V, VEC>(e, P.A2, __ldcs(P.c2 + qq), R, lg);
+#pragma unroll
+                    for (int t = 0; t < V; ++t) h[t] = b[t] * e[t];
+                    T sw;
+                    if (P.use_d2) {
+                        T part = T(0);
+#pragma unroll
+                        for (int t = 0; t < V; ++t) part += arow[t] * h[t];
+                        const T m = group_sum<G>(part);
+                        T phi, d1, d2;
+                        bool ok = true;
+                        loss_terms(P.loss, __ldcs(P.t + qq), m, phi, d1, d2, ok);
+                        if (!ok && valid) record_error(P.status, TC_ERR_DOMAIN);
+                        sw = d2;
+                    } else {
+                        sw = weight_at(P.w, qq);
+                    }
+                    if (!valid) {
+                        sw = T(0);
+#pragma unroll
+                        for (int t = 0; t < V; ++t) h[t] = T(0);
+                    }
+#pragma unroll
+                    for (int t = 0; t < V; ++t) hs[slot * S + lg * V + t] = h[t];
+                    if (lg == 0) ws[slot] = sw;
+                }
+                __syncthreads();
+                eng.template accumulate<S>(hs, ws, (int)min((int64_t)KB, se - base));
+                __syncthreads();
+            }
+            // ---- flush the row's triangle
+            const bool whole = rs >= cs && re <= ce;
+            const int64_t slot = whole ? -1 : cut_slot(rs, re, nb, B.ch);
+            T *lrow = B.light + (i - B.row0) * (int64_t)tri;
+            double *crow = slot >= 0 ? B.cut + slot * (int64_t)tri : nullptr;
+            if constexpr (E::DIRECT) {
+                eng.flush(lrow, crow, whole, R);
+            } else {
+                // K groups reduced through `red` (the next flush writes `red`
+                // only after at least one stage, whose barriers order it
+                // after these reads)
+                eng.to_red(red);
+                __syncthreads();
+#pragma unroll
+                for (int u = 0; u < Q::EPT; ++u) {
+                    const int e = tid + u * Q::NTH;
+                    if (e < tri) {
+                        double v;
+                        float v32;
+                        eng.from_red(red, er[u], ec[u], v, v32);
+                        if (whole) lrow[e] = v32;
+                        else atomicAdd(crow + e, v);
+                    }
+                }
+            }
+            if (re >= ce) break;
+            i = search_le(P.row_ptr, i + 1, last, re);   // next nonempty row
+        }
+    }
+}
+
+// ------------------------------------------------------------------ kernel A, small ranks
+// For R <= 16 (FFMA form) every warp works alone: it takes every nwarps-th
+// chunk of the batch's nonzeros, stages DEPTH x NG nonzeros (h_e and weight)
+// in its own shared-memory region, and each lane accumulates a TR x TC block
+// of the full R x R Gram in registers (the whole square is 32 lanes x TR x TC
+// entries, so every entry has one owner and no reduction is needed; the
+// upper half is computed and dropped, which costs less than splitting the
+// triangle unevenly).  Sums are folded every 32 terms into compensated FP32
+// pairs as in the block form.  No block barrier anywhere: warps stall only
+// on their own gathers.
+template <typename T, int RT>
+struct WarpGram {
+    static constexpr int NW = 4, NTH = NW * 32;
+    using L = Lay<T, RT, 32>;
+    static constexpr int V = L::V, G = L::G, NG = L::NG;
+    static constexpr int DEPTH = 4;
+    static constexpr int KBW = NG * DEPTH;                 // nonzeros per warp stage
+    static constexpr int TC = RT >= 16 ? 4 : 2;            // lane block: TR rows x TC cols
+    static constexpr int TR = RT * RT / 32 / TC;
+    static constexpr int S = RT + (sizeof(T) == 4 ? 4 : 0);
+    static constexpr size_t warp_bytes = ((sizeof(T) * (KBW * S + KBW) + 15) / 16) * 16;
+    static constexpr size_t smem = NW * warp_bytes;
+    static constexpr bool COMP = sizeof(T) == 4;
+    static_assert(TR * TC * 32 == RT * RT, "the lanes cover the square");
+};
+
+template <typename T, int RT, bool VEC>
+__global__ void __launch_bounds__(128) gram_warp_kernel(const SolveParams<T> P, const Batch<T> B) {
+    using Q = WarpGram<T, RT>;
+    constexpr int V = Q::V, G = Q::G, NG = Q::NG, KBW = Q::KBW, S = Q::S, TR = Q::TR, TC = Q::TC;
+    constexpr int FB = 32;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    T *hs = reinterpret_cast<T *>(smem_raw + w * Q::warp_bytes);
+    T *ws = hs + KBW * S;
+    const int g = lane / G, lg = lane % G;
+    const int R = VEC ? RT : P.R;
+    const int tri = R * (R + 1) / 2;
+    const int r0 = (lane / (RT / TC)) * TR, c0 = (lane % (RT / TC)) * TC;
+    const int64_t nb = __ldg(P.row_ptr + B.row0), ne = __ldg(P.row_ptr + B.row0 + B.nrows);
+    const int64_t last = B.row0 + B.nrows - 1;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    T acc[TR][TC];
+    float hi[TR][TC], lo[TR][TC];
+    for (int64_t cs = nb + gw * B.ch; cs < ne; cs += nwarps * B.ch) {
+        const int64_t ce = min(cs + B.ch, ne);
+        int64_t i = search_le(P.row_ptr, B.row0, last, cs);
+        for (;;) {
+            const int64_t rs = __ldg(P.row_ptr + i), re = __ldg(P.row_ptr + i + 1);
+            const int64_t ss = max(rs, cs), se = min(re, ce);
+            T arow[V];
+            if (P.use_d2) load_slice<T, V, VEC>(arow, P.Ad, i, R, lg);
+#pragma unroll
+            for (int a = 0; a < TR; ++a)
+#pragma unroll
+                for (int b = 0; b < TC; ++b) {
+                    acc[a][b] = T(0);
+                    hi[a][b] = lo[a][b] = 0.f;
+                }
+            int cnt = 0;
+            for (int64_t base = ss; base < se; base += KBW) {
+#pragma unroll
+                for (int st = 0; st < Q::DEPTH; ++st) {
+                    const int slot = st * NG + g;
+                    const bool valid = base + slot < se;
+                    const int64_t qq = valid ? base + slot : se - 1;
+                    T b[V], e[V], h[V];
+                    load_slice<T, V, VEC>(b, P.A1, __ldcs(P.c1 + qq), R, lg);
+                    load_slice<T, V, VEC>(e, P.A2, __ldcs(P.c2 + qq), R, lg);
+#pragma unroll
+                    for (int t = 0; t < V; ++t) h[t] = b[t] * e[t];
+                    T sw;
+                    if (P.use_d2) {
+                        T part = T(0);
+#pragma unroll
+                        for (int t = 0; t < V; ++t) part += arow[t] * h[t];
+                        const T m = group_sum<G>(part);
+                        T phi, d1, d2;
+                        bool ok = true;
+                        loss_terms(P.loss, __ldcs(P.t + qq), m, phi, d1, d2, ok);
+                        if (!ok && valid) record_error(P.status, TC_ERR_DOMAIN);
+                        sw = d2;
+                    } else {
+                        sw = weight_at(P.w, qq);
+                    }
+                    if (!valid) {
+                        sw = T(0);
+#pragma unroll
+                        for (int t = 0; t < V; ++t) h[t] = T(0);
+                    }
+#pragma unroll
+                    for (int t = 0; t < V; ++t) hs[slot * S + lg * V + t] = h[t];
+                    if (lg == 0) ws[slot] = sw;
+                }
+                __syncwarp();
+                const int nvalid = (int)min((int64_t)KBW, se - base);
+                for (int k = 0; k < nvalid; ++k) {
+                    const T wk = ws[k];
+                    const T *hk = hs + k * S;
+                    T a[TR], c[TC];
+#pragma unroll
+                    for (int q = 0; q < TR; ++q) a[q] = wk * hk[r0 + q];
+#pragma unroll
+                    for (int q = 0; q < TC; ++q) c[q] = hk[c0 + q];
+#pragma unroll
+                    for (int x = 0; x < TR; ++x)
+#pragma unroll
+                        for (int y = 0; y < TC; ++y) acc[x][y] += a[x] * c[y];
+                    if constexpr (Q::COMP) {
+                        if (++cnt == FB) {
+                            cnt = 0;
+#pragma unroll
+                            for (int x = 0; x < TR; ++x)
+#pragma unroll
+                                for (int y = 0; y < TC; ++y) {
+                                    float s, er;
+                                    two_sum(hi[x][y], acc[x][y], s, er);
+                                    hi[x][y] = s;
+                                    lo[x][y] += er;
+                                    acc[x][y] = 0.f;
+                                }
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+            // ---- flush: each lane writes its own lower entries
+            const bool whole = rs >= cs && re <= ce;
+            const int64_t slot = whole ? -1 : cut_slot(rs, re, nb, B.ch);
+            T *lrow = B.light + (i - B.row0) * (int64_t)tri;
+            double *crow = slot >= 0 ? B.cut + slot * (int64_t)tri : nullptr;
+#pragma unroll
+            for (int x = 0; x < TR; ++x)
+#pragma unroll
+                for (int y = 0; y < TC; ++y) {
+                    const int r = r0 + x, c = c0 + y;
+                    if (c > r || r >= R) continue;
+                    const int e = tri_idx(r, c);
+                    if constexpr (Q::COMP) {
+                        float s, er;
+                        two_sum(hi[x][y], acc[x][y], s, er);
+                        const float l2 = lo[x][y] + er;
+                        if (whole) lrow[e] = s + l2;
+                        else atomicAdd(crow + e, (double)s + (double)l2);
+                    } else {
+                        if (whole) lrow[e] = acc[x][y];
+                        else atomicAdd(crow + e, (double)acc[x][y]);
+                    }
+                }
+            if (re >= ce) break;
+            i = search_le(P.row_ptr, i + 1, last, re);   // next nonempty row
+        }
+    }
+}
+
+// Gram entry e of batch row q (zero for an empty row).
+template <typename T>
+__device__ __forceinline__ double gram_entry(const T *lrow, const double *crow, int e) {
+    if (crow) return crow[e];
+    if (lrow) return (double)lrow[e];
+    return 0.0;
+}
+
+template <typename T>
+__device__ __forceinline__ void gram_source(const SolveParams<T> &P, const Batch<T> &B, int64_t nb,
+                                            int64_t i, int tri, const T *&lrow,
+                                            const double *&crow) {
+    const int64_t rs = __ldg(P.row_ptr + i), re = __ldg(P.row_ptr + i + 1);
+    lrow = nullptr;
+    crow = nullptr;
+    if (re == rs) return;
+    const int64_t slot = cut_slot(rs, re, nb, B.ch);
+    if (slot >= 0) crow = B.cut + slot * (int64_t)tri;
+    else lrow = B.light + (i - B.row0) * (int64_t)tri;
+}
+
+// ------------------------------------------------------------------ kernel B, R <= 32
+// One row per lane, rpw rows per warp.  Shared layout: packed entry e of slot
+// s at e * (rpw + 1) + s (the pad keeps the transposing loads and the per-lane
+// accesses on distinct banks).  With refinement the factor L is written back
+// over the batch's Gram rows (pattern dtype; a zero first entry marks a row
+// that did not factor) for the correction step.
+template <typename T>
+__global__ void __launch_bounds__(32) chol_rows_kernel(const SolveParams<T> P, const Batch<T> B,
+                                                       int rpw) {
+    extern __shared__ __align__(16) double sh[];
+    const int lane = threadIdx.x;
+    const int R = P.R, tri = R * (R + 1) / 2, ps = rpw + 1;
+    const int64_t grp = blockIdx.x;
+    const int64_t nb = __ldg(P.row_ptr + B.row0);
+    double *Tri = sh;
+    double *Vv = sh + (int64_t)tri * ps;
+    double *Dinv = Vv + (int64_t)R * ps;
+    for (int s = 0; s < rpw; ++s) {
+        const int64_t q = grp * rpw + s;
+        if (q >= B.nrows) break;
+        const T *lrow;
+        const double *crow;
+        gram_source(P, B, nb, B.row0 + q, tri, lrow, crow);
+        for (int e = lane; e < tri; e += 32) Tri[e * ps + s] = gram_entry(lrow, crow, e);
+    }
+    __syncwarp();
+    const int slot = lane;
+    const bool mine = slot < rpw && grp * rpw + slot < B.nrows;
+    const int64_t i = B.row0 + grp * rpw + slot;
+#define TC_TRI(r, c) Tri[tri_idx(r, c) * ps + slot]
+#define TC_VEC(r) Vv[(r) * ps + slot]
+#define TC_DINV(r) Dinv[(r) * ps + slot]
+    if (mine) {
+        for (int r = 0; r < R; ++r) TC_TRI(r, r) += P.lambda;
+        bool ok = true;
+        for (int j = 0; j < R; ++j) {
+            const double dj = TC_TRI(j, j);
+            if (!(dj > 0.0)) {
+                ok = false;
+                break;
+            }
+            const double inv = rsqrt_nr(dj), ljj = dj * inv;
+            TC_TRI(j, j) = ljj;
+            TC_DINV(j) = inv;
+            for (int r = j + 1; r < R; ++r) TC_TRI(r, j) *= inv;
+            for (int r = j + 1; r < R; ++r) {
+                const double lrj = TC_TRI(r, j);
+                // four entries per pass, loads before stores (independent FMAs)
+                int k = j + 1;
+                for (; k + 3 <= r; k += 4) {
+                    const double a0 = TC_TRI(r, k), a1 = TC_TRI(r, k + 1), a2 = TC_TRI(r, k + 2),
+                                 a3 = TC_TRI(r, k + 3);
+                    const double b0 = TC_TRI(k, j), b1 = TC_TRI(k + 1, j), b2 = TC_TRI(k + 2, j),
+                                 b3 = TC_TRI(k + 3, j);
+                    TC_TRI(r, k) = a0 - lrj * b0;
+                    TC_TRI(r, k + 1) = a1 - lrj * b1;
+                    TC_TRI(r, k + 2) = a2 - lrj * b2;
+                    TC_TRI(r, k + 3) = a3 - lrj * b3;
+                }
+                for (; k <= r; ++k) TC_TRI(r, k) -= lrj * TC_TRI(k, j);
+            }
+        }
+        if (!ok) {
+            record_error(P.status, TC_ERR_NOT_SPD);
+            if (P.row_status) P.row_status[i] = 1;
+            if (P.pinv) {  // an identity block keeps the preconditioner defined
+                T *Po = P.pinv + i * (int64_t)R * R;
+                for (int q = 0; q < R * R; ++q) Po[q] = (q / R == q % R) ? T(1) : T(0);
+            }
+            TC_TRI(0, 0) = 0.0;
+        } else {
+            if (P.row_status) P.row_status[i] = 0;
+            if (!P.pinv) {
+                for (int r = 0; r < R; ++r) {           // L y = b
+                    double v0 = (double)P.rhs[i * (int64_t)R + r], v1 = 0.0, v2 = 0.0, v3 = 0.0;
+                    int k = 0;
+                    for (; k + 3 < r; k += 4) {
+                        v0 -= TC_TRI(r, k) * TC_VEC(k);
+                        v1 -= TC_TRI(r, k + 1) * TC_VEC(k + 1);
+                        v2 -= TC_TRI(r, k + 2) * TC_VEC(k + 2);
+                        v3 -= TC_TRI(r, k + 3) * TC_VEC(k + 3);
+                    }
+                    for (; k < r; ++k) v0 -= TC_TRI(r, k) * TC_VEC(k);
+                    TC_VEC(r) = ((v0 + v1) + (v2 + v3)) * TC_DINV(r);
+                }
+                for (int r = R - 1; r >= 0; --r) {      // L^T x = y
+                    double v0 = TC_VEC(r), v1 = 0.0, v2 = 0.0, v3 = 0.0;
+                    int k = r + 1;
+                    for (; k + 3 < R; k += 4) {
+                        v0 -= TC_TRI(k, r) * TC_VEC(k);
+                        v1 -= TC_TRI(k + 1, r) * TC_VEC(k + 1);
+                        v2 -= TC_TRI(k + 2, r) * TC_VEC(k + 2);
+                        v3 -= TC_TRI(k + 3, r) * TC_VEC(k + 3);
+                    }
+                    for (; k < R; ++k) v0 -= TC_TRI(k, r) * TC_VEC(k);
+                    TC_VEC(r) = ((v0 + v1) + (v2 + v3)) * TC_DINV(r);
+                }
+                for (int r = 0; r < R; ++r) P.out[i * (int64_t)R + r] = (T)TC_VEC(r);
+            } else {
+                // L^-1 in place, column by column: for r > j, L^-1[r][j] =
+                // -(sum_{k=j}^{r-1} L[r][k] L^-1[k][j]) / L[r][r]; columns > j still hold L.
+                for (int j = 0; j < R; ++j) {
+                    TC_TRI(j, j) = TC_DINV(j);
+                    for (int r = j + 1; r < R; ++r) {
+                        double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+                        int k = j;
+                        for (; k + 3 < r; k += 4) {
+                            v0 += TC_TRI(r, k) * TC_TRI(k, j);
+                            v1 += TC_TRI(r, k + 1) * TC_TRI(k + 1, j);
+                            v2 += TC_TRI(r, k + 2) * TC_TRI(k + 2, j);
+                            v3 += TC_TRI(r, k + 3) * TC_TRI(k + 3, j);
+                        }
+                        for (; k < r; ++k) v0 += TC_TRI(r, k) * TC_TRI(k, j);
+                        TC_TRI(r, j) = -((v0 + v1) + (v2 + v3)) * TC_DINV(r);
+                    }
+                }
+                // (L L^T)^-1 [r][c] = sum_{k >= max(r, c)} L^-1[k][r] L^-1[k][c]
+                T *Po = P.pinv + i * (int64_t)R * R;
+                for (int r = 0; r < R; ++r)
+                    for (int c = 0; c <= r; ++c) {
+                        double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+                        int k = r;
+                        for (; k + 3 < R; k += 4) {
+                            v0 += TC_TRI(k, r) * TC_TRI(k, c);
+                            v1 += TC_TRI(k + 1, r) * TC_TRI(k + 1, c);
+                            v2 += TC_TRI(k + 2, r) * TC_TRI(k + 2, c);
+                            v3 += TC_TRI(k + 3, r) * TC_TRI(k + 3, c);
+                        }
+                        for (; k < R; ++k) v0 += TC_TRI(k, r) * TC_TRI(k, c);
+                        const double v = (v0 + v1) + (v2 + v3);
+                        Po[r * R + c] = (T)v;
+                        Po[c * R + r] = (T)v;
+                    }
+            }
+        }
+    }
+#undef TC_TRI
+#undef TC_VEC
+#undef TC_DINV
+    if (P.refine) {   // the factors, back over the Gram rows (coalesced per row)
+        __syncwarp();
+        for (int s = 0; s < rpw; ++s) {
+            const int64_t q = grp * rpw + s;
+            if (q >= B.nrows) break;
+            T *lrow = B.light + q * (int64_t)tri;
+            for (int e = lane; e < tri; e += 32) lrow[e] = (T)Tri[e * ps + s];
+        }
+    }
+}
+
+// ------------------------------------------------------------------ kernel B, R > 32
+// One warp per row (grid-stride), FP64 packed triangle in shared memory.  The
+// trailing update of step j touches the packed triangle of rows and columns
+// j+1 .. R-1; its entries are dealt to the lanes in packed order through a
+// decode table (rr, kk) shared by the block, so every lane does the same work.
+constexpr int kCholWarps = 4;
+
+template <typename T>
+__global__ void __launch_bounds__(kCholWarps * 32) chol_warp_kernel(const SolveParams<T> P,
+                                                                    const Batch<T> B) {
+    extern __shared__ __align__(16) double sh[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int R = P.R, tri = R * (R + 1) / 2;
+    const bool inv_mode = P.pinv != nullptr;
+    const int per_warp = tri * (inv_mode ? 2 : 1) + 2 * R;
+    uint32_t *tab = reinterpret_cast<uint32_t *>(sh + (size_t)kCholWarps * per_warp);
+    for (int e = threadIdx.x; e < tri; e += blockDim.x) {
+        int r, c;
+        tri_rc(e, r, c);
+        tab[e] = ((uint32_t)r << 16) | (uint32_t)c;
+    }
+    __syncthreads();
+    double *S = sh + (size_t)w * per_warp;
+    double *Y = S + tri;                         // L^-1 (inverse mode)
+    double *bv = S + tri * (inv_mode ? 2 : 1);
+    double *Dinv = bv + R;
+    const int64_t nb = __ldg(P.row_ptr + B.row0);
+    for (int64_t q = (int64_t)blockIdx.x * kCholWarps + w; q < B.nrows;
+         q += (int64_t)gridDim.x * kCholWarps) {
+        const int64_t i = B.row0 + q;
+        const T *lrow;
+        const double *crow;
+        gram_source(P, B, nb, i, tri, lrow, crow);
+        for (int e = lane; e < tri; e += 32) S[e] = gram_entry(lrow, crow, e);
+        __syncwarp();
+        for (int r = lane; r < R; r += 32) S[tri_idx(r, r)] += P.lambda;
+        __syncwarp();
+        bool ok = true;
+        for (int j = 0; j < R; ++j) {
+            const double dj = S[tri_idx(j, j)];
+            if (!(dj > 0.0)) {       // same value in every lane: a uniform exit
+                ok = false;
+                break;
+            }
+            const double inv = rsqrt_nr(dj), ljj = dj * inv;
+            __syncwarp();
+            for (int r = j + 1 + lane; r < R; r += 32) S[tri_idx(r, j)] *= inv;
+            if (lane == 0) {
+                S[tri_idx(j, j)] = ljj;
+                Dinv[j] = inv;
+            }
+            __syncwarp();
+            const int nr = R - 1 - j, ntr = nr * (nr + 1) / 2;
+            for (int e = lane; e < ntr; e += 32) {
+                const uint32_t rc = tab[e];
+                const int r = j + 1 + (int)(rc >> 16), k = j + 1 + (int)(rc & 0xffffu);
+                S[tri_idx(r, k)] -= S[tri_idx(r, j)] * S[tri_idx(k, j)];
+            }
+            __syncwarp();
+        }
+        T *lout = B.light + q * (int64_t)tri;   // the factor, for the correction step
+        if (!ok) {
+            if (lane == 0) {
+                record_error(P.status, TC_ERR_NOT_SPD);
+                if (P.row_status) P.row_status[i] = 1;
+                if (P.refine) lout[0] = T(0);
+            }
+            if (inv_mode) {
+                T *Po = P.pinv + i * (int64_t)R * R;
+                for (int e = lane; e < R * R; e += 32) Po[e] = (e / R == e % R) ? T(1) : T(0);
+            }
+            __syncwarp();
+            continue;
+        }
+        if (lane == 0 && P.row_status) P.row_status[i] = 0;
+        if (!inv_mode) {
+            if (P.refine)
+                for (int e = lane; e < tri; e += 32) lout[e] = (T)S[e];
+            for (int r = lane; r < R; r += 32) bv[r] = (double)P.rhs[i * (int64_t)R + r];
+            __syncwarp();
+            for (int j = 0; j < R; ++j) {        // L y = b
+                const double yj = bv[j] * Dinv[j];
+                __syncwarp();
+                for (int r = j + 1 + lane; r < R; r += 32) bv[r] -= S[tri_idx(r, j)] * yj;
+                if (lane == 0) bv[j] = yj;
+                __syncwarp();
+            }
+            for (int j = R - 1; j >= 0; --j) {   // L^T x = y
+                const double xj = bv[j] * Dinv[j];
+                __syncwarp();
+                for (int r = lane; r < j; r += 32) bv[r] -= S[tri_idx(j, r)] * xj;
+                if (lane == 0) bv[j] = xj;
+                __syncwarp();
+            }
+            for (int r = lane; r < R; r += 32) P.out[i * (int64_t)R + r] = (T)bv[r];
+            __syncwarp();
+            continue;
+        }
+        // L^-1 into Y, one column per lane (columns c and R - 1 - c pair up
+        // a long and a short column): for r > c,
+        // L^-1[r][c] = -(sum_{k=c}^{r-1} L[r][k] L^-1[k][c]) / L[r][r]
+        for (int pass = 0; pass < 2; ++pass) {
+            const int c = pass == 0 ? lane : R - 1 - lane;
+            if (c < 0 || c >= R || (pass == 1 && c < 32)) continue;
+            Y[tri_idx(c, c)] = Dinv[c];
+            for (int r = c + 1; r < R; ++r) {
+                double v = 0.0;
+                for (int k = c; k < r; ++k) v += S[tri_idx(r, k)] * Y[tri_idx(k, c)];
+                Y[tri_idx(r, c)] = -v * Dinv[r];
+            }
+        }
+        __syncwarp();
+        // (L L^T)^-1 [r][c] = sum_{k >= r} L^-1[k][r] L^-1[k][c], c <= r
+        T *Po = P.pinv + i * (int64_t)R * R;
+        for (int e = lane; e < tri; e += 32) {
+            const uint32_t rc = tab[e];
+            const int r = (int)(rc >> 16), c = (int)(rc & 0xffffu);
+            double v = 0.0;
+            for (int k = r; k < R; ++k) v += Y[tri_idx(k, r)] * Y[tri_idx(k, c)];
+            Po[r * R + c] = (T)v;
+            Po[c * R + r] = (T)v;
         }
         __syncwarp();
     }
 }
 
-// ------------------------------------------------------------------ two-kernel path, R <= 32
-// Kernel A forms the Gram matrices: one block of W warps per row, the warps
-// splitting the row's nonzeros (every W-th batch), their partial Grams summed
-// in shared memory and written as packed FP64 lower triangles, plus lambda on
-// the diagonal, to a scratch buffer.  Kernel B runs the FP64 part with one row
-// per lane and RPW rows per warp: the unpivoted Cholesky factorization, then
-// either the two triangular solves or the inverse (L L^T)^-1 = L^-T L^-1.  One
-// row per lane makes every FP64 instruction do a full warp of useful work, and
-// many independent warps overlap the long dependence chains.
-//
-// Scratch layout (shared by both kernels): row q of the batch keeps packed
-// entry e = r (r + 1) / 2 + c at ((q / RPW) * TRI + e) * RPW + q % RPW.
-template <typename T, int RT>
-struct GramCfg {
-    static constexpr int W = 4;
-    static constexpr bool MMA = sizeof(T) == 4;               // FP32: tensor-core Gram
-    static constexpr int NG = Lay<T, RT, 32>::NG;
-    static constexpr size_t stage_elems = MMA ? MmaGram<RT>::stage_floats : (size_t)(NG * RT + NG);
-    static constexpr size_t stage_per_warp = ((sizeof(T) * stage_elems + 15) / 16) * 16;
-    static constexpr size_t dense_off = W * stage_per_warp;
-    static constexpr size_t bytes = dense_off + (size_t)W * RT * RT * sizeof(T);
-};
-
+// ------------------------------------------------------------------ refinement (kernels C, D)
+// One step of iterative refinement of the solved rows a_i (in `out`):
+//   res_i = rhs_i - lambda a_i - sum_{e in row i} s_e h_e (h_e^T a_i),
+//   a_i  += (L_i L_i^T)^-1 res_i,
+// with L_i the row's Cholesky factor.  Kernel C accumulates the sum over the
+// nonzeros in FP64 (h_e formed in FP64 from the stored factors, so exactly
+// for FP32 data) with the same chunked traversal as the Gram (a warp per
+// chunk, FP64 atomics into a zeroed buffer).  Kernel D forms res_i and applies
+// the correction with the stored factor, one warp per row.
 template <typename T, int RT, bool VEC>
-__global__ void __launch_bounds__(128) gram_rows_kernel(const SolveParams<T> P, int64_t row0,
-                                                        int64_t nrows, int rpw, double *gram) {
-    using C = GramCfg<T, RT>;
-    using GL = GramLay<RT>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    T *stage = reinterpret_cast<T *>(smem_raw + w * C::stage_per_warp);
-    T *dense = reinterpret_cast<T *>(smem_raw + C::dense_off);
-    T *mine = dense + w * RT * RT;
+__global__ void __launch_bounds__(128) refine_resid_kernel(const SolveParams<T> P, const Batch<T> B,
+                                                           int64_t ch) {
+    using L = Lay<T, RT, 32>;
+    constexpr int V = L::V, G = L::G, NG = L::NG;
+    const int lane = threadIdx.x & 31;
+    const int g = lane / G, lg = lane % G;
     const int R = VEC ? RT : P.R;
-    const int tri = R * (R + 1) / 2;
-    for (int64_t q = blockIdx.x; q < nrows; q += gridDim.x) {
-        const int64_t i = row0 + q;
-        if constexpr (C::MMA) {
-            using MG = MmaGram<RT>;
-            float d[MG::MT][MG::NT][4];
-            gram_row_mma<RT, VEC>(reinterpret_cast<const SolveParams<float> &>(P), i,
-                                  reinterpret_cast<float *>(stage), d, w, C::W);
-            const int gid = lane >> 2, tig = lane & 3;
+    const int64_t nb = __ldg(P.row_ptr + B.row0), ne = __ldg(P.row_ptr + B.row0 + B.nrows);
+    const int64_t last = B.row0 + B.nrows - 1;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t cs = nb + wid * ch; cs < ne; cs += nwarps * ch) {
+        const int64_t ce = min(cs + ch, ne);
+        int64_t i = search_le(P.row_ptr, B.row0, last, cs);
+        for (;;) {
+            const int64_t rs = __ldg(P.row_ptr + i), re = __ldg(P.row_ptr + i + 1);
+            const int64_t ss = max(rs, cs), se = min(re, ce);
+            T a32[V];
+            load_slice<T, V, false>(a32, P.out, i, R, lg);
+            double av[V], acc[V];
 #pragma unroll
-            for (int mt = 0; mt < MG::MT; ++mt)
+            for (int t = 0; t < V; ++t) {
+                av[t] = (double)a32[t];
+                acc[t] = 0.0;
+            }
+            for (int64_t base = ss; base < se; base += NG) {
+                const bool valid = base + g < se;
+                const int64_t qq = valid ? base + g : se - 1;
+                T b[V], e[V];
+                load_slice<T, V, VEC>(b, P.A1, __ldcs(P.c1 + qq), R, lg);
+                load_slice<T, V, VEC>(e, P.A2, __ldcs(P.c2 + qq), R, lg);
+                double h[V], part = 0.0;
 #pragma unroll
-                for (int nt = 0; nt < MG::NT; ++nt)
+                for (int t = 0; t < V; ++t) {
+                    h[t] = (double)b[t] * (double)e[t];
+                    part += h[t] * av[t];
+                }
+                const double z = group_sum<G>(part);
+                const double coef = valid ? (double)weight_at(P.w, qq) * z : 0.0;
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int r = mt * 16 + gid + (e >= 2 ? 8 : 0);
-                        const int c = nt * 8 + tig * 2 + (e & 1);
-                        if (r < RT) mine[r * RT + c] = d[mt][nt][e];
-                    }
-        } else {
-            T acc[GL::RPL][GL::CPL];
-            gram_row<T, RT, VEC>(P, i, stage, stage + C::NG * RT, acc, w, C::W);
-            const int r0 = (lane / GL::LPR) * GL::RPL, cb = (lane % GL::LPR) * GL::CPL;
+                for (int t = 0; t < V; ++t) acc[t] += coef * h[t];
+            }
 #pragma unroll
-            for (int a = 0; a < GL::RPL; ++a)
+            for (int t = 0; t < V; ++t) acc[t] = across_groups<G>(acc[t]);
+            if (g == 0) {
+                double *dst = B.res + (i - B.row0) * (int64_t)R + lg * V;
 #pragma unroll
-                for (int bb = 0; bb < GL::CPL; ++bb) mine[(r0 + a) * RT + cb + bb] = acc[a][bb];
+                for (int t = 0; t < V; ++t)
+                    if (lg * V + t < R) atomicAdd(dst + t, -acc[t]);
+            }
+            if (re >= ce) break;
+            i = search_le(P.row_ptr, i + 1, last, re);   // next nonempty row
         }
-        __syncthreads();
-        double *dst = gram + (q / rpw) * (int64_t)tri * rpw + q % rpw;
-        for (int e = threadIdx.x; e < tri; e += blockDim.x) {
-            int r = (int)((sqrtf(8.f * e + 1.f) - 1.f) * 0.5f);
-            while (r * (r + 1) / 2 > e) --r;
-            while ((r + 1) * (r + 2) / 2 <= e) ++r;
-            const int c = e - r * (r + 1) / 2;
-            double v = 0.0;
-#pragma unroll
-            for (int ww = 0; ww < C::W; ++ww) v += (double)dense[ww * RT * RT + r * RT + c];
-            if (r == c) v += P.lambda;
-            dst[(int64_t)e * rpw] = v;
-        }
-        __syncthreads();
     }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(32) chol_rows_kernel(const SolveParams<T> P, int64_t row0,
-                                                       int64_t nrows, int rpw, const double *gram) {
-    extern __shared__ __align__(16) double sh[];
-    const int lane = threadIdx.x;
+__global__ void __launch_bounds__(kCholWarps * 32) refine_correct_kernel(const SolveParams<T> P,
+                                                                         const Batch<T> B) {
+    __shared__ T rv[kCholWarps][TC_MAX_RANK];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int R = P.R, tri = R * (R + 1) / 2;
-    const int64_t grp = blockIdx.x;
-    double *Tri = sh;
-    double *Vv = sh + (int64_t)tri * rpw;
-    double *Dinv = Vv + (int64_t)R * rpw;
-    const double *src = gram + grp * (int64_t)tri * rpw;
-    for (int e = lane; e < tri * rpw; e += 32) Tri[e] = src[e];
-    __syncwarp();
-    const int slot = lane;
-    if (slot >= rpw || grp * rpw + slot >= nrows) return;
-    const int64_t i = row0 + grp * rpw + slot;
-#define TC_TRI(r, c) Tri[((r) * ((r) + 1) / 2 + (c)) * rpw + slot]
-#define TC_VEC(r) Vv[(r) * rpw + slot]
-#define TC_DINV(r) Dinv[(r) * rpw + slot]
-    bool ok = true;
-    for (int j = 0; j < R; ++j) {
-        const double dj = TC_TRI(j, j);
-        if (!(dj > 0.0)) {
-            ok = false;
-            break;
+    T *v = rv[w];
+    for (int64_t q = (int64_t)blockIdx.x * kCholWarps + w; q < B.nrows;
+         q += (int64_t)gridDim.x * kCholWarps) {
+        const int64_t i = B.row0 + q;
+        const T *Lq = B.light + q * (int64_t)tri;
+        if (!((double)Lq[0] > 0.0)) continue;   // the row did not factor (uniform)
+        for (int r = lane; r < R; r += 32) {
+            const double a = (double)P.out[i * (int64_t)R + r];
+            v[r] = (T)((double)P.rhs[i * (int64_t)R + r] - P.lambda * a +
+                       B.res[q * (int64_t)R + r]);
         }
-        const double ljj = sqrt(dj), inv = 1.0 / ljj;
-        TC_TRI(j, j) = ljj;
-        TC_DINV(j) = inv;
-        for (int r = j + 1; r < R; ++r) TC_TRI(r, j) *= inv;
-        for (int r = j + 1; r < R; ++r) {
-            const double lrj = TC_TRI(r, j);
-            for (int k = j + 1; k <= r; ++k) TC_TRI(r, k) -= lrj * TC_TRI(k, j);
+        __syncwarp();
+        for (int j = 0; j < R; ++j) {          // L y = res
+            const T yj = v[j] / Lq[tri_idx(j, j)];
+            __syncwarp();
+            for (int r = j + 1 + lane; r < R; r += 32) v[r] -= Lq[tri_idx(r, j)] * yj;
+            if (lane == 0) v[j] = yj;
+            __syncwarp();
         }
+        for (int j = R - 1; j >= 0; --j) {     // L^T d = y
+            const T dj = v[j] / Lq[tri_idx(j, j)];
+            __syncwarp();
+            for (int r = lane; r < j; r += 32) v[r] -= Lq[tri_idx(j, r)] * dj;
+            if (lane == 0) v[j] = dj;
+            __syncwarp();
+        }
+        for (int r = lane; r < R; r += 32) {
+            T *o = P.out + i * (int64_t)R + r;
+            *o = (T)((double)*o + (double)v[r]);
+        }
+        __syncwarp();
     }
-    if (!ok) {
-        record_error(P.status, TC_ERR_NOT_SPD);
-        if (P.row_status) P.row_status[i] = 1;
-        if (P.pinv) {  // an identity block keeps the preconditioner defined
-            T *Po = P.pinv + i * (int64_t)R * R;
-            for (int q = 0; q < R * R; ++q) Po[q] = (q / R == q % R) ? T(1) : T(0);
-        }
-        return;
-    }
-    if (P.row_status) P.row_status[i] = 0;
-    if (!P.pinv) {
-        for (int r = 0; r < R; ++r) {           // L y = b
-            double v = (double)P.rhs[i * (int64_t)R + r];
-            for (int k = 0; k < r; ++k) v -= TC_TRI(r, k) * TC_VEC(k);
-            TC_VEC(r) = v * TC_DINV(r);
-        }
-        for (int r = R - 1; r >= 0; --r) {      // L^T x = y
-            double v = TC_VEC(r);
-            for (int k = r + 1; k < R; ++k) v -= TC_TRI(k, r) * TC_VEC(k);
-            TC_VEC(r) = v * TC_DINV(r);
-        }
-        for (int r = 0; r < R; ++r) P.out[i * (int64_t)R + r] = (T)TC_VEC(r);
-        return;
-    }
-    // L^-1 in place, column by column: for r > j,
-    // L^-1[r][j] = -(sum_{k=j}^{r-1} L[r][k] L^-1[k][j]) / L[r][r]; columns > j still hold L.
-    for (int j = 0; j < R; ++j) {
-        TC_TRI(j, j) = TC_DINV(j);
-        for (int r = j + 1; r < R; ++r) {
-            double v = 0.0;
-            for (int k = j; k < r; ++k) v += TC_TRI(r, k) * TC_TRI(k, j);
-            TC_TRI(r, j) = -v * TC_DINV(r);
-        }
-    }
-    // (L L^T)^-1 [r][c] = sum_{k >= max(r, c)} L^-1[k][r] L^-1[k][c]
-    T *Po = P.pinv + i * (int64_t)R * R;
-    for (int r = 0; r < R; ++r)
-        for (int c = 0; c <= r; ++c) {
-            double v = 0.0;
-            for (int k = r; k < R; ++k) v += TC_TRI(k, r) * TC_TRI(k, c);
-            Po[r * R + c] = (T)v;
-            Po[c * R + r] = (T)v;
-        }
-#undef TC_TRI
-#undef TC_VEC
-#undef TC_DINV
 }
 
-template <typename T, int RT, bool VEC>
-static tc_status launch_solve_two(const SolveParams<T> &P, cudaStream_t st) {
-    using C = GramCfg<T, RT>;
+// ------------------------------------------------------------------ host side
+static int device_sms() {
+    static int sms[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+    if (!sms[dev]) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0)
+            v = 152;
+        sms[dev] = v;
+    }
+    return sms[dev];
+}
+
+// Process-wide tuning per dtype and rank tier (0 = automatic).
+static tc_solve_tuning g_tuning[2][4];
+
+static int tier_slot(int tier) { return tier <= 8 ? 0 : tier <= 16 ? 1 : tier <= 32 ? 2 : 3; }
+
+// Nonzeros per chunk: about eight chunks per resident block, a power of two
+// in [256, 16384], unless tuned.
+static int64_t chunk_nnz(int64_t m, int64_t grid, const tc_solve_tuning &t) {
+    if (t.chunk_nnz > 0) return t.chunk_nnz;
+    int64_t want = m / (8 * grid);
+    int64_t ch = 256;
+    while (ch < want && ch < 16384) ch <<= 1;
+    return ch;
+}
+
+template <typename T, int RT, bool VEC, int KIND>
+static tc_status launch_solve_rt(const SolveParams<T> &P, int64_t m, cudaStream_t st) {
+    using Q = GramGeo<T, RT, KIND>;
     const int R = P.R, tri = R * (R + 1) / 2;
-    const int rpw = RT <= 16 ? 32 : 16;                     // rows per warp in kernel B
-    // rows per batch: scratch of at most 256 MB, a multiple of rpw
-    int64_t batch = ((int64_t)256 << 20) / ((int64_t)tri * 8);
-    batch = batch / rpw * rpw;
-    if (batch < rpw) batch = rpw;
-    if (batch > P.I) batch = (P.I + rpw - 1) / rpw * rpw;
-    double *gram = nullptr;
-    TC_CUDA(cudaMallocAsync((void **)&gram, sizeof(double) * tri * batch, st));
-    auto ka = gram_rows_kernel<T, RT, VEC>;
-    if (C::bytes > 48 * 1024)
-        TC_CUDA(cudaFuncSetAttribute(ka, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::bytes));
-    const size_t smem_b = sizeof(double) * (size_t)(tri + 2 * R) * rpw;
-    auto kb = chol_rows_kernel<T>;
-    if (smem_b > 48 * 1024)
+    const int sms = device_sms();
+    auto ka = gram_chunk_kernel<T, RT, VEC, (KIND == GK_FFMA && RT <= 16) ? GK_FFMA : KIND>;
+    static int occ_a = 0;
+    if (!(KIND == GK_FFMA && RT <= 16) && !occ_a) {
+        if (Q::smem > 48 * 1024)
+            TC_CUDA(cudaFuncSetAttribute(ka, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Q::smem));
+        int v = 0;
+        TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, ka, Q::NTH, Q::smem));
+        occ_a = v > 0 ? v : 1;
+    }
+    const tc_solve_tuning tun = g_tuning[sizeof(T) == 8 ? 1 : 0][tier_slot(RT)];
+    // small ranks, FFMA form: one warp per chunk (gram_warp_kernel)
+    constexpr bool WARP_A = KIND == GK_FFMA && RT <= 16;
+    static int occ_w = 0;
+    if constexpr (WARP_A) {
+        using QW = WarpGram<T, RT>;
+        if (!occ_w) {
+            auto kaw = gram_warp_kernel<T, RT, VEC>;
+            if (QW::smem > 48 * 1024)
+                TC_CUDA(cudaFuncSetAttribute(kaw, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)QW::smem));
+            int v = 0;
+            TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kaw, QW::NTH, QW::smem));
+            occ_w = v > 0 ? v : 1;
+        }
+    }
+    const int64_t grid_a = (int64_t)sms * (WARP_A ? occ_w : occ_a);
+    const int64_t ch = chunk_nnz(m, WARP_A ? grid_a * 4 : grid_a, tun);
+    const int64_t ch_c = ch / 4 > 64 ? ch / 4 : 64;    // refinement: a warp per chunk
+
+    const bool warp_b = RT > 32;
+    const int rpw = RT <= 16 ? 32 : 16;
+    const int align = warp_b ? kCholWarps : rpw;
+    size_t smem_b;
+    if (warp_b)
+        smem_b = sizeof(double) * (size_t)kCholWarps * (tri * (P.pinv ? 2 : 1) + 2 * R) +
+                 sizeof(uint32_t) * tri;
+    else
+        smem_b = sizeof(double) * (size_t)(tri + 2 * R) * (rpw + 1);
+    if (warp_b) {
+        auto kb = chol_warp_kernel<T>;
         TC_CUDA(cudaFuncSetAttribute(kb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b));
-    for (int64_t row0 = 0; row0 < P.I; row0 += batch) {
-        const int64_t n = min(batch, P.I - row0);
-        ka<<<(unsigned)n, C::W * 32, C::bytes, st>>>(P, row0, n, rpw, gram);
-        kb<<<(unsigned)((n + rpw - 1) / rpw), 32, smem_b, st>>>(P, row0, n, rpw, gram);
-        count_launch(2);
+    } else if (smem_b > 48 * 1024) {
+        auto kb = chol_rows_kernel<T>;
+        TC_CUDA(cudaFuncSetAttribute(kb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b));
     }
-    TC_CUDA(cudaFreeAsync(gram, st));
-    return TC_OK;
+
+    // rows per batch: Gram triangles of at most 1 GiB (or as tuned)
+    const int64_t budget = tun.batch_bytes > 0 ? tun.batch_bytes : ((int64_t)1 << 30);
+    int64_t batch = budget / ((int64_t)tri * (int64_t)sizeof(T));
+    batch = batch / align * align;
+    if (batch < align) batch = align;
+    if (batch > P.I) batch = P.I;
+    const int64_t slots = (m + ch - 1) / ch + 1;
+    T *light = nullptr;
+    double *cut = nullptr, *res = nullptr;
+    TC_CUDA(cudaMallocAsync((void **)&light, sizeof(T) * (size_t)tri * batch, st));
+    if (cudaMallocAsync((void **)&cut, sizeof(double) * (size_t)tri * slots, st) != cudaSuccess ||
+        (P.refine && cudaMallocAsync((void **)&res, sizeof(double) * (size_t)R * batch, st) != cudaSuccess)) {
+        if (cut) cudaFreeAsync(cut, st);
+        cudaFreeAsync(light, st);
+        return TC_ERR_OOM;
+    }
+    const int64_t nblk_w0 = (int64_t)sms * 16;
+    for (int64_t row0 = 0; row0 < P.I; row0 += batch) {
+        Batch<T> Bt{row0, min(batch, P.I - row0), ch, light, cut, res};
+        int64_t zb = (slots * tri + 255) / 256;
+        if (zb > (int64_t)sms * 4) zb = (int64_t)sms * 4;
+        if (zb < 1) zb = 1;
+        zero_cut_kernel<T><<<(unsigned)zb, 256, 0, st>>>(P.row_ptr, Bt, tri);
+        if constexpr (WARP_A)
+            gram_warp_kernel<T, RT, VEC><<<(unsigned)grid_a, WarpGram<T, RT>::NTH,
+                                           WarpGram<T, RT>::smem, st>>>(P, Bt);
+        else
+            ka<<<(unsigned)grid_a, Q::NTH, Q::smem, st>>>(P, Bt);
+        int64_t nblk_w = (Bt.nrows + kCholWarps - 1) / kCholWarps;
+        if (nblk_w > nblk_w0) nblk_w = nblk_w0;
+        if (warp_b)
+            chol_warp_kernel<T><<<(unsigned)nblk_w, kCholWarps * 32, smem_b, st>>>(P, Bt);
+        else
+            chol_rows_kernel<T><<<(unsigned)((Bt.nrows + rpw - 1) / rpw), 32, smem_b, st>>>(P, Bt, rpw);
+        count_launch(3);
+        if (P.refine) {
+            TC_CUDA(cudaMemsetAsync(res, 0, sizeof(double) * (size_t)R * Bt.nrows, st));
+            refine_resid_kernel<T, RT, VEC><<<(unsigned)(sms * 8), 128, 0, st>>>(P, Bt, ch_c);
+            refine_correct_kernel<T><<<(unsigned)nblk_w, kCholWarps * 32, 0, st>>>(P, Bt);
+            count_launch(2);
+        }
+    }
+    const cudaError_t le = cudaGetLastError();
+    cudaError_t f0 = cudaSuccess;
+    if (res) f0 = cudaFreeAsync(res, st);
+    const cudaError_t f1 = cudaFreeAsync(cut, st), f2 = cudaFreeAsync(light, st);
+    return (le == cudaSuccess && f0 == cudaSuccess && f1 == cudaSuccess && f2 == cudaSuccess)
+               ? TC_OK
+               : TC_ERR_CUDA;
 }
 
-template <typename T, int RT, bool VEC>
-static tc_status launch_solve_rt(const SolveParams<T> &P, cudaStream_t st) {
-    using SM = SolveSmem<T, RT>;
-    const int warps = RT >= 64 ? 2 : 4;
-    const size_t smem = (P.pinv ? SM::per_warp_inv : SM::per_warp) * warps;
-    auto kern = solve_kernel<T, RT, VEC>;
-    if (smem > 48 * 1024) TC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                       (int)smem));
-    const int64_t blocks = (P.I + warps - 1) / warps;
-    kern<<<(unsigned)blocks, warps * 32, smem, st>>>(P);
-    count_launch();
-    return TC_OK;
+template <typename T, int KIND>
+static tc_status dispatch_rt(const SolveParams<T> &P, int tier, bool vec, int64_t m,
+                             cudaStream_t st) {
+    switch (tier) {
+        case 8: return vec ? launch_solve_rt<T, 8, true, KIND>(P, m, st) : launch_solve_rt<T, 8, false, KIND>(P, m, st);
+        case 16: return vec ? launch_solve_rt<T, 16, true, KIND>(P, m, st) : launch_solve_rt<T, 16, false, KIND>(P, m, st);
+        case 32: return vec ? launch_solve_rt<T, 32, true, KIND>(P, m, st) : launch_solve_rt<T, 32, false, KIND>(P, m, st);
+        default: return vec ? launch_solve_rt<T, 64, true, KIND>(P, m, st) : launch_solve_rt<T, 64, false, KIND>(P, m, st);
+    }
 }
 
 template <typename T>
 static tc_status solve_t(const tc_pattern *p, tc_weights w, const void *s, int R,
                          const void *const *A, int mode, const void *rhs, double lambda,
-                         void *out, int8_t *row_status, int use_d2, tc_loss loss, void *pinv,
-                         cudaStream_t st) {
+                         tc_prec prec, void *out, int8_t *row_status, int use_d2, tc_loss loss,
+                         void *pinv, cudaStream_t st) {
     const ModeData &md = p->md[mode];
     int o1, o2;
     other_modes(mode, o1, o2);
@@ -592,6 +1295,7 @@ static tc_status solve_t(const tc_pattern *p, tc_weights w, const void *s, int R
     P.lambda = lambda;
     P.R = R;
     P.status = p->status;
+    P.refine = (!pinv && prec != TC_PREC_FP32) ? 1 : 0;
     if (!use_d2) {
         P.w.kind = (int)w;
         P.w.s = nullptr;
@@ -606,26 +1310,66 @@ static tc_status solve_t(const tc_pattern *p, tc_weights w, const void *s, int R
             }
         }
     }
+    if (P.I == 0) return TC_OK;
     const int tier = rank_tier(R);
     const bool vec = vec_ok(R, tier, sizeof(T)) && aligned16({A[o1], A[o2]}) &&
                      (!use_d2 || aligned16({A[mode]}));
-    switch (tier) {
-        case 8: return vec ? launch_solve_two<T, 8, true>(P, st) : launch_solve_two<T, 8, false>(P, st);
-        case 16: return vec ? launch_solve_two<T, 16, true>(P, st) : launch_solve_two<T, 16, false>(P, st);
-        case 32: return vec ? launch_solve_two<T, 32, true>(P, st) : launch_solve_two<T, 32, false>(P, st);
-        default: return vec ? launch_solve_rt<T, 64, true>(P, st) : launch_solve_rt<T, 64, false>(P, st);
+    const int64_t m = p->nnz;
+    if (sizeof(T) == 8 && (prec == TC_PREC_TF32_REFINE || prec == TC_PREC_BF16_REFINE))
+        return TC_ERR_UNSUPPORTED;
+    // the correction step reads rhs after the solve wrote out: keep a copy
+    // when they alias
+    T *rhs_copy = nullptr;
+    if (P.refine && (const void *)P.out == (const void *)P.rhs) {
+        const size_t bytes = sizeof(T) * (size_t)P.I * R;
+        TC_CUDA(cudaMallocAsync((void **)&rhs_copy, bytes, st));
+        if (cudaMemcpyAsync(rhs_copy, P.rhs, bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
+            cudaFreeAsync(rhs_copy, st);
+            return TC_ERR_CUDA;
+        }
+        P.rhs = rhs_copy;
     }
+    tc_status rc = TC_OK;
+    if constexpr (sizeof(T) == 4) {
+        if (prec == TC_PREC_TF32_REFINE) rc = dispatch_rt<T, GK_TF32>(P, tier, vec, m, st);
+        else if (prec == TC_PREC_BF16_REFINE) rc = dispatch_rt<T, GK_BF16>(P, tier, vec, m, st);
+        else rc = dispatch_rt<T, GK_FFMA>(P, tier, vec, m, st);
+    } else {
+        rc = dispatch_rt<T, GK_FFMA>(P, tier, vec, m, st);
+    }
+    if (rhs_copy && cudaFreeAsync(rhs_copy, st) != cudaSuccess && rc == TC_OK) rc = TC_ERR_CUDA;
+    return rc;
 }
+
+}  // namespace tc
+
+extern "C" tc_status tc_set_solve_tuning(tc_dtype dtype, int R, const tc_solve_tuning *t) {
+    if ((dtype != TC_F32 && dtype != TC_F64) || R < 0 || R > TC_MAX_RANK) return TC_ERR_ARG;
+    if (t && (t->chunk_nnz < 0 || t->chunk_nnz > ((int64_t)1 << 30) || t->batch_bytes < 0))
+        return TC_ERR_ARG;
+    const tc_solve_tuning v = t ? *t : tc_solve_tuning{0, 0};
+    for (int k = 0; k < 4; ++k)
+        if (R == 0 || tc::tier_slot(tc::rank_tier(R)) == k) tc::g_tuning[dtype][k] = v;
+    return TC_OK;
+}
+
+extern "C" tc_status tc_get_solve_tuning(tc_dtype dtype, int R, tc_solve_tuning *t) {
+    if ((dtype != TC_F32 && dtype != TC_F64) || R < 1 || R > TC_MAX_RANK || !t) return TC_ERR_ARG;
+    *t = tc::g_tuning[dtype][tc::tier_slot(tc::rank_tier(R))];
+    return TC_OK;
+}
+
+namespace tc {
 
 tc_status launch_solve_factor(const tc_pattern *p, tc_weights w, const void *s, int R,
                               const void *const *A, int mode, const void *rhs, double lambda,
-                              void *out, int8_t *row_status, int use_loss_d2, tc_loss loss,
-                              void *pinv_out, cudaStream_t st) {
+                              tc_prec prec, void *out, int8_t *row_status, int use_loss_d2,
+                              tc_loss loss, void *pinv_out, cudaStream_t st) {
     if (p->dtype == TC_F64)
-        return solve_t<double>(p, w, s, R, A, mode, rhs, lambda, out, row_status, use_loss_d2,
-                               loss, pinv_out, st);
-    return solve_t<float>(p, w, s, R, A, mode, rhs, lambda, out, row_status, use_loss_d2, loss,
-                          pinv_out, st);
+        return solve_t<double>(p, w, s, R, A, mode, rhs, lambda, prec, out, row_status,
+                               use_loss_d2, loss, pinv_out, st);
+    return solve_t<float>(p, w, s, R, A, mode, rhs, lambda, prec, out, row_status, use_loss_d2,
+                          loss, pinv_out, st);
 }
 
 }  // namespace tc

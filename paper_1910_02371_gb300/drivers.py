@@ -12,13 +12,16 @@ from __future__ import annotations
 from . import tc
 
 
-def als_sweep(p: "tc.Pattern", factors, lam: float, rhs=None, row_status=None, stream=None):
-    """One ALS sweep in place over modes 0, 1, 2.  rhs: optional work buffers."""
+def als_sweep(p: "tc.Pattern", factors, lam: float, rhs=None, row_status=None, prec="fp32",
+              stream=None):
+    """One ALS sweep in place over modes 0, 1, 2.  rhs: optional work buffers;
+    prec: the Solve Factor precision form (tc.PRECS)."""
     for d in range(len(factors)):
         b = tc.mttkrp(p, factors, d, weights="values", out=None if rhs is None else rhs[d],
                       stream=stream)
         tc.solve_factor(p, factors, d, b, lam, weights=None, out=factors[d],
-                        row_status=None if row_status is None else row_status[d], stream=stream)
+                        row_status=None if row_status is None else row_status[d], prec=prec,
+                        stream=stream)
     return factors
 
 

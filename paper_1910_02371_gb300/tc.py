@@ -21,6 +21,7 @@ OK, ERR_ARG, ERR_RANGE, ERR_DUPLICATE, ERR_OOM, ERR_CUDA, ERR_NOT_SPD, ERR_DOMAI
 F32, F64 = 0, 1
 LOSSES = {"ls": 0, "poisson_log": 1, "poisson_id": 2}
 W_ONE, W_VALUES, W_ARRAY = 0, 1, 2
+PRECS = {"fp32": 0, "tf32_refine": 1, "bf16_refine": 2, "fp32_refine": 3}
 CHECK_DUPLICATES = 1
 REFILLABLE = 2
 
@@ -42,7 +43,7 @@ _SIGS = {
     "tc_last_error": [_P, _P],
     "tc_tttp": [_P, _I, _P, _I, _P, _P, _P],
     "tc_mttkrp": [_P, _I, _P, _I, _P, _I, _P, _I, _P],
-    "tc_solve_factor": [_P, _I, _P, _I, _P, _I, _P, _D, _P, _P, _P],
+    "tc_solve_factor": [_P, _I, _P, _I, _P, _I, _P, _D, _I, _P, _P, _P],
     "tc_loss_grad": [_P, _I, _I, _P, _D, _P, _P, _P],
     "tc_ggn_matvec": [_P, _I, _I, _P, _P, _D, _P, _P],
     "tc_cg_create": [_P, _I, _I, _P, _D, _I, _P],
@@ -53,6 +54,8 @@ _SIGS = {
     "tc_ggn_step": [_P, _I, _P, _P],
     "tc_cg_matvec": [_P, _P, _P, _P],
     "tc_sort_mode_noalloc": [_I64, _P, _I64, _P, _P, _P, _P],
+    "tc_set_solve_tuning": [_I, _I, _P],
+    "tc_get_solve_tuning": [_I, _I, _P],
 }
 for _name, _args in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -222,14 +225,15 @@ def mttkrp(p: Pattern, factors, mode: int, weights="values", out=None, accumulat
 
 
 def solve_factor(p: Pattern, factors, mode: int, rhs: torch.Tensor, lam: float, weights=None,
-                 out=None, row_status=None, stream=None):
-    """tc_solve_factor: per-row (G_i + lam I) a_i = rhs_i."""
+                 out=None, row_status=None, prec: str = "fp32", stream=None):
+    """tc_solve_factor: per-row (G_i + lam I) a_i = rhs_i.  prec: one of PRECS."""
     R = rhs.shape[1]
     wk, s = _wcode(weights)
     if out is None:
         out = torch.empty_like(rhs)
     _check(_lib.tc_solve_factor(p.handle, wk, _ptr(s), R, _ptrs(factors), mode, _ptr(rhs),
-                                float(lam), _ptr(out), _ptr(row_status), _stream(stream)),
+                                float(lam), PRECS[prec], _ptr(out), _ptr(row_status),
+                                _stream(stream)),
            "tc_solve_factor")
     return out
 
@@ -320,3 +324,23 @@ def sort_mode_noalloc(key: torch.Tensor, I: int, perm=None, row_ptr=None, status
     _check(_lib.tc_sort_mode_noalloc(n, _ptr(key), int(I), _ptr(perm), _ptr(row_ptr), _ptr(status),
                                      _stream(stream)), "tc_sort_mode_noalloc")
     return perm, row_ptr
+
+
+class _SolveTuning(ctypes.Structure):
+    _fields_ = [("chunk_nnz", _I64), ("batch_bytes", _I64)]
+
+
+def set_solve_tuning(dtype: torch.dtype, R: int = 0, chunk_nnz: int = 0, batch_bytes: int = 0,
+                     reset: bool = False):
+    """tc_set_solve_tuning: chunk size and batch budget of Solve Factor for the
+    rank tier of R (R = 0: every tier); reset=True restores the automatic choice."""
+    t = None if reset else ctypes.byref(_SolveTuning(int(chunk_nnz), int(batch_bytes)))
+    _check(_lib.tc_set_solve_tuning(_dtype_code(dtype), int(R), t), "tc_set_solve_tuning")
+
+
+def get_solve_tuning(dtype: torch.dtype, R: int):
+    """tc_get_solve_tuning: (chunk_nnz, batch_bytes), 0 meaning automatic."""
+    t = _SolveTuning()
+    _check(_lib.tc_get_solve_tuning(_dtype_code(dtype), int(R), ctypes.byref(t)),
+           "tc_get_solve_tuning")
+    return int(t.chunk_nnz), int(t.batch_bytes)
