@@ -199,16 +199,35 @@ tc_status tc_solve_factor(const tc_pattern *p, tc_weights w, const void *s, int 
  *                block, a power of two in [256, 16384]);
  *   batch_bytes  >= 0; 0: automatic (1 GiB).  At least one warp's rows are
  *                taken per batch whatever the value.
+ *   chol_rows_per_warp  for R <= 32 the FP64 factorization runs one row per
+ *                lane; fewer rows per warp spread a small mode over more
+ *                warps (0: automatic).
  * Settings are process-wide, per dtype and rank tier (the tier of R: 1..8,
  * 9..16, 17..32, 33..64; R = 0 sets every tier).  t == NULL restores the
  * automatic choice.  Not synchronized with calls in flight on other threads. */
 typedef struct {
     int64_t chunk_nnz;
     int64_t batch_bytes;
+    int32_t chol_rows_per_warp;  /* R <= 32: rows one warp factors (one per lane):
+                                    1, 2, 4, 8, 16 or 32; 0: automatic */
 } tc_solve_tuning;
 
 tc_status tc_set_solve_tuning(tc_dtype dtype, int R, const tc_solve_tuning *t);
 tc_status tc_get_solve_tuning(tc_dtype dtype, int R, tc_solve_tuning *t);
+
+/* Autotuner for Solve Factor (a service of the library; the paper tunes by
+ * hand).  Runs tc_solve_factor on the given inputs at each candidate tuning of
+ * the rank tier of R -- chunk_nnz in {automatic, 256, 1024, 4096, 16384} times
+ * chol_rows_per_warp in {8, 16, 32} (R <= 16) or {4, 8, 16} (R <= 32) -- once
+ * untimed and once timed with CUDA events on `stream`, and installs the
+ * fastest for the pattern's dtype (batch_bytes is kept).  `out` is
+ * overwritten with a solution; the stream is synchronized.  best, ms_out (may
+ * be NULL) receive the chosen tuning and its time in milliseconds.  On an
+ * error the previous tuning is restored. */
+tc_status tc_autotune_solve(const tc_pattern *p, tc_weights w, const void *s, int R,
+                            const void *const *factors, int mode, const void *rhs,
+                            double lambda, tc_prec prec, void *out, tc_solve_tuning *best,
+                            float *ms_out, tc_stream_t stream);
 
 /* Objective and gradient (eq. obj; Table 1; Appendix A):
  *   f = sum_e phi(t_e, m_e) + lambda sum_n ||A^(n)||_F^2,  m_e = sum_r prod_n A^(n)[i_n(e), r]

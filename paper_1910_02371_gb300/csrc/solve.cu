@@ -108,12 +108,17 @@ __global__ void zero_cut_kernel(const int64_t *__restrict__ row_ptr, const Batch
 //            4 x 4 tile of the lower triangle and keeps FP32 partial sums of at
 //            most 32 terms, folded into a compensated (TwoSum) FP32 pair, so
 //            the Gram is accurate to a few FP32 ulps whatever the row length;
+//   GK_TF32X3 tensor cores, mma.sync m16n8k8: each FP32 operand x is split
+//            into x_hi = tf32(x) and x_lo = tf32(x - x_hi) and the product is
+//            formed as hi*hi + hi*lo + lo*hi (about 21 significant bits per
+//            product); FP32 accumulator tiles folded every 128 nonzeros into
+//            compensated pairs like the FFMA form: an FP32-class Gram;
 //   GK_TF32  tensor cores, mma.sync m16n8k8 with TF32 inputs (11-bit
 //            significands) and FP32 accumulation;
 //   GK_BF16  tensor cores, mma.sync m16n8k16 with BF16 inputs (8-bit
 //            significands) and FP32 accumulation.
-// The tensor-core forms are meant to be followed by a refinement step.
-enum GramKind { GK_FFMA = 0, GK_TF32 = 1, GK_BF16 = 2 };
+// TF32 / BF16 are meant to be followed by a refinement step.
+enum GramKind { GK_FFMA = 0, GK_TF32 = 1, GK_BF16 = 2, GK_TF32X3 = 3 };
 
 // s + e = a + b exactly (Knuth's TwoSum; no FMA contraction applies).
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
@@ -154,6 +159,73 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
+__device__ __forceinline__ void split_tf32(float x, uint32_t &hi, uint32_t &lo) {
+    hi = to_tf32(x);
+    lo = to_tf32(x - __uint_as_float(hi));
+}
+
+// One K step of the tensor-core Gram on a staged block of h rows (stride S,
+// weights wf): the A fragment of row tile mt (load_a), then the product into
+// tile (mt, nt) (apply).  K step kc covers nonzeros 8 kc .. 8 kc + 7
+// (16 kc .. 16 kc + 15 for BF16).
+template <int RT, int KIND, int S>
+struct MmaStep {
+    uint32_t ah[4], al[4];
+
+    __device__ __forceinline__ void load_a(const float *hf, int kc, int mt, int gid, int tig) {
+        const int ra = mt * 16 + gid, rb = ra + 8;
+        const bool vb = rb < RT;
+        if constexpr (KIND == GK_BF16) {
+            const int k0 = kc * 16 + tig * 2;
+            ah[0] = pack_bf16(hf[k0 * S + ra], hf[(k0 + 1) * S + ra]);
+            ah[1] = pack_bf16(vb ? hf[k0 * S + rb] : 0.f, vb ? hf[(k0 + 1) * S + rb] : 0.f);
+            ah[2] = pack_bf16(hf[(k0 + 8) * S + ra], hf[(k0 + 9) * S + ra]);
+            ah[3] = pack_bf16(vb ? hf[(k0 + 8) * S + rb] : 0.f, vb ? hf[(k0 + 9) * S + rb] : 0.f);
+        } else {
+            const int k0 = kc * 8 + tig, k1 = k0 + 4;
+            const float x[4] = {hf[k0 * S + ra], vb ? hf[k0 * S + rb] : 0.f, hf[k1 * S + ra],
+                                vb ? hf[k1 * S + rb] : 0.f};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if constexpr (KIND == GK_TF32X3) split_tf32(x[q], ah[q], al[q]);
+                else ah[q] = to_tf32(x[q]);
+            }
+        }
+    }
+    __device__ __forceinline__ void apply(const float *hf, const float *wf, int kc, int nt, int gid,
+                                          int tig, float (&d)[4]) const {
+        const int cn = nt * 8 + gid;
+        if constexpr (KIND == GK_BF16) {
+            const int k0 = kc * 16 + tig * 2;
+            const uint32_t b0 = pack_bf16(wf[k0] * hf[k0 * S + cn], wf[k0 + 1] * hf[(k0 + 1) * S + cn]);
+            const uint32_t b1 = pack_bf16(wf[k0 + 8] * hf[(k0 + 8) * S + cn],
+                                          wf[k0 + 9] * hf[(k0 + 9) * S + cn]);
+            mma_bf16(d, ah, b0, b1);
+        } else {
+            const int k0 = kc * 8 + tig, k1 = k0 + 4;
+            const float x0 = wf[k0] * hf[k0 * S + cn], x1 = wf[k1] * hf[k1 * S + cn];
+            if constexpr (KIND == GK_TF32X3) {
+                // the three split products of this K step into a zeroed tile,
+                // then one round-to-nearest FP32 add into the running sum: the
+                // tensor core's accumulator adds then only ever see one K
+                // step's magnitude (their rounding would otherwise bias long
+                // sums)
+                uint32_t bh0, bl0, bh1, bl1;
+                split_tf32(x0, bh0, bl0);
+                split_tf32(x1, bh1, bl1);
+                float t[4] = {0.f, 0.f, 0.f, 0.f};
+                mma_tf32(t, al, bh0, bh1);
+                mma_tf32(t, ah, bl0, bl1);
+                mma_tf32(t, ah, bh0, bh1);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) d[q] += t[q];
+            } else {
+                mma_tf32(d, ah, to_tf32(x0), to_tf32(x1));
+            }
+        }
+    }
+};
+
 // Lower-triangle output tiles of the tensor-core forms: tile (mt, nt) covers
 // rows 16 mt .. 16 mt + 15 and columns 8 nt .. 8 nt + 7.
 template <int RT>
@@ -168,6 +240,28 @@ struct Tiles {
     }
     static constexpr int NTL = count();
 };
+
+// (mt, nt) of lower tile t, tiles in row-major order (compile-time form).
+template <int RT>
+constexpr int tile_mt(int t) {
+    int mt = 0;
+    for (;;) {
+        const int in_row = Tiles<RT>::NT < (16 * mt + 15) / 8 + 1 ? Tiles<RT>::NT : (16 * mt + 15) / 8 + 1;
+        if (t < in_row) return mt;
+        t -= in_row;
+        ++mt;
+    }
+}
+template <int RT>
+constexpr int tile_nt(int t) {
+    int mt = 0;
+    for (;;) {
+        const int in_row = Tiles<RT>::NT < (16 * mt + 15) / 8 + 1 ? Tiles<RT>::NT : (16 * mt + 15) / 8 + 1;
+        if (t < in_row) return t;
+        t -= in_row;
+        ++mt;
+    }
+}
 
 // (mt, nt) of lower tile t, tiles in row-major order.
 template <int RT>
@@ -201,7 +295,7 @@ struct GramShape {
     static constexpr int KCH = KIND == GK_BF16 ? 16 : 8;   // nonzeros per mma K step
     static constexpr bool COMP = !MMA && sizeof(T) == 4;
     // tensor cores: per-K-group partial tiles, reduced through shared memory
-    static constexpr size_t red_bytes = MMA ? (size_t)KS * RT * RT * sizeof(float) : 0;
+    static constexpr size_t red_bytes = (MMA && KS > 1) ? (size_t)KS * RT * RT * sizeof(float) : 0;
     // nonzero slices each thread gathers per stage (more for small ranks,
     // whose gathers are short and latency-bound)
     static constexpr int DEPTH = MMA ? 1 : (RT <= 16 ? 4 : 2);
@@ -356,15 +450,22 @@ struct FfmaEngine {
     }
 };
 
-// Tensor-core forms (FP32 data only).  Warp w owns tiles (w % NGRP) * TPW ..
-// + TPW - 1 for K group w / NGRP.
+// Tensor-core forms (FP32 data only), block kernel: warp w owns tiles
+// (w % NGRP) * TPW .. + TPW - 1 for K group w / NGRP.  With one K group (R =
+// 64) every accumulator entry has one owner and the flush writes directly;
+// otherwise the K groups are summed through shared memory.  The FP32-class
+// form (TF32X3) folds its accumulators into compensated pairs every FOLDK
+// K steps.
 template <int RT, int KIND>
 struct MmaEngine {
     using SH = GramShape<float, RT, KIND>;
-    static constexpr bool DIRECT = false;   // flushes through the shared buffer
-    int kg, gid, tig;
+    static constexpr bool DIRECT = SH::KS == 1;
+    static constexpr bool COMP = KIND == GK_TF32X3;
+    static constexpr int FOLDK = 16;      // K steps (128 nonzeros) between folds
+    int kg, gid, tig, fc;
     int tmt[SH::TPW], tnt[SH::TPW];
     float d[SH::TPW][4];
+    float hi[COMP ? SH::TPW : 1][4], lo[COMP ? SH::TPW : 1][4];
 
     __device__ __forceinline__ void init(int tid) {
         const int lane = tid & 31, w = tid >> 5;
@@ -379,51 +480,72 @@ struct MmaEngine {
 #pragma unroll
         for (int u = 0; u < SH::TPW; ++u)
 #pragma unroll
-            for (int q = 0; q < 4; ++q) d[u][q] = 0.f;
+            for (int q = 0; q < 4; ++q) {
+                d[u][q] = 0.f;
+                if constexpr (COMP) hi[u][q] = lo[u][q] = 0.f;
+            }
+        fc = 0;
+    }
+    __device__ __forceinline__ void fold() {
+        if constexpr (COMP) {
+#pragma unroll
+            for (int u = 0; u < SH::TPW; ++u)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    float s, e;
+                    two_sum(hi[u][q], d[u][q], s, e);
+                    hi[u][q] = s;
+                    lo[u][q] += e;
+                    d[u][q] = 0.f;
+                }
+        }
     }
     template <int S>
     __device__ __forceinline__ void accumulate(const float *hf, const float *wf, int nvalid) {
         const int nkc = (nvalid + SH::KCH - 1) / SH::KCH;
+        MmaStep<RT, KIND, S> step;
         for (int kc = kg; kc < nkc; kc += SH::KS) {
-            if constexpr (KIND == GK_TF32) {
-                const int k0 = kc * 8 + tig, k1 = k0 + 4;
-                const float w0 = wf[k0], w1 = wf[k1];
-                uint32_t a[4];
 #pragma unroll
-                for (int u = 0; u < SH::TPW; ++u) {
-                    if (u == 0 || tmt[u] != tmt[u - 1]) {
-                        const int ra = tmt[u] * 16 + gid, rb = ra + 8;
-                        a[0] = to_tf32(hf[k0 * S + ra]);
-                        a[1] = to_tf32(rb < RT ? hf[k0 * S + rb] : 0.f);
-                        a[2] = to_tf32(hf[k1 * S + ra]);
-                        a[3] = to_tf32(rb < RT ? hf[k1 * S + rb] : 0.f);
-                    }
-                    const int cn = tnt[u] * 8 + gid;
-                    mma_tf32(d[u], a, to_tf32(w0 * hf[k0 * S + cn]), to_tf32(w1 * hf[k1 * S + cn]));
-                }
-            } else {
-                const int k0 = kc * 16 + tig * 2;     // k0, k0 + 1, k0 + 8, k0 + 9
-                const float w0 = wf[k0], w1 = wf[k0 + 1], w8 = wf[k0 + 8], w9 = wf[k0 + 9];
-                uint32_t a[4];
-#pragma unroll
-                for (int u = 0; u < SH::TPW; ++u) {
-                    if (u == 0 || tmt[u] != tmt[u - 1]) {
-                        const int ra = tmt[u] * 16 + gid, rb = ra + 8;
-                        const bool vb = rb < RT;
-                        a[0] = pack_bf16(hf[k0 * S + ra], hf[(k0 + 1) * S + ra]);
-                        a[1] = pack_bf16(vb ? hf[k0 * S + rb] : 0.f, vb ? hf[(k0 + 1) * S + rb] : 0.f);
-                        a[2] = pack_bf16(hf[(k0 + 8) * S + ra], hf[(k0 + 9) * S + ra]);
-                        a[3] = pack_bf16(vb ? hf[(k0 + 8) * S + rb] : 0.f, vb ? hf[(k0 + 9) * S + rb] : 0.f);
-                    }
-                    const int cn = tnt[u] * 8 + gid;
-                    const uint32_t b0 = pack_bf16(w0 * hf[k0 * S + cn], w1 * hf[(k0 + 1) * S + cn]);
-                    const uint32_t b1 = pack_bf16(w8 * hf[(k0 + 8) * S + cn], w9 * hf[(k0 + 9) * S + cn]);
-                    mma_bf16(d[u], a, b0, b1);
+            for (int u = 0; u < SH::TPW; ++u) {
+                if (u == 0 || tmt[u] != tmt[u - 1]) step.load_a(hf, kc, tmt[u], gid, tig);
+                step.apply(hf, wf, kc, tnt[u], gid, tig, d[u]);
+            }
+            if constexpr (COMP) {
+                if (++fc == FOLDK) {
+                    fold();
+                    fc = 0;
                 }
             }
         }
     }
+    __device__ __forceinline__ float value(int u, int q) const {
+        if constexpr (COMP) return hi[u][q] + (lo[u][q] + d[u][q]);
+        else return d[u][q];
+    }
+    // DIRECT: writes this lane's lower entries of rows < R.
+    __device__ __forceinline__ void flush(float *lrow, double *crow, bool whole, int R) {
+        fold();
+        fc = 0;
+#pragma unroll
+        for (int u = 0; u < SH::TPW; ++u)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int r = tmt[u] * 16 + gid + (q >= 2 ? 8 : 0);
+                const int c = tnt[u] * 8 + tig * 2 + (q & 1);
+                if (r >= R || c > r) continue;
+                const int e = tri_idx(r, c);
+                if constexpr (COMP) {
+                    if (whole) lrow[e] = hi[u][q] + lo[u][q];
+                    else atomicAdd(crow + e, (double)hi[u][q] + (double)lo[u][q]);
+                } else {
+                    if (whole) lrow[e] = d[u][q];
+                    else atomicAdd(crow + e, (double)d[u][q]);
+                }
+            }
+    }
     __device__ __forceinline__ void to_red(unsigned char *red) {
+        fold();
+        fc = 0;
         float *mine = reinterpret_cast<float *>(red) + kg * RT * RT;
 #pragma unroll
         for (int u = 0; u < SH::TPW; ++u)
@@ -431,7 +553,7 @@ struct MmaEngine {
             for (int q = 0; q < 4; ++q) {
                 const int r = tmt[u] * 16 + gid + (q >= 2 ? 8 : 0);
                 const int c = tnt[u] * 8 + tig * 2 + (q & 1);
-                if (r < RT) mine[r * RT + c] = d[u][q];
+                if (r < RT) mine[r * RT + c] = value(u, q);
             }
     }
     __device__ __forceinline__ void from_red(const unsigned char *red, int r, int c, double &v,
@@ -456,6 +578,10 @@ struct EngineOf<float, RT, GK_TF32> {
 template <int RT>
 struct EngineOf<float, RT, GK_BF16> {
     using type = MmaEngine<RT, GK_BF16>;
+};
+template <int RT>
+struct EngineOf<float, RT, GK_TF32X3> {
+    using type = MmaEngine<RT, GK_TF32X3>;
 };
 
 template <typename T, int RT, bool VEC, int KIND>
@@ -498,18 +624,31 @@ __global__ void __launch_bounds__(GramShape<T, RT, KIND>::NTH, 2)
             T arow[V];
             if (P.use_d2) load_slice<T, V, VEC>(arow, P.Ad, i, R, lg);
             eng.zero();
+            // Software pipeline: the loads of stage s + 1 are issued right
+            // after stage s is in shared memory, so they are in flight while
+            // the engine consumes stage s.  pb / pe / pw hold the fetched
+            // factor slices and raw weights (the value t for phi'').
+            T pb[Q::NSTEP][V], pe[Q::NSTEP][V], pw[Q::NSTEP];
+            auto fetch = [&](int64_t base) {
+#pragma unroll
+                for (int st = 0; st < Q::NSTEP; ++st) {
+                    const int slot = st * Q::BSTEP + w * NG + g;
+                    const int64_t qq = base + slot < se ? base + slot : se - 1;
+                    load_slice<T, V, VEC>(pb[st], P.A1, __ldcs(P.c1 + qq), R, lg);
+                    load_slice<T, V, VEC>(pe[st], P.A2, __ldcs(P.c2 + qq), R, lg);
+                    pw[st] = P.use_d2 ? __ldcs(P.t + qq) : weight_at(P.w, qq);
+                }
+            };
+            fetch(ss);
             for (int64_t base = ss; base < se; base += KB) {
-                // ---- gather KB nonzeros: h_e and weights
+                // ---- stage KB nonzeros: h_e and weights
 #pragma unroll
                 for (int st = 0; st < Q::NSTEP; ++st) {
                     const int slot = st * Q::BSTEP + w * NG + g;
                     const bool valid = base + slot < se;
-                    const int64_t qq = valid ? base + slot : se - 1;
-                    T b[V], e[V], h[V];
-                    load_slice<T, V, VEC>(b, P.A1, __ldcs(P.c1 + qq), R, lg);
-                    load_slice<T, V, VEC>(e, P.A2, __ldcs(P.c2 + qq), R, lg);
+                    T h[V];
 #pragma unroll
-                    for (int t = 0; t < V; ++t) h[t] = b[t] * e[t];
+                    for (int t = 0; t < V; ++t) h[t] = pb[st][t] * pe[st][t];
                     T sw;
                     if (P.use_d2) {
                         T part = T(0);
@@ -518,11 +657,11 @@ __global__ void __launch_bounds__(GramShape<T, RT, KIND>::NTH, 2)
                         const T m = group_sum<G>(part);
                         T phi, d1, d2;
                         bool ok = true;
-                        loss_terms(P.loss, __ldcs(P.t + qq), m, phi, d1, d2, ok);
+                        loss_terms(P.loss, pw[st], m, phi, d1, d2, ok);
                         if (!ok && valid) record_error(P.status, TC_ERR_DOMAIN);
                         sw = d2;
                     } else {
-                        sw = weight_at(P.w, qq);
+                        sw = pw[st];
                     }
                     if (!valid) {
                         sw = T(0);
@@ -534,6 +673,7 @@ __global__ void __launch_bounds__(GramShape<T, RT, KIND>::NTH, 2)
                     if (lg == 0) ws[slot] = sw;
                 }
                 __syncthreads();
+                if (base + KB < se) fetch(base + KB);
                 eng.template accumulate<S>(hs, ws, (int)min((int64_t)KB, se - base));
                 __syncthreads();
             }
@@ -724,6 +864,157 @@ __global__ void __launch_bounds__(128) gram_warp_kernel(const SolveParams<T> P, 
     }
 }
 
+// ------------------------------------------------------------------ kernel A, tensor cores, R <= 32
+// Tensor-core forms for ranks up to 32: every warp works alone, like
+// gram_warp_kernel, and holds every lower output tile of the Gram in its
+// mma accumulators (R = 32: 6 tiles, 24 floats per lane; R = 16: 2 tiles),
+// so each entry has one owner lane and the flush needs no reduction.  The
+// FP32-class form folds the accumulators every 16 K steps into compensated
+// pairs held in registers.
+template <int RT, int KIND>
+struct WarpMma {
+    static constexpr int NW = 4, NTH = NW * 32;
+    using L = Lay<float, RT, 32>;
+    static constexpr int V = L::V, G = L::G, NG = L::NG;
+    static constexpr int KCH = KIND == GK_BF16 ? 16 : 8;
+    static constexpr int DEPTH = 4;
+    static constexpr int KBW = NG * DEPTH;                 // nonzeros per warp stage
+    static constexpr int S = RT + (RT >= 16 ? 8 : 0);
+    static constexpr int NTL = Tiles<RT>::NTL;
+    static constexpr bool COMP = KIND == GK_TF32X3;
+    static constexpr int FOLDK = 16;
+    static constexpr size_t warp_bytes = ((sizeof(float) * (KBW * S + KBW) + 15) / 16) * 16;
+    static constexpr size_t smem = NW * warp_bytes;
+    static_assert(KBW % KCH == 0, "whole K steps per stage");
+};
+
+template <int RT, bool VEC, int KIND>
+__global__ void __launch_bounds__(128) gram_warp_mma_kernel(const SolveParams<float> P,
+                                                            const Batch<float> B) {
+    using Q = WarpMma<RT, KIND>;
+    constexpr int V = Q::V, G = Q::G, NG = Q::NG, KBW = Q::KBW, S = Q::S, NTL = Q::NTL;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    float *hs = reinterpret_cast<float *>(smem_raw + w * Q::warp_bytes);
+    float *ws = hs + KBW * S;
+    const int g = lane / G, lg = lane % G;
+    const int gid = lane >> 2, tig = lane & 3;
+    const int R = VEC ? RT : P.R;
+    const int tri = R * (R + 1) / 2;
+    const int64_t nb = __ldg(P.row_ptr + B.row0), ne = __ldg(P.row_ptr + B.row0 + B.nrows);
+    const int64_t last = B.row0 + B.nrows - 1;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    float d[NTL][4];
+    float hi[Q::COMP ? NTL : 1][4], lo[Q::COMP ? NTL : 1][4];
+    for (int64_t cs = nb + gw * B.ch; cs < ne; cs += nwarps * B.ch) {
+        const int64_t ce = min(cs + B.ch, ne);
+        int64_t i = search_le(P.row_ptr, B.row0, last, cs);
+        for (;;) {
+            const int64_t rs = __ldg(P.row_ptr + i), re = __ldg(P.row_ptr + i + 1);
+            const int64_t ss = max(rs, cs), se = min(re, ce);
+            float arow[V];
+            if (P.use_d2) load_slice<float, V, VEC>(arow, P.Ad, i, R, lg);
+#pragma unroll
+            for (int u = 0; u < NTL; ++u)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    d[u][q] = 0.f;
+                    if constexpr (Q::COMP) hi[u][q] = lo[u][q] = 0.f;
+                }
+            int fc = 0;
+            for (int64_t base = ss; base < se; base += KBW) {
+#pragma unroll
+                for (int st = 0; st < Q::DEPTH; ++st) {
+                    const int slot = st * NG + g;
+                    const bool valid = base + slot < se;
+                    const int64_t qq = valid ? base + slot : se - 1;
+                    float b[V], e[V], h[V];
+                    load_slice<float, V, VEC>(b, P.A1, __ldcs(P.c1 + qq), R, lg);
+                    load_slice<float, V, VEC>(e, P.A2, __ldcs(P.c2 + qq), R, lg);
+#pragma unroll
+                    for (int t = 0; t < V; ++t) h[t] = b[t] * e[t];
+                    float sw;
+                    if (P.use_d2) {
+                        float part = 0.f;
+#pragma unroll
+                        for (int t = 0; t < V; ++t) part += arow[t] * h[t];
+                        const float m = group_sum<G>(part);
+                        float phi, d1, d2;
+                        bool ok = true;
+                        loss_terms(P.loss, __ldcs(P.t + qq), m, phi, d1, d2, ok);
+                        if (!ok && valid) record_error(P.status, TC_ERR_DOMAIN);
+                        sw = d2;
+                    } else {
+                        sw = weight_at(P.w, qq);
+                    }
+                    if (!valid) {
+                        sw = 0.f;
+#pragma unroll
+                        for (int t = 0; t < V; ++t) h[t] = 0.f;
+                    }
+#pragma unroll
+                    for (int t = 0; t < V; ++t) hs[slot * S + lg * V + t] = h[t];
+                    if (lg == 0) ws[slot] = sw;
+                }
+                __syncwarp();
+                const int nkc = ((int)min((int64_t)KBW, se - base) + Q::KCH - 1) / Q::KCH;
+                MmaStep<RT, KIND, S> step;
+                for (int kc = 0; kc < nkc; ++kc) {
+#pragma unroll
+                    for (int u = 0; u < NTL; ++u) {
+                        if (u == 0 || tile_mt<RT>(u) != tile_mt<RT>(u - 1))
+                            step.load_a(hs, kc, tile_mt<RT>(u), gid, tig);
+                        step.apply(hs, ws, kc, tile_nt<RT>(u), gid, tig, d[u]);
+                    }
+                    if constexpr (Q::COMP) {
+                        if (++fc == Q::FOLDK) {
+                            fc = 0;
+#pragma unroll
+                            for (int u = 0; u < NTL; ++u)
+#pragma unroll
+                                for (int q = 0; q < 4; ++q) {
+                                    float sm, er;
+                                    two_sum(hi[u][q], d[u][q], sm, er);
+                                    hi[u][q] = sm;
+                                    lo[u][q] += er;
+                                    d[u][q] = 0.f;
+                                }
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+            // ---- flush: each lane writes its own lower entries
+            const bool whole = rs >= cs && re <= ce;
+            const int64_t slot = whole ? -1 : cut_slot(rs, re, nb, B.ch);
+            float *lrow = B.light + (i - B.row0) * (int64_t)tri;
+            double *crow = slot >= 0 ? B.cut + slot * (int64_t)tri : nullptr;
+#pragma unroll
+            for (int u = 0; u < NTL; ++u)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int r = tile_mt<RT>(u) * 16 + gid + (q >= 2 ? 8 : 0);
+                    const int c = tile_nt<RT>(u) * 8 + tig * 2 + (q & 1);
+                    if (r >= R || c > r) continue;
+                    const int e = tri_idx(r, c);
+                    if constexpr (Q::COMP) {
+                        float sm, er;
+                        two_sum(hi[u][q], d[u][q], sm, er);
+                        const float l2 = lo[u][q] + er;
+                        if (whole) lrow[e] = sm + l2;
+                        else atomicAdd(crow + e, (double)sm + (double)l2);
+                    } else {
+                        if (whole) lrow[e] = d[u][q];
+                        else atomicAdd(crow + e, (double)d[u][q]);
+                    }
+                }
+            if (re >= ce) break;
+            i = search_le(P.row_ptr, i + 1, last, re);   // next nonempty row
+        }
+    }
+}
+
 // Gram entry e of batch row q (zero for an empty row).
 template <typename T>
 __device__ __forceinline__ double gram_entry(const T *lrow, const double *crow, int e) {
@@ -762,13 +1053,29 @@ __global__ void __launch_bounds__(32) chol_rows_kernel(const SolveParams<T> P, c
     double *Tri = sh;
     double *Vv = sh + (int64_t)tri * ps;
     double *Dinv = Vv + (int64_t)R * ps;
-    for (int s = 0; s < rpw; ++s) {
-        const int64_t q = grp * rpw + s;
-        if (q >= B.nrows) break;
-        const T *lrow;
-        const double *crow;
-        gram_source(P, B, nb, B.row0 + q, tri, lrow, crow);
-        for (int e = lane; e < tri; e += 32) Tri[e * ps + s] = gram_entry(lrow, crow, e);
+    {
+        // every lane finds its own row's Gram (in parallel), then the warp
+        // copies all rows' triangles in one flat loop, the row pointers
+        // broadcast by shuffles, so no load waits on another
+        const int64_t q0 = grp * rpw;
+        const int nr = (int)min((int64_t)rpw, B.nrows - q0);
+        const T *lmine = nullptr;
+        const double *cmine = nullptr;
+        if (lane < nr) gram_source(P, B, nb, B.row0 + q0 + lane, tri, lmine, cmine);
+        const int n = nr * tri;
+#pragma unroll 4
+        for (int base = 0; base < n; base += 32) {
+            const int idx = base + lane;
+            const int sl = idx < n ? idx / tri : 0;
+            const T *lrow = reinterpret_cast<const T *>(
+                __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(lmine), sl));
+            const double *crow = reinterpret_cast<const double *>(
+                __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(cmine), sl));
+            if (idx < n) {
+                const int e = idx - sl * tri;
+                Tri[e * ps + sl] = gram_entry(lrow, crow, e);
+            }
+        }
     }
     __syncwarp();
     const int slot = lane;
@@ -1156,42 +1463,74 @@ static int64_t chunk_nnz(int64_t m, int64_t grid, const tc_solve_tuning &t) {
     return ch;
 }
 
+// Kernel A variant for (dtype, rank tier, form): warp-local kernels (one warp
+// per chunk) for FP64 ranks <= 16 and tensor-core ranks <= 32, the block
+// kernel otherwise.
+template <typename T, int RT, bool VEC, int KIND>
+struct GramLaunch {
+    static constexpr int VAR = (sizeof(T) == 8 && RT <= 16) ? 1 : (sizeof(T) == 4 && RT <= 32 && KIND != GK_FFMA) ? 2 : 0;
+    static constexpr bool PER_WARP = VAR != 0;
+    static int threads() {
+        if constexpr (VAR == 1) return WarpGram<T, RT>::NTH;
+        else if constexpr (VAR == 2) return WarpMma<RT, KIND>::NTH;
+        else return GramGeo<T, RT, KIND>::NTH;
+    }
+    static size_t smem() {
+        if constexpr (VAR == 1) return WarpGram<T, RT>::smem;
+        else if constexpr (VAR == 2) return WarpMma<RT, KIND>::smem;
+        else return GramGeo<T, RT, KIND>::smem;
+    }
+    static const void *fn() {
+        if constexpr (VAR == 1) return (const void *)gram_warp_kernel<T, RT, VEC>;
+        else if constexpr (VAR == 2) return (const void *)gram_warp_mma_kernel<RT, VEC, KIND>;
+        else return (const void *)gram_chunk_kernel<T, RT, VEC, KIND>;
+    }
+    // resident blocks per SM (queried once)
+    static tc_status occupancy(int &occ) {
+        static int cached = 0;
+        if (!cached) {
+            if (smem() > 48 * 1024)
+                TC_CUDA(cudaFuncSetAttribute(fn(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem()));
+            int v = 0;
+            TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, fn(), threads(), smem()));
+            cached = v > 0 ? v : 1;
+        }
+        occ = cached;
+        return TC_OK;
+    }
+    static void launch(int64_t grid, const SolveParams<T> &P, const Batch<T> &Bt, cudaStream_t st) {
+        if constexpr (VAR == 1)
+            gram_warp_kernel<T, RT, VEC><<<(unsigned)grid, threads(), smem(), st>>>(P, Bt);
+        else if constexpr (VAR == 2)
+            gram_warp_mma_kernel<RT, VEC, KIND><<<(unsigned)grid, threads(), smem(), st>>>(P, Bt);
+        else
+            gram_chunk_kernel<T, RT, VEC, KIND><<<(unsigned)grid, threads(), smem(), st>>>(P, Bt);
+    }
+};
+
 template <typename T, int RT, bool VEC, int KIND>
 static tc_status launch_solve_rt(const SolveParams<T> &P, int64_t m, cudaStream_t st) {
-    using Q = GramGeo<T, RT, KIND>;
+    using GL = GramLaunch<T, RT, VEC, KIND>;
     const int R = P.R, tri = R * (R + 1) / 2;
     const int sms = device_sms();
-    auto ka = gram_chunk_kernel<T, RT, VEC, (KIND == GK_FFMA && RT <= 16) ? GK_FFMA : KIND>;
-    static int occ_a = 0;
-    if (!(KIND == GK_FFMA && RT <= 16) && !occ_a) {
-        if (Q::smem > 48 * 1024)
-            TC_CUDA(cudaFuncSetAttribute(ka, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Q::smem));
-        int v = 0;
-        TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, ka, Q::NTH, Q::smem));
-        occ_a = v > 0 ? v : 1;
+    int occ = 1;
+    {
+        const tc_status rc = GL::occupancy(occ);
+        if (rc != TC_OK) return rc;
     }
     const tc_solve_tuning tun = g_tuning[sizeof(T) == 8 ? 1 : 0][tier_slot(RT)];
-    // small ranks, FFMA form: one warp per chunk (gram_warp_kernel)
-    constexpr bool WARP_A = KIND == GK_FFMA && RT <= 16;
-    static int occ_w = 0;
-    if constexpr (WARP_A) {
-        using QW = WarpGram<T, RT>;
-        if (!occ_w) {
-            auto kaw = gram_warp_kernel<T, RT, VEC>;
-            if (QW::smem > 48 * 1024)
-                TC_CUDA(cudaFuncSetAttribute(kaw, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)QW::smem));
-            int v = 0;
-            TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kaw, QW::NTH, QW::smem));
-            occ_w = v > 0 ? v : 1;
-        }
-    }
-    const int64_t grid_a = (int64_t)sms * (WARP_A ? occ_w : occ_a);
-    const int64_t ch = chunk_nnz(m, WARP_A ? grid_a * 4 : grid_a, tun);
+    const int64_t grid_a = (int64_t)sms * occ;
+    const int64_t ch = chunk_nnz(m, GL::PER_WARP ? grid_a * (GL::threads() / 32) : grid_a, tun);
     const int64_t ch_c = ch / 4 > 64 ? ch / 4 : 64;    // refinement: a warp per chunk
 
     const bool warp_b = RT > 32;
-    const int rpw = RT <= 16 ? 32 : 16;
+    // rows per warp of the one-row-per-lane factorization.  Measured on
+    // GB300 (FP64 issue is per warp instruction, and each FP64 triangle of a
+    // lane's row takes R(R+1)/2 * 8 bytes of shared memory): 16 for R <= 16,
+    // 8 for R = 32 (more rows per warp leave too few warps per SM)
+    int rpw = RT <= 16 ? 16 : 8;
+    if (tun.chol_rows_per_warp > 0) rpw = tun.chol_rows_per_warp < 32 ? tun.chol_rows_per_warp : 32;
+    if (RT > 16 && rpw > 16) rpw = 16;
     const int align = warp_b ? kCholWarps : rpw;
     size_t smem_b;
     if (warp_b)
@@ -1230,11 +1569,7 @@ static tc_status launch_solve_rt(const SolveParams<T> &P, int64_t m, cudaStream_
         if (zb > (int64_t)sms * 4) zb = (int64_t)sms * 4;
         if (zb < 1) zb = 1;
         zero_cut_kernel<T><<<(unsigned)zb, 256, 0, st>>>(P.row_ptr, Bt, tri);
-        if constexpr (WARP_A)
-            gram_warp_kernel<T, RT, VEC><<<(unsigned)grid_a, WarpGram<T, RT>::NTH,
-                                           WarpGram<T, RT>::smem, st>>>(P, Bt);
-        else
-            ka<<<(unsigned)grid_a, Q::NTH, Q::smem, st>>>(P, Bt);
+        GL::launch(grid_a, P, Bt, st);
         int64_t nblk_w = (Bt.nrows + kCholWarps - 1) / kCholWarps;
         if (nblk_w > nblk_w0) nblk_w = nblk_w0;
         if (warp_b)
@@ -1333,7 +1668,7 @@ static tc_status solve_t(const tc_pattern *p, tc_weights w, const void *s, int R
     if constexpr (sizeof(T) == 4) {
         if (prec == TC_PREC_TF32_REFINE) rc = dispatch_rt<T, GK_TF32>(P, tier, vec, m, st);
         else if (prec == TC_PREC_BF16_REFINE) rc = dispatch_rt<T, GK_BF16>(P, tier, vec, m, st);
-        else rc = dispatch_rt<T, GK_FFMA>(P, tier, vec, m, st);
+        else rc = dispatch_rt<T, GK_TF32X3>(P, tier, vec, m, st);
     } else {
         rc = dispatch_rt<T, GK_FFMA>(P, tier, vec, m, st);
     }
@@ -1347,7 +1682,11 @@ extern "C" tc_status tc_set_solve_tuning(tc_dtype dtype, int R, const tc_solve_t
     if ((dtype != TC_F32 && dtype != TC_F64) || R < 0 || R > TC_MAX_RANK) return TC_ERR_ARG;
     if (t && (t->chunk_nnz < 0 || t->chunk_nnz > ((int64_t)1 << 30) || t->batch_bytes < 0))
         return TC_ERR_ARG;
-    const tc_solve_tuning v = t ? *t : tc_solve_tuning{0, 0};
+    if (t && t->chol_rows_per_warp != 0) {
+        const int v = t->chol_rows_per_warp;
+        if (v < 1 || v > 32 || (v & (v - 1))) return TC_ERR_ARG;
+    }
+    const tc_solve_tuning v = t ? *t : tc_solve_tuning{0, 0, 0};
     for (int k = 0; k < 4; ++k)
         if (R == 0 || tc::tier_slot(tc::rank_tier(R)) == k) tc::g_tuning[dtype][k] = v;
     return TC_OK;
@@ -1356,6 +1695,64 @@ extern "C" tc_status tc_set_solve_tuning(tc_dtype dtype, int R, const tc_solve_t
 extern "C" tc_status tc_get_solve_tuning(tc_dtype dtype, int R, tc_solve_tuning *t) {
     if ((dtype != TC_F32 && dtype != TC_F64) || R < 1 || R > TC_MAX_RANK || !t) return TC_ERR_ARG;
     *t = tc::g_tuning[dtype][tc::tier_slot(tc::rank_tier(R))];
+    return TC_OK;
+}
+
+// Candidate tunings for the rank tier: chunk sizes around the automatic
+// choice, and the factorization's rows per warp where it applies.
+extern "C" tc_status tc_autotune_solve(const tc_pattern *p, tc_weights w, const void *s, int R,
+                                       const void *const *factors, int mode, const void *rhs,
+                                       double lambda, tc_prec prec, void *out,
+                                       tc_solve_tuning *best, float *ms_out, tc_stream_t stream) {
+    if (!p || R < 1 || R > TC_MAX_RANK || !factors || !rhs || !out || mode < 0 || mode >= p->order)
+        return TC_ERR_ARG;
+    const int dt = p->dtype == TC_F64 ? 1 : 0;
+    const int tier = tc::rank_tier(R), slot = tc::tier_slot(tier);
+    const tc_solve_tuning saved = tc::g_tuning[dt][slot];
+    const int64_t chunks[] = {0, 256, 1024, 4096, 16384};
+    int rpws[3] = {0, 0, 0};
+    int nr = 1;
+    if (tier <= 16) { rpws[0] = 8; rpws[1] = 16; rpws[2] = 32; nr = 3; }
+    else if (tier <= 32) { rpws[0] = 4; rpws[1] = 8; rpws[2] = 16; nr = 3; }
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return TC_ERR_CUDA;
+    }
+    tc_solve_tuning win = saved;
+    float win_ms = -1.f;
+    tc_status rc = TC_OK;
+    for (int64_t ch : chunks) {
+        for (int k = 0; k < nr && rc == TC_OK; ++k) {
+            tc::g_tuning[dt][slot] = tc_solve_tuning{ch, saved.batch_bytes, rpws[k]};
+            // one untimed call (allocator, caches), then one timed
+            rc = tc::launch_solve_factor(p, w, s, R, factors, mode, rhs, lambda, prec, out, nullptr,
+                                         0, TC_LOSS_LS, nullptr, st);
+            if (rc != TC_OK) break;
+            if (cudaEventRecord(e0, st) != cudaSuccess) { rc = TC_ERR_CUDA; break; }
+            rc = tc::launch_solve_factor(p, w, s, R, factors, mode, rhs, lambda, prec, out, nullptr,
+                                         0, TC_LOSS_LS, nullptr, st);
+            if (rc != TC_OK) break;
+            float ms = 0.f;
+            if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                rc = TC_ERR_CUDA;
+                break;
+            }
+            if (win_ms < 0.f || ms < win_ms) {
+                win_ms = ms;
+                win = tc::g_tuning[dt][slot];
+            }
+        }
+        if (rc != TC_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    tc::g_tuning[dt][slot] = rc == TC_OK ? win : saved;
+    if (rc != TC_OK) return rc;
+    if (best) *best = win;
+    if (ms_out) *ms_out = win_ms;
     return TC_OK;
 }
 

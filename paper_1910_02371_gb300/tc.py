@@ -56,6 +56,7 @@ _SIGS = {
     "tc_sort_mode_noalloc": [_I64, _P, _I64, _P, _P, _P, _P],
     "tc_set_solve_tuning": [_I, _I, _P],
     "tc_get_solve_tuning": [_I, _I, _P],
+    "tc_autotune_solve": [_P, _I, _P, _I, _P, _I, _P, _D, _I, _P, _P, _P, _P],
 }
 for _name, _args in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -327,20 +328,38 @@ def sort_mode_noalloc(key: torch.Tensor, I: int, perm=None, row_ptr=None, status
 
 
 class _SolveTuning(ctypes.Structure):
-    _fields_ = [("chunk_nnz", _I64), ("batch_bytes", _I64)]
+    _fields_ = [("chunk_nnz", _I64), ("batch_bytes", _I64), ("chol_rows_per_warp", ctypes.c_int32)]
 
 
 def set_solve_tuning(dtype: torch.dtype, R: int = 0, chunk_nnz: int = 0, batch_bytes: int = 0,
-                     reset: bool = False):
-    """tc_set_solve_tuning: chunk size and batch budget of Solve Factor for the
-    rank tier of R (R = 0: every tier); reset=True restores the automatic choice."""
-    t = None if reset else ctypes.byref(_SolveTuning(int(chunk_nnz), int(batch_bytes)))
+                     chol_rows_per_warp: int = 0, reset: bool = False):
+    """tc_set_solve_tuning: chunk size, batch budget and factorization rows per
+    warp of Solve Factor for the rank tier of R (R = 0: every tier);
+    reset=True restores the automatic choice."""
+    t = None if reset else ctypes.byref(
+        _SolveTuning(int(chunk_nnz), int(batch_bytes), int(chol_rows_per_warp)))
     _check(_lib.tc_set_solve_tuning(_dtype_code(dtype), int(R), t), "tc_set_solve_tuning")
 
 
 def get_solve_tuning(dtype: torch.dtype, R: int):
-    """tc_get_solve_tuning: (chunk_nnz, batch_bytes), 0 meaning automatic."""
+    """tc_get_solve_tuning: (chunk_nnz, batch_bytes, chol_rows_per_warp), 0 meaning automatic."""
     t = _SolveTuning()
     _check(_lib.tc_get_solve_tuning(_dtype_code(dtype), int(R), ctypes.byref(t)),
            "tc_get_solve_tuning")
-    return int(t.chunk_nnz), int(t.batch_bytes)
+    return int(t.chunk_nnz), int(t.batch_bytes), int(t.chol_rows_per_warp)
+
+
+def autotune_solve(p: Pattern, factors, mode: int, rhs: torch.Tensor, lam: float, weights=None,
+                   out=None, prec: str = "fp32", stream=None):
+    """tc_autotune_solve: times Solve Factor at the candidate tunings, installs
+    the fastest; returns ((chunk_nnz, batch_bytes, chol_rows_per_warp), ms)."""
+    R = rhs.shape[1]
+    wk, s = _wcode(weights)
+    if out is None:
+        out = torch.empty_like(rhs)
+    best = _SolveTuning()
+    ms = ctypes.c_float()
+    _check(_lib.tc_autotune_solve(p.handle, wk, _ptr(s), R, _ptrs(factors), mode, _ptr(rhs),
+                                  float(lam), PRECS[prec], _ptr(out), ctypes.byref(best),
+                                  ctypes.byref(ms), _stream(stream)), "tc_autotune_solve")
+    return (int(best.chunk_nnz), int(best.batch_bytes), int(best.chol_rows_per_warp)), float(ms.value)

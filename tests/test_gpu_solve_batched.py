@@ -27,9 +27,10 @@ CASES = {
                         dist=("zipf", "zipf", "uniform")),
     "uni_f32_r16": dict(dims=(2000, 2000, 2000), nnz=200000, R=16, dtype="f32"),
 }
-# (chunk_nnz, batch_bytes): automatic, tiny chunks (nearly every row is cut),
-# odd chunks with one warp's rows per batch, and a chunk longer than most rows
-TUNINGS = [(0, 0), (16, 0), (37, 1), (5000, 1 << 20)]
+# (chunk_nnz, batch_bytes, chol_rows_per_warp): automatic, tiny chunks (nearly
+# every row is cut), odd chunks with one warp's rows per batch, a chunk longer
+# than most rows, and one row per warp in the factorization
+TUNINGS = [(0, 0, 0), (16, 0, 0), (37, 1, 0), (5000, 1 << 20, 2), (0, 0, 1)]
 
 _cache = {}
 
@@ -56,8 +57,9 @@ def _tune(tc, prob, tuning):
     import torch
     dt = torch.float32 if prob.dtype == "f32" else torch.float64
     tc.set_solve_tuning(dt, 0, reset=True)
-    if tuning != (0, 0):
-        tc.set_solve_tuning(dt, prob.R, chunk_nnz=tuning[0], batch_bytes=tuning[1])
+    if tuning != (0, 0, 0):
+        tc.set_solve_tuning(dt, prob.R, chunk_nnz=tuning[0], batch_bytes=tuning[1],
+                            chol_rows_per_warp=tuning[2])
         assert tc.get_solve_tuning(dt, prob.R) == tuning
 
 
@@ -100,7 +102,7 @@ def row_conditions(prob, mode, lam2, weight=2.0):
 
 
 @pytest.mark.parametrize("name", ["zipf_f32_r64", "f32_r40", "zipf_f32_r16", "f64_r64"])
-@pytest.mark.parametrize("tuning", [(0, 0), (37, 1)])
+@pytest.mark.parametrize("tuning", [(0, 0, 0), (37, 1, 4)])
 def test_preconditioner_uneven_rows(tc, name, tuning):
     """The preconditioner is an operator built once from an FP32 (or FP64)
     Gram: no refinement can apply to it, so each row's agreement with the FP64
@@ -139,7 +141,7 @@ def test_refined_solve_ill_conditioned(tc, name):
     output back within the FP32 tolerance of the FP64 oracle."""
     import torch
     prob = problem(name)
-    _tune(tc, prob, (0, 0))
+    _tune(tc, prob, (0, 0, 0))
     p = build(prob)
     A = [to_dev(a, prob.dtype) for a in prob.factors]
     lam = 0.05
@@ -177,7 +179,7 @@ def test_mixed_precision_objective(tc, name, prec):
     and stated, not bounded here)."""
     from paper_1910_02371_gb300 import drivers
     prob = problem(name)
-    _tune(tc, prob, (0, 0))
+    _tune(tc, prob, (0, 0, 0))
     p = build(prob)
     lam = 0.5
     A = [to_dev(a, prob.dtype) for a in prob.factors]
@@ -207,7 +209,7 @@ def test_not_spd_rows_warp_cholesky(tc):
     untouched."""
     import torch
     prob = problem("zipf_f32_r64")
-    _tune(tc, prob, (0, 0))
+    _tune(tc, prob, (0, 0, 0))
     p = build(prob)
     mode = 0
     rhs = np.random.default_rng(1).standard_normal((prob.dims[mode], prob.R))
