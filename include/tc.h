@@ -99,7 +99,12 @@ typedef enum {
     TC_PREC_FP32 = 0,
     TC_PREC_TF32_REFINE = 1,
     TC_PREC_BF16_REFINE = 2,
-    TC_PREC_FP32_REFINE = 3
+    TC_PREC_FP32_REFINE = 3,
+    /* OR-ed into a *_REFINE form: factor in FP32 instead of FP64.  The
+     * refinement step corrects the factorization's rounding like the Gram's
+     * (its convergence factor is kappa_i times the larger unit roundoff), and
+     * FP32 runs far faster than FP64 on this GPU.  Ignored without refinement. */
+    TC_PREC_CHOL32 = 0x100
 } tc_prec;
 
 /* tc_build_pattern flags */

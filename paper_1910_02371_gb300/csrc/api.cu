@@ -163,8 +163,9 @@ tc_status tc_solve_factor(const tc_pattern *p, tc_weights w, const void *s, int 
                           tc_prec prec, void *out, int8_t *row_status, tc_stream_t stream) {
     if (!p || !rank_ok(R) || !out || !rhs || mode < 0 || mode >= p->order) return TC_ERR_ARG;
     if (!factors_ok(factors, mode) || check_weights(p, w, s) != TC_OK) return TC_ERR_ARG;
-    if (prec != TC_PREC_FP32 && prec != TC_PREC_TF32_REFINE && prec != TC_PREC_BF16_REFINE &&
-        prec != TC_PREC_FP32_REFINE)
+    const int form = prec & ~TC_PREC_CHOL32;
+    if (form != TC_PREC_FP32 && form != TC_PREC_TF32_REFINE && form != TC_PREC_BF16_REFINE &&
+        form != TC_PREC_FP32_REFINE)
         return TC_ERR_ARG;
     tc_status rc = launch_solve_factor(p, w, s, R, factors, mode, rhs, lambda, prec, out,
                                        row_status, 0, TC_LOSS_LS, nullptr, (cudaStream_t)stream);

@@ -23,6 +23,8 @@
 // (L L^T)^-1 = L^-T L^-1 for the preconditioner.  For R <= 32 one lane owns
 // one row (every FP64 instruction does a warp of useful work); for R > 32 a
 // warp owns one row and the trailing updates are spread evenly over the lanes.
+#include <type_traits>
+
 #include "internal.cuh"
 
 namespace tc {
@@ -82,6 +84,13 @@ __device__ __forceinline__ double rsqrt_nr(double d) {
     y = y * (1.5 - h * y * y);
     y = y * (1.5 - h * y * y);
     return y;
+}
+
+// The same in FP32 (for the FP32 factorization of the refined forms): the
+// hardware estimate and one Newton step.
+__device__ __forceinline__ float rsqrt_nr(float d) {
+    const float y = rsqrtf(d);
+    return y * (1.5f - 0.5f * d * y * y);
 }
 
 // Slot of a nonempty row [rs, re) that crosses a chunk boundary: the first
@@ -1042,17 +1051,18 @@ __device__ __forceinline__ void gram_source(const SolveParams<T> &P, const Batch
 // accesses on distinct banks).  With refinement the factor L is written back
 // over the batch's Gram rows (pattern dtype; a zero first entry marks a row
 // that did not factor) for the correction step.
-template <typename T>
+template <typename T, typename CT>
 __global__ void __launch_bounds__(32) chol_rows_kernel(const SolveParams<T> P, const Batch<T> B,
                                                        int rpw) {
-    extern __shared__ __align__(16) double sh[];
+    extern __shared__ __align__(16) unsigned char sh_raw[];
+    CT *sh = reinterpret_cast<CT *>(sh_raw);
     const int lane = threadIdx.x;
     const int R = P.R, tri = R * (R + 1) / 2, ps = rpw + 1;
     const int64_t grp = blockIdx.x;
     const int64_t nb = __ldg(P.row_ptr + B.row0);
-    double *Tri = sh;
-    double *Vv = sh + (int64_t)tri * ps;
-    double *Dinv = Vv + (int64_t)R * ps;
+    CT *Tri = sh;
+    CT *Vv = sh + (int64_t)tri * ps;
+    CT *Dinv = Vv + (int64_t)R * ps;
     {
         // every lane finds its own row's Gram (in parallel), then the warp
         // copies all rows' triangles in one flat loop, the row pointers
@@ -1085,26 +1095,26 @@ __global__ void __launch_bounds__(32) chol_rows_kernel(const SolveParams<T> P, c
 #define TC_VEC(r) Vv[(r) * ps + slot]
 #define TC_DINV(r) Dinv[(r) * ps + slot]
     if (mine) {
-        for (int r = 0; r < R; ++r) TC_TRI(r, r) += P.lambda;
+        for (int r = 0; r < R; ++r) TC_TRI(r, r) += (CT)P.lambda;
         bool ok = true;
         for (int j = 0; j < R; ++j) {
-            const double dj = TC_TRI(j, j);
-            if (!(dj > 0.0)) {
+            const CT dj = TC_TRI(j, j);
+            if (!(dj > CT(0))) {
                 ok = false;
                 break;
             }
-            const double inv = rsqrt_nr(dj), ljj = dj * inv;
+            const CT inv = rsqrt_nr(dj), ljj = dj * inv;
             TC_TRI(j, j) = ljj;
             TC_DINV(j) = inv;
             for (int r = j + 1; r < R; ++r) TC_TRI(r, j) *= inv;
             for (int r = j + 1; r < R; ++r) {
-                const double lrj = TC_TRI(r, j);
+                const CT lrj = TC_TRI(r, j);
                 // four entries per pass, loads before stores (independent FMAs)
                 int k = j + 1;
                 for (; k + 3 <= r; k += 4) {
-                    const double a0 = TC_TRI(r, k), a1 = TC_TRI(r, k + 1), a2 = TC_TRI(r, k + 2),
+                    const CT a0 = TC_TRI(r, k), a1 = TC_TRI(r, k + 1), a2 = TC_TRI(r, k + 2),
                                  a3 = TC_TRI(r, k + 3);
-                    const double b0 = TC_TRI(k, j), b1 = TC_TRI(k + 1, j), b2 = TC_TRI(k + 2, j),
+                    const CT b0 = TC_TRI(k, j), b1 = TC_TRI(k + 1, j), b2 = TC_TRI(k + 2, j),
                                  b3 = TC_TRI(k + 3, j);
                     TC_TRI(r, k) = a0 - lrj * b0;
                     TC_TRI(r, k + 1) = a1 - lrj * b1;
@@ -1121,12 +1131,12 @@ __global__ void __launch_bounds__(32) chol_rows_kernel(const SolveParams<T> P, c
                 T *Po = P.pinv + i * (int64_t)R * R;
                 for (int q = 0; q < R * R; ++q) Po[q] = (q / R == q % R) ? T(1) : T(0);
             }
-            TC_TRI(0, 0) = 0.0;
+            TC_TRI(0, 0) = CT(0);
         } else {
             if (P.row_status) P.row_status[i] = 0;
             if (!P.pinv) {
                 for (int r = 0; r < R; ++r) {           // L y = b
-                    double v0 = (double)P.rhs[i * (int64_t)R + r], v1 = 0.0, v2 = 0.0, v3 = 0.0;
+                    CT v0 = (CT)P.rhs[i * (int64_t)R + r], v1 = CT(0), v2 = CT(0), v3 = CT(0);
                     int k = 0;
                     for (; k + 3 < r; k += 4) {
                         v0 -= TC_TRI(r, k) * TC_VEC(k);
@@ -1138,7 +1148,7 @@ __global__ void __launch_bounds__(32) chol_rows_kernel(const SolveParams<T> P, c
                     TC_VEC(r) = ((v0 + v1) + (v2 + v3)) * TC_DINV(r);
                 }
                 for (int r = R - 1; r >= 0; --r) {      // L^T x = y
-                    double v0 = TC_VEC(r), v1 = 0.0, v2 = 0.0, v3 = 0.0;
+                    CT v0 = TC_VEC(r), v1 = CT(0), v2 = CT(0), v3 = CT(0);
                     int k = r + 1;
                     for (; k + 3 < R; k += 4) {
                         v0 -= TC_TRI(k, r) * TC_VEC(k);
@@ -1156,7 +1166,7 @@ __global__ void __launch_bounds__(32) chol_rows_kernel(const SolveParams<T> P, c
                 for (int j = 0; j < R; ++j) {
                     TC_TRI(j, j) = TC_DINV(j);
                     for (int r = j + 1; r < R; ++r) {
-                        double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+                        CT v0 = CT(0), v1 = CT(0), v2 = CT(0), v3 = CT(0);
                         int k = j;
                         for (; k + 3 < r; k += 4) {
                             v0 += TC_TRI(r, k) * TC_TRI(k, j);
@@ -1172,7 +1182,7 @@ __global__ void __launch_bounds__(32) chol_rows_kernel(const SolveParams<T> P, c
                 T *Po = P.pinv + i * (int64_t)R * R;
                 for (int r = 0; r < R; ++r)
                     for (int c = 0; c <= r; ++c) {
-                        double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+                        CT v0 = CT(0), v1 = CT(0), v2 = CT(0), v3 = CT(0);
                         int k = r;
                         for (; k + 3 < R; k += 4) {
                             v0 += TC_TRI(k, r) * TC_TRI(k, c);
@@ -1181,7 +1191,7 @@ __global__ void __launch_bounds__(32) chol_rows_kernel(const SolveParams<T> P, c
                             v3 += TC_TRI(k + 3, r) * TC_TRI(k + 3, c);
                         }
                         for (; k < R; ++k) v0 += TC_TRI(k, r) * TC_TRI(k, c);
-                        const double v = (v0 + v1) + (v2 + v3);
+                        const CT v = (v0 + v1) + (v2 + v3);
                         Po[r * R + c] = (T)v;
                         Po[c * R + r] = (T)v;
                     }
@@ -1209,10 +1219,11 @@ __global__ void __launch_bounds__(32) chol_rows_kernel(const SolveParams<T> P, c
 // decode table (rr, kk) shared by the block, so every lane does the same work.
 constexpr int kCholWarps = 4;
 
-template <typename T>
+template <typename T, typename CT>
 __global__ void __launch_bounds__(kCholWarps * 32) chol_warp_kernel(const SolveParams<T> P,
                                                                     const Batch<T> B) {
-    extern __shared__ __align__(16) double sh[];
+    extern __shared__ __align__(16) unsigned char sh_raw[];
+    CT *sh = reinterpret_cast<CT *>(sh_raw);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int R = P.R, tri = R * (R + 1) / 2;
     const bool inv_mode = P.pinv != nullptr;
@@ -1224,10 +1235,10 @@ __global__ void __launch_bounds__(kCholWarps * 32) chol_warp_kernel(const SolveP
         tab[e] = ((uint32_t)r << 16) | (uint32_t)c;
     }
     __syncthreads();
-    double *S = sh + (size_t)w * per_warp;
-    double *Y = S + tri;                         // L^-1 (inverse mode)
-    double *bv = S + tri * (inv_mode ? 2 : 1);
-    double *Dinv = bv + R;
+    CT *S = sh + (size_t)w * per_warp;
+    CT *Y = S + tri;                         // L^-1 (inverse mode)
+    CT *bv = S + tri * (inv_mode ? 2 : 1);
+    CT *Dinv = bv + R;
     const int64_t nb = __ldg(P.row_ptr + B.row0);
     for (int64_t q = (int64_t)blockIdx.x * kCholWarps + w; q < B.nrows;
          q += (int64_t)gridDim.x * kCholWarps) {
@@ -1237,16 +1248,16 @@ __global__ void __launch_bounds__(kCholWarps * 32) chol_warp_kernel(const SolveP
         gram_source(P, B, nb, i, tri, lrow, crow);
         for (int e = lane; e < tri; e += 32) S[e] = gram_entry(lrow, crow, e);
         __syncwarp();
-        for (int r = lane; r < R; r += 32) S[tri_idx(r, r)] += P.lambda;
+        for (int r = lane; r < R; r += 32) S[tri_idx(r, r)] += (CT)P.lambda;
         __syncwarp();
         bool ok = true;
         for (int j = 0; j < R; ++j) {
-            const double dj = S[tri_idx(j, j)];
-            if (!(dj > 0.0)) {       // same value in every lane: a uniform exit
+            const CT dj = S[tri_idx(j, j)];
+            if (!(dj > CT(0))) {       // same value in every lane: a uniform exit
                 ok = false;
                 break;
             }
-            const double inv = rsqrt_nr(dj), ljj = dj * inv;
+            const CT inv = rsqrt_nr(dj), ljj = dj * inv;
             __syncwarp();
             for (int r = j + 1 + lane; r < R; r += 32) S[tri_idx(r, j)] *= inv;
             if (lane == 0) {
@@ -1280,17 +1291,17 @@ __global__ void __launch_bounds__(kCholWarps * 32) chol_warp_kernel(const SolveP
         if (!inv_mode) {
             if (P.refine)
                 for (int e = lane; e < tri; e += 32) lout[e] = (T)S[e];
-            for (int r = lane; r < R; r += 32) bv[r] = (double)P.rhs[i * (int64_t)R + r];
+            for (int r = lane; r < R; r += 32) bv[r] = (CT)P.rhs[i * (int64_t)R + r];
             __syncwarp();
             for (int j = 0; j < R; ++j) {        // L y = b
-                const double yj = bv[j] * Dinv[j];
+                const CT yj = bv[j] * Dinv[j];
                 __syncwarp();
                 for (int r = j + 1 + lane; r < R; r += 32) bv[r] -= S[tri_idx(r, j)] * yj;
                 if (lane == 0) bv[j] = yj;
                 __syncwarp();
             }
             for (int j = R - 1; j >= 0; --j) {   // L^T x = y
-                const double xj = bv[j] * Dinv[j];
+                const CT xj = bv[j] * Dinv[j];
                 __syncwarp();
                 for (int r = lane; r < j; r += 32) bv[r] -= S[tri_idx(j, r)] * xj;
                 if (lane == 0) bv[j] = xj;
@@ -1308,7 +1319,7 @@ __global__ void __launch_bounds__(kCholWarps * 32) chol_warp_kernel(const SolveP
             if (c < 0 || c >= R || (pass == 1 && c < 32)) continue;
             Y[tri_idx(c, c)] = Dinv[c];
             for (int r = c + 1; r < R; ++r) {
-                double v = 0.0;
+                CT v = CT(0);
                 for (int k = c; k < r; ++k) v += S[tri_idx(r, k)] * Y[tri_idx(k, c)];
                 Y[tri_idx(r, c)] = -v * Dinv[r];
             }
@@ -1319,7 +1330,7 @@ __global__ void __launch_bounds__(kCholWarps * 32) chol_warp_kernel(const SolveP
         for (int e = lane; e < tri; e += 32) {
             const uint32_t rc = tab[e];
             const int r = (int)(rc >> 16), c = (int)(rc & 0xffffu);
-            double v = 0.0;
+            CT v = CT(0);
             for (int k = r; k < R; ++k) v += Y[tri_idx(k, r)] * Y[tri_idx(k, c)];
             Po[r * R + c] = (T)v;
             Po[c * R + r] = (T)v;
@@ -1333,9 +1344,13 @@ __global__ void __launch_bounds__(kCholWarps * 32) chol_warp_kernel(const SolveP
 //   res_i = rhs_i - lambda a_i - sum_{e in row i} s_e h_e (h_e^T a_i),
 //   a_i  += (L_i L_i^T)^-1 res_i,
 // with L_i the row's Cholesky factor.  Kernel C accumulates the sum over the
-// nonzeros in FP64 (h_e formed in FP64 from the stored factors, so exactly
-// for FP32 data) with the same chunked traversal as the Gram (a warp per
-// chunk, FP64 atomics into a zeroed buffer).  Kernel D forms res_i and applies
+// nonzeros with the same chunked traversal as the Gram (a warp per chunk,
+// FP64 atomics into a zeroed buffer), in FP64 arithmetic for FP64 data and in
+// double-float arithmetic for FP32 data: h_e = b (.) e split exactly into two
+// FP32 words by a fused multiply-add, products and sums carried as FP32 pairs
+// by error-free transforms (Dekker's product, Knuth's TwoSum), about 48
+// significant bits at FP32 speed -- FP64 runs at about one operation per
+// clock per SM on this GPU.  Kernel D forms res_i and applies
 // the correction with the stored factor, one warp per row.
 template <typename T, int RT, bool VEC>
 __global__ void __launch_bounds__(128) refine_resid_kernel(const SolveParams<T> P, const Batch<T> B,
@@ -1357,36 +1372,106 @@ __global__ void __launch_bounds__(128) refine_resid_kernel(const SolveParams<T> 
             const int64_t ss = max(rs, cs), se = min(re, ce);
             T a32[V];
             load_slice<T, V, false>(a32, P.out, i, R, lg);
-            double av[V], acc[V];
+            if constexpr (sizeof(T) == 4) {
+                // double-float (pairs of FP32 words, error-free transforms):
+                // h = b e exactly as (hh, hl); z = <h, a> and the sums
+                // s z h accumulated as (hi, lo) pairs, about 48 significant bits
+                float ah[V], al[V];
 #pragma unroll
-            for (int t = 0; t < V; ++t) {
-                av[t] = (double)a32[t];
-                acc[t] = 0.0;
-            }
-            for (int64_t base = ss; base < se; base += NG) {
-                const bool valid = base + g < se;
-                const int64_t qq = valid ? base + g : se - 1;
-                T b[V], e[V];
-                load_slice<T, V, VEC>(b, P.A1, __ldcs(P.c1 + qq), R, lg);
-                load_slice<T, V, VEC>(e, P.A2, __ldcs(P.c2 + qq), R, lg);
-                double h[V], part = 0.0;
+                for (int t = 0; t < V; ++t) ah[t] = al[t] = 0.f;
+                for (int64_t base = ss; base < se; base += NG) {
+                    const bool valid = base + g < se;
+                    const int64_t qq = valid ? base + g : se - 1;
+                    T b[V], e[V];
+                    load_slice<T, V, VEC>(b, P.A1, __ldcs(P.c1 + qq), R, lg);
+                    load_slice<T, V, VEC>(e, P.A2, __ldcs(P.c2 + qq), R, lg);
+                    float hh[V], hl[V], zh = 0.f, zl = 0.f;
+#pragma unroll
+                    for (int t = 0; t < V; ++t) {
+                        // __fmul_rn: products that enter TwoSum must not be
+                        // contracted into a fused multiply-add
+                        hh[t] = __fmul_rn(b[t], e[t]);
+                        hl[t] = fmaf(b[t], e[t], -hh[t]);
+                        const float pr = __fmul_rn(hh[t], a32[t]);
+                        const float pe = fmaf(hh[t], a32[t], -pr) + hl[t] * a32[t];
+                        float sm, er;
+                        two_sum(zh, pr, sm, er);
+                        zh = sm;
+                        zl += er + pe;
+                    }
+#pragma unroll
+                    for (int o = G / 2; o > 0; o >>= 1) {
+                        const float h2 = __shfl_xor_sync(0xffffffffu, zh, o);
+                        const float l2 = __shfl_xor_sync(0xffffffffu, zl, o);
+                        float sm, er;
+                        two_sum(zh, h2, sm, er);
+                        zh = sm;
+                        zl += er + l2;
+                    }
+                    const float sw = valid ? (float)weight_at(P.w, qq) : 0.f;
+                    const float ch = __fmul_rn(sw, zh);
+                    const float cl = fmaf(sw, zh, -ch) + sw * zl;
+#pragma unroll
+                    for (int t = 0; t < V; ++t) {
+                        const float pr = __fmul_rn(ch, hh[t]);
+                        const float pe = fmaf(ch, hh[t], -pr) + (ch * hl[t] + cl * hh[t]);
+                        float sm, er;
+                        two_sum(ah[t], pr, sm, er);
+                        ah[t] = sm;
+                        al[t] += er + pe;
+                    }
+                }
+                // sum the nonzero groups (lanes with equal lg)
 #pragma unroll
                 for (int t = 0; t < V; ++t) {
-                    h[t] = (double)b[t] * (double)e[t];
-                    part += h[t] * av[t];
+#pragma unroll
+                    for (int o = G; o < 32; o <<= 1) {
+                        const float h2 = __shfl_xor_sync(0xffffffffu, ah[t], o);
+                        const float l2 = __shfl_xor_sync(0xffffffffu, al[t], o);
+                        float sm, er;
+                        two_sum(ah[t], h2, sm, er);
+                        ah[t] = sm;
+                        al[t] += er + l2;
+                    }
                 }
-                const double z = group_sum<G>(part);
-                const double coef = valid ? (double)weight_at(P.w, qq) * z : 0.0;
+                if (g == 0) {
+                    double *dst = B.res + (i - B.row0) * (int64_t)R + lg * V;
 #pragma unroll
-                for (int t = 0; t < V; ++t) acc[t] += coef * h[t];
-            }
+                    for (int t = 0; t < V; ++t)
+                        if (lg * V + t < R) atomicAdd(dst + t, -((double)ah[t] + (double)al[t]));
+                }
+            } else {
+                double av[V], acc[V];
 #pragma unroll
-            for (int t = 0; t < V; ++t) acc[t] = across_groups<G>(acc[t]);
-            if (g == 0) {
-                double *dst = B.res + (i - B.row0) * (int64_t)R + lg * V;
+                for (int t = 0; t < V; ++t) {
+                    av[t] = (double)a32[t];
+                    acc[t] = 0.0;
+                }
+                for (int64_t base = ss; base < se; base += NG) {
+                    const bool valid = base + g < se;
+                    const int64_t qq = valid ? base + g : se - 1;
+                    T b[V], e[V];
+                    load_slice<T, V, VEC>(b, P.A1, __ldcs(P.c1 + qq), R, lg);
+                    load_slice<T, V, VEC>(e, P.A2, __ldcs(P.c2 + qq), R, lg);
+                    double h[V], part = 0.0;
 #pragma unroll
-                for (int t = 0; t < V; ++t)
-                    if (lg * V + t < R) atomicAdd(dst + t, -acc[t]);
+                    for (int t = 0; t < V; ++t) {
+                        h[t] = (double)b[t] * (double)e[t];
+                        part += h[t] * av[t];
+                    }
+                    const double z = group_sum<G>(part);
+                    const double coef = valid ? (double)weight_at(P.w, qq) * z : 0.0;
+#pragma unroll
+                    for (int t = 0; t < V; ++t) acc[t] += coef * h[t];
+                }
+#pragma unroll
+                for (int t = 0; t < V; ++t) acc[t] = across_groups<G>(acc[t]);
+                if (g == 0) {
+                    double *dst = B.res + (i - B.row0) * (int64_t)R + lg * V;
+#pragma unroll
+                    for (int t = 0; t < V; ++t)
+                        if (lg * V + t < R) atomicAdd(dst + t, -acc[t]);
+                }
             }
             if (re >= ce) break;
             i = search_le(P.row_ptr, i + 1, last, re);   // next nonempty row
@@ -1508,9 +1593,10 @@ struct GramLaunch {
     }
 };
 
-template <typename T, int RT, bool VEC, int KIND>
+template <typename T, int RT, bool VEC, int KIND, bool CHOL32>
 static tc_status launch_solve_rt(const SolveParams<T> &P, int64_t m, cudaStream_t st) {
     using GL = GramLaunch<T, RT, VEC, KIND>;
+    using CT = typename std::conditional<CHOL32, float, double>::type;   // factorization type
     const int R = P.R, tri = R * (R + 1) / 2;
     const int sms = device_sms();
     int occ = 1;
@@ -1534,15 +1620,15 @@ static tc_status launch_solve_rt(const SolveParams<T> &P, int64_t m, cudaStream_
     const int align = warp_b ? kCholWarps : rpw;
     size_t smem_b;
     if (warp_b)
-        smem_b = sizeof(double) * (size_t)kCholWarps * (tri * (P.pinv ? 2 : 1) + 2 * R) +
+        smem_b = sizeof(CT) * (size_t)kCholWarps * (tri * (P.pinv ? 2 : 1) + 2 * R) +
                  sizeof(uint32_t) * tri;
     else
-        smem_b = sizeof(double) * (size_t)(tri + 2 * R) * (rpw + 1);
+        smem_b = sizeof(CT) * (size_t)(tri + 2 * R) * (rpw + 1);
     if (warp_b) {
-        auto kb = chol_warp_kernel<T>;
+        auto kb = chol_warp_kernel<T, CT>;
         TC_CUDA(cudaFuncSetAttribute(kb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b));
     } else if (smem_b > 48 * 1024) {
-        auto kb = chol_rows_kernel<T>;
+        auto kb = chol_rows_kernel<T, CT>;
         TC_CUDA(cudaFuncSetAttribute(kb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b));
     }
 
@@ -1573,9 +1659,9 @@ static tc_status launch_solve_rt(const SolveParams<T> &P, int64_t m, cudaStream_
         int64_t nblk_w = (Bt.nrows + kCholWarps - 1) / kCholWarps;
         if (nblk_w > nblk_w0) nblk_w = nblk_w0;
         if (warp_b)
-            chol_warp_kernel<T><<<(unsigned)nblk_w, kCholWarps * 32, smem_b, st>>>(P, Bt);
+            chol_warp_kernel<T, CT><<<(unsigned)nblk_w, kCholWarps * 32, smem_b, st>>>(P, Bt);
         else
-            chol_rows_kernel<T><<<(unsigned)((Bt.nrows + rpw - 1) / rpw), 32, smem_b, st>>>(P, Bt, rpw);
+            chol_rows_kernel<T, CT><<<(unsigned)((Bt.nrows + rpw - 1) / rpw), 32, smem_b, st>>>(P, Bt, rpw);
         count_launch(3);
         if (P.refine) {
             TC_CUDA(cudaMemsetAsync(res, 0, sizeof(double) * (size_t)R * Bt.nrows, st));
@@ -1593,14 +1679,14 @@ static tc_status launch_solve_rt(const SolveParams<T> &P, int64_t m, cudaStream_
                : TC_ERR_CUDA;
 }
 
-template <typename T, int KIND>
+template <typename T, int KIND, bool C32>
 static tc_status dispatch_rt(const SolveParams<T> &P, int tier, bool vec, int64_t m,
                              cudaStream_t st) {
     switch (tier) {
-        case 8: return vec ? launch_solve_rt<T, 8, true, KIND>(P, m, st) : launch_solve_rt<T, 8, false, KIND>(P, m, st);
-        case 16: return vec ? launch_solve_rt<T, 16, true, KIND>(P, m, st) : launch_solve_rt<T, 16, false, KIND>(P, m, st);
-        case 32: return vec ? launch_solve_rt<T, 32, true, KIND>(P, m, st) : launch_solve_rt<T, 32, false, KIND>(P, m, st);
-        default: return vec ? launch_solve_rt<T, 64, true, KIND>(P, m, st) : launch_solve_rt<T, 64, false, KIND>(P, m, st);
+        case 8: return vec ? launch_solve_rt<T, 8, true, KIND, C32>(P, m, st) : launch_solve_rt<T, 8, false, KIND, C32>(P, m, st);
+        case 16: return vec ? launch_solve_rt<T, 16, true, KIND, C32>(P, m, st) : launch_solve_rt<T, 16, false, KIND, C32>(P, m, st);
+        case 32: return vec ? launch_solve_rt<T, 32, true, KIND, C32>(P, m, st) : launch_solve_rt<T, 32, false, KIND, C32>(P, m, st);
+        default: return vec ? launch_solve_rt<T, 64, true, KIND, C32>(P, m, st) : launch_solve_rt<T, 64, false, KIND, C32>(P, m, st);
     }
 }
 
@@ -1630,7 +1716,7 @@ static tc_status solve_t(const tc_pattern *p, tc_weights w, const void *s, int R
     P.lambda = lambda;
     P.R = R;
     P.status = p->status;
-    P.refine = (!pinv && prec != TC_PREC_FP32) ? 1 : 0;
+    P.refine = (!pinv && (prec & ~TC_PREC_CHOL32) != TC_PREC_FP32) ? 1 : 0;
     if (!use_d2) {
         P.w.kind = (int)w;
         P.w.s = nullptr;
@@ -1650,7 +1736,8 @@ static tc_status solve_t(const tc_pattern *p, tc_weights w, const void *s, int R
     const bool vec = vec_ok(R, tier, sizeof(T)) && aligned16({A[o1], A[o2]}) &&
                      (!use_d2 || aligned16({A[mode]}));
     const int64_t m = p->nnz;
-    if (sizeof(T) == 8 && (prec == TC_PREC_TF32_REFINE || prec == TC_PREC_BF16_REFINE))
+    if (sizeof(T) == 8 && ((prec & ~TC_PREC_CHOL32) == TC_PREC_TF32_REFINE ||
+                           (prec & ~TC_PREC_CHOL32) == TC_PREC_BF16_REFINE))
         return TC_ERR_UNSUPPORTED;
     // the correction step reads rhs after the solve wrote out: keep a copy
     // when they alias
@@ -1665,12 +1752,21 @@ static tc_status solve_t(const tc_pattern *p, tc_weights w, const void *s, int R
         P.rhs = rhs_copy;
     }
     tc_status rc = TC_OK;
+    const tc_prec form = (tc_prec)(prec & ~TC_PREC_CHOL32);
+    const bool c32 = (prec & TC_PREC_CHOL32) != 0 && P.refine;
     if constexpr (sizeof(T) == 4) {
-        if (prec == TC_PREC_TF32_REFINE) rc = dispatch_rt<T, GK_TF32>(P, tier, vec, m, st);
-        else if (prec == TC_PREC_BF16_REFINE) rc = dispatch_rt<T, GK_BF16>(P, tier, vec, m, st);
-        else rc = dispatch_rt<T, GK_TF32X3>(P, tier, vec, m, st);
+        if (form == TC_PREC_TF32_REFINE)
+            rc = c32 ? dispatch_rt<T, GK_TF32, true>(P, tier, vec, m, st)
+                     : dispatch_rt<T, GK_TF32, false>(P, tier, vec, m, st);
+        else if (form == TC_PREC_BF16_REFINE)
+            rc = c32 ? dispatch_rt<T, GK_BF16, true>(P, tier, vec, m, st)
+                     : dispatch_rt<T, GK_BF16, false>(P, tier, vec, m, st);
+        else
+            rc = c32 ? dispatch_rt<T, GK_TF32X3, true>(P, tier, vec, m, st)
+                     : dispatch_rt<T, GK_TF32X3, false>(P, tier, vec, m, st);
     } else {
-        rc = dispatch_rt<T, GK_FFMA>(P, tier, vec, m, st);
+        rc = c32 ? dispatch_rt<T, GK_FFMA, true>(P, tier, vec, m, st)
+                 : dispatch_rt<T, GK_FFMA, false>(P, tier, vec, m, st);
     }
     if (rhs_copy && cudaFreeAsync(rhs_copy, st) != cudaSuccess && rc == TC_OK) rc = TC_ERR_CUDA;
     return rc;

@@ -22,6 +22,9 @@ F32, F64 = 0, 1
 LOSSES = {"ls": 0, "poisson_log": 1, "poisson_id": 2}
 W_ONE, W_VALUES, W_ARRAY = 0, 1, 2
 PRECS = {"fp32": 0, "tf32_refine": 1, "bf16_refine": 2, "fp32_refine": 3}
+CHOL32 = 0x100
+# the refined forms with an FP32 factorization
+PRECS.update({k + "_chol32": v | CHOL32 for k, v in list(PRECS.items()) if k.endswith("_refine")})
 CHECK_DUPLICATES = 1
 REFILLABLE = 2
 

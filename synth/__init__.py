@@ -145,6 +145,9 @@ def distinct_coords(dims, nnz, dists, seed, zipf_s=1.1):
     prng = stream(seed, _S_PERM)
     perms = [prng.permutation(I).astype(np.int64) for I in dims]
     cols = [np.zeros(0, np.int32) for _ in dims]
+    parts = [[] for _ in dims]
+    seen = None               # sorted keys kept so far (linear keys only)
+    linear = total < (1 << 62)
     have = 0
     rounds = 0
     while have < nnz:
@@ -153,14 +156,32 @@ def distinct_coords(dims, nnz, dists, seed, zipf_s=1.1):
         if total - have < 4 * need:   # nearly full tensors: draw more per round
             n = max(n, 4 * need)
         new = _draw(dims, n, dists, zipf_s, rng, perms)
-        cols = [np.concatenate([a, b]) for a, b in zip(cols, new)]
-        _, first = np.unique(_keys(cols, dims), return_index=True)
-        first.sort()
-        cols = [c[first] for c in cols]
-        have = cols[0].shape[0]
+        if linear:
+            # keep the first occurrence of every key not seen in earlier rounds,
+            # in draw order: the same coordinates as deduplicating the whole
+            # draw sequence at once, without re-sorting earlier rounds
+            keys = _keys(new, dims)
+            uk, first = np.unique(keys, return_index=True)
+            if seen is not None and seen.size:
+                pos = np.minimum(np.searchsorted(seen, uk), seen.size - 1)
+                fresh = seen[pos] != uk
+                uk, first = uk[fresh], first[fresh]
+            first.sort()
+            for d in range(len(dims)):
+                parts[d].append(new[d][first])
+            seen = uk if seen is None else np.sort(np.concatenate([seen, uk]), kind="stable")
+            have += first.shape[0]
+        else:
+            cols = [np.concatenate([a, b]) for a, b in zip(cols, new)]
+            _, first = np.unique(_keys(cols, dims), return_index=True)
+            first.sort()
+            cols = [c[first] for c in cols]
+            have = cols[0].shape[0]
         rounds += 1
         if rounds > 200:
             raise RuntimeError("could not draw enough distinct coordinates")
+    if linear:
+        cols = [np.concatenate(pp) for pp in parts]
     return [np.ascontiguousarray(c[:nnz]) for c in cols]
 
 

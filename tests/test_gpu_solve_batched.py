@@ -154,6 +154,10 @@ def test_refined_solve_ill_conditioned(tc, name):
         rd = to_dev(rhs, prob.dtype)
         out = host(tc.solve_factor(p, A, mode, rd, lam, prec="fp32_refine"))
         assert rel(out, ref) <= TOL[prob.dtype], (name, mode)
+        # the same with an FP32 factorization: the refinement step corrects
+        # its rounding as well
+        out = host(tc.solve_factor(p, A, mode, rd, lam, prec="fp32_refine_chol32"))
+        assert rel(out, ref) <= TOL[prob.dtype], (name, mode, "chol32")
         # out aliasing rhs: the correction must still see the original rhs
         alias = rd.clone()
         tc.solve_factor(p, A, mode, alias, lam, out=alias, prec="fp32_refine")
@@ -167,10 +171,12 @@ def test_refined_solve_ill_conditioned(tc, name):
 # one step leaves 1e-6 .. 1e-4 (measured and stated with the design), while a
 # well-conditioned uniform tensor reaches 1e-6
 OBJ_TOL = {("tf32_refine", None): 1e-6, ("bf16_refine", None): 1e-4,
-           ("bf16_refine", "uni_f32_r16"): 1e-6}
+           ("bf16_refine", "uni_f32_r16"): 1e-6, ("tf32_refine_chol32", None): 1e-6,
+           ("bf16_refine_chol32", None): 1e-4, ("bf16_refine_chol32", "uni_f32_r16"): 1e-6}
 
 
-@pytest.mark.parametrize("prec", ["tf32_refine", "bf16_refine"])
+@pytest.mark.parametrize("prec", ["tf32_refine", "bf16_refine", "tf32_refine_chol32",
+                                  "bf16_refine_chol32"])
 @pytest.mark.parametrize("name", ["zipf_f32_r64", "zipf_f32_r16", "f32_r40", "uni_f32_r16"])
 def test_mixed_precision_objective(tc, name, prec):
     """Tensor-core Gram (TF32 or BF16 inputs) + one refinement step: one ALS
