@@ -13,6 +13,11 @@ routines the way the paper composes its kernels:
   mode in turn, the right-hand side is the MTTKRP of the observed values, then
   Solve Factor with the pattern (unit weights) and lambda; the new factor is
   used at once (block Gauss-Seidel, Appendix A).
+* General-loss ALS (Sec. 2.2, last paragraph; tolerances of Sec. 5.7): for each
+  mode in turn, Newton steps on that factor with the others fixed -- gradient
+  MTTKRP(phi') + 2 lambda A, the row Hessians sum phi'' h h^T + 2 lambda I
+  solved through Solve Factor with weights phi'' -- until the step is small
+  relative to the factor or an iteration cap is reached.
 * Gauss-Newton step (Sec. 2.5): gradient, block-diagonal preconditioner (the
   diagonal blocks of the Gauss-Newton matrix, applied through Solve Factor with
   weights phi'' and regularization 2 lambda), preconditioned CG from zero for a
@@ -283,3 +288,40 @@ def ggn_step(dims, idx, t, factors, loss, lam, n_iter, precondition=True):
 
 def objective(dims, idx, t, factors, loss, lam):
     return loss_grad(dims, idx, t, factors, loss, lam, want_grad=False)[0]
+
+
+def loss_derivs(dims, idx, t, factors, loss):
+    """phi' and phi'' at every observed entry (input order), at the model
+    entries of `factors` (Table 1 notation, Sec. 2.1 / 5.7 losses)."""
+    _, d1, d2 = loss_terms(loss, t, model_entries(dims, idx, factors))
+    return d1, d2
+
+
+def newton_als_mode(dims, idx, t, factors, mode, loss, lam, inner_iters=5, tol=1e-3):
+    """Newton iterations on factor `mode` with the others fixed (Sec. 2.2: the
+    per-row Newton step for a general loss, gradient and Hessian of Table 1):
+      g = MTTKRP(phi', mode) + 2 lam A,   H_i = sum_e phi''_e h_e h_e^T + 2 lam I,
+      A <- A - H^-1 g   (row by row, through Solve Factor with weights phi''),
+    stopping when ||step||_F <= tol ||A||_F (a reading: one test for the whole
+    factor) or after inner_iters steps.  Returns (factors, steps taken)."""
+    A = [_f64(a).copy() for a in factors]
+    taken = 0
+    for _ in range(inner_iters):
+        d1, d2 = loss_derivs(dims, idx, t, A, loss)
+        g = mttkrp(dims, idx, d1, A, mode) + 2.0 * lam * A[mode]
+        step, _, rc = solve_factor(dims, idx, d2, A, mode, -g, 2.0 * lam)
+        if rc != OK:
+            raise OracleError(rc, "newton_als_mode")
+        A[mode] = A[mode] + step
+        taken += 1
+        if np.linalg.norm(step) <= tol * np.linalg.norm(A[mode]):
+            break
+    return A, taken
+
+
+def newton_als_sweep(dims, idx, t, factors, loss, lam, inner_iters=5, tol=1e-3):
+    """One general-loss ALS sweep: newton_als_mode for modes 0, 1, 2 in order."""
+    A = [_f64(a).copy() for a in factors]
+    for d in range(len(dims)):
+        A, _ = newton_als_mode(dims, idx, t, A, d, loss, lam, inner_iters, tol)
+    return A

@@ -379,3 +379,61 @@ def test_precond_is_block_diagonal_inverse(rng):
         for l in range(dims[p]):
             sl = slice(offs[p] + l * R, offs[p] + (l + 1) * R)
             np.testing.assert_allclose(z[sl], np.linalg.solve(H[sl, sl], fr[sl]), rtol=1e-12, atol=1e-12)
+
+
+# ------------------------------------------------------------ general-loss ALS (Sec. 2.2)
+def test_newton_als_ls_one_step_is_als_solve(rng):
+    """For least squares the block objective is quadratic, so one Newton step
+    from any starting factor lands on the block minimizer, which is the ALS
+    solve (G_i + lambda I) a_i = sum_e h_e t_e (Sec. 2.2) -- here by dense
+    normal equations per row."""
+    dims = (7, 6, 5)
+    idx, A, _ = rand_case(rng, dims, density=0.6, R=3)
+    t = rng.standard_normal(len(idx[0]))
+    lam = 0.3
+    for mode in range(3):
+        got, taken = oracle.newton_als_mode(dims, idx, t, A, mode, "ls", lam, inner_iters=1)
+        assert taken == 1
+        o1, o2 = [d for d in range(3) if d != mode]
+        for i in range(dims[mode]):
+            sel = idx[mode] == i
+            H = A[o1][idx[o1][sel]] * A[o2][idx[o2][sel]]
+            want = np.linalg.solve(H.T @ H + lam * np.eye(3), H.T @ t[sel])
+            np.testing.assert_allclose(got[mode][i], want, rtol=1e-10, atol=1e-12)
+        for d in range(3):
+            if d != mode:
+                np.testing.assert_array_equal(got[d], A[d])
+
+
+def test_newton_als_poisson_reaches_block_stationarity():
+    """Poisson with the log link (Sec. 5.7): each row problem is convex, so the
+    Newton iterations drive the gradient of the objective with respect to the
+    factor being updated (pinned by finite differences above) to zero."""
+    dims = (15, 12, 10)
+    idx, planted, _ = small_problem(dims, 700, 3, seed=5, factor="uniform01", recipe="poisson")
+    model = oracle.model_entries(dims, idx, planted)
+    t = synth.observe(model, "poisson", 5)
+    A = [0.7 * a for a in synth.perturb(planted, 5)]
+    lam = 0.1
+    _, g0 = oracle.loss_grad(dims, idx, t, A, "poisson_log", lam)
+    A1, taken = oracle.newton_als_mode(dims, idx, t, A, 0, "poisson_log", lam, inner_iters=40,
+                                       tol=1e-14)
+    _, g1 = oracle.loss_grad(dims, idx, t, A1, "poisson_log", lam)
+    assert np.linalg.norm(g1[0]) <= 1e-9 * np.linalg.norm(g0[0])
+    assert taken >= 2
+
+
+def test_newton_als_poisson_descends():
+    """A general-loss ALS sweep with the paper's inner tolerances (1e-3, at most
+    5 Newton steps) does not increase the Poisson objective."""
+    dims = (20, 18, 16)
+    idx, planted, _ = small_problem(dims, 1500, 4, seed=8, factor="uniform01", recipe="poisson")
+    t = synth.observe(oracle.model_entries(dims, idx, planted), "poisson", 8)
+    A = [0.8 * a for a in synth.perturb(planted, 8)]
+    lam = 0.1
+    f = oracle.objective(dims, idx, t, A, "poisson_log", lam)
+    for _ in range(3):
+        A = oracle.newton_als_sweep(dims, idx, t, A, "poisson_log", lam)
+        f_new = oracle.objective(dims, idx, t, A, "poisson_log", lam)
+        assert f_new <= f * (1 + 1e-12)
+        f = f_new
