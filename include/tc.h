@@ -251,6 +251,24 @@ tc_status tc_loss_grad(const tc_pattern *p, tc_loss loss, int R, const void *con
 tc_status tc_ggn_matvec(const tc_pattern *p, tc_loss loss, int R, const void *const *factors,
                         const void *const *x, double lambda, void *const *y, tc_stream_t stream);
 
+/* ------------------------------------------------------------------ general-loss ALS */
+
+/* General-loss ALS (Sec. 2.2, last paragraph; tolerances as in Sec. 5.7):
+ * Newton steps on factor `mode` with the other factors fixed.  Each step forms
+ * phi', phi'' at the model entries (TTTP), the gradient
+ * g = MTTKRP(phi', mode) + 2 lambda A^(mode), solves per row
+ *   (sum_e phi''_e h_e h_e^T + 2 lambda I) step_i = -g_i
+ * with Solve Factor (weights phi'', precision form `prec`), and sets
+ * A^(mode) += step (in place in factors[mode]).  It stops after inner_iters
+ * steps or as soon as ||step||_F <= tol ||A^(mode)||_F.  For least squares one
+ * step is the ALS solve.  Needs the pattern's values; a domain error (identity
+ * link at m <= 0) or a non-SPD row is recorded for tc_last_error.
+ * steps_out (host, may be NULL) receives the number of steps taken.
+ * Synchronizes `stream` once per step (the stop test reads two norms). */
+tc_status tc_newton_als_mode(const tc_pattern *p, tc_loss loss, int R, void *const *factors,
+                             int mode, double lambda, int inner_iters, double tol, tc_prec prec,
+                             int *steps_out, tc_stream_t stream);
+
 /* ------------------------------------------------------------------ GGN / PCG */
 
 /* A preconditioned-CG solver for the Gauss-Newton system H dx = b at fixed

@@ -93,6 +93,28 @@ __device__ __forceinline__ float rsqrt_nr(float d) {
     return y * (1.5f - 0.5f * d * y * y);
 }
 
+// Exact float -> double widening with integer operations (sign, exponent
+// rebias, mantissa shift), so that the cut-row flushes below keep the SM's
+// FP64 pipe (about one operation per clock per SM on this GPU) free; zero,
+// subnormal, infinite and NaN inputs take the ordinary conversion.
+__device__ __forceinline__ double widen(float f) {
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t ex = (u >> 23) & 0xffu;
+    if (ex == 0u || ex == 0xffu) return (double)f;
+    const uint64_t bits = ((uint64_t)(u >> 31) << 63) | ((uint64_t)(ex + 896u) << 52) |
+                          ((uint64_t)(u & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)bits);
+}
+
+// Adds an FP32 pair (hi + lo) or one FP32 value into an FP64 slot: the
+// additions are FP64 atomics, carried out in the L2 cache.
+__device__ __forceinline__ void add_cut(double *slot, float hi, float lo) {
+    atomicAdd(slot, widen(hi));
+    if (lo != 0.f) atomicAdd(slot, widen(lo));
+}
+__device__ __forceinline__ void add_cut(double *slot, float v) { atomicAdd(slot, widen(v)); }
+__device__ __forceinline__ void add_cut(double *slot, double v) { atomicAdd(slot, v); }
+
 // Slot of a nonempty row [rs, re) that crosses a chunk boundary: the first
 // boundary after rs (boundary b >= 1 sits at nb + b ch; slot b - 1); -1 when
 // the row lies within one chunk.
@@ -450,10 +472,10 @@ struct FfmaEngine {
                 const int e = tri_idx(r, c);
                 if constexpr (SH::COMP) {
                     if (whole) lrow[e] = hi[i][j] + lo[i][j];
-                    else atomicAdd(crow + e, (double)hi[i][j] + (double)lo[i][j]);
+                    else add_cut(crow + e, hi[i][j], lo[i][j]);
                 } else {
                     if (whole) lrow[e] = acc[i][j];
-                    else atomicAdd(crow + e, (double)acc[i][j]);
+                    else add_cut(crow + e, acc[i][j]);
                 }
             }
     }
@@ -545,10 +567,10 @@ struct MmaEngine {
                 const int e = tri_idx(r, c);
                 if constexpr (COMP) {
                     if (whole) lrow[e] = hi[u][q] + lo[u][q];
-                    else atomicAdd(crow + e, (double)hi[u][q] + (double)lo[u][q]);
+                    else add_cut(crow + e, hi[u][q], lo[u][q]);
                 } else {
                     if (whole) lrow[e] = d[u][q];
-                    else atomicAdd(crow + e, (double)d[u][q]);
+                    else add_cut(crow + e, d[u][q]);
                 }
             }
     }
@@ -861,10 +883,10 @@ __global__ void __launch_bounds__(128) gram_warp_kernel(const SolveParams<T> P, 
                         two_sum(hi[x][y], acc[x][y], s, er);
                         const float l2 = lo[x][y] + er;
                         if (whole) lrow[e] = s + l2;
-                        else atomicAdd(crow + e, (double)s + (double)l2);
+                        else add_cut(crow + e, s, l2);
                     } else {
                         if (whole) lrow[e] = acc[x][y];
-                        else atomicAdd(crow + e, (double)acc[x][y]);
+                        else add_cut(crow + e, acc[x][y]);
                     }
                 }
             if (re >= ce) break;
@@ -1012,10 +1034,10 @@ __global__ void __launch_bounds__(128) gram_warp_mma_kernel(const SolveParams<fl
                         two_sum(hi[u][q], d[u][q], sm, er);
                         const float l2 = lo[u][q] + er;
                         if (whole) lrow[e] = sm + l2;
-                        else atomicAdd(crow + e, (double)sm + (double)l2);
+                        else add_cut(crow + e, sm, l2);
                     } else {
                         if (whole) lrow[e] = d[u][q];
-                        else atomicAdd(crow + e, (double)d[u][q]);
+                        else add_cut(crow + e, d[u][q]);
                     }
                 }
             if (re >= ce) break;

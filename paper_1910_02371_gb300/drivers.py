@@ -3,6 +3,8 @@
 * ``als_sweep`` -- alternating least squares (Sec. 2.2): for each mode, the
   right-hand sides are the MTTKRP of the observed tensor, then Solve Factor
   with the pattern and lambda overwrites that factor (block Gauss-Seidel order).
+* ``newton_als_sweep`` -- ALS for a general loss (Sec. 2.2): Newton steps on
+  each factor in turn with weights phi'' in Solve Factor.
 * ``GaussNewton`` -- the generalized Gauss-Newton method with implicit
   preconditioned CG (Sec. 2.5), one ``tc_ggn_step`` per call.
 Every arithmetic step runs in libtc kernels; this module only orders calls.
@@ -23,6 +25,14 @@ def als_sweep(p: "tc.Pattern", factors, lam: float, rhs=None, row_status=None, p
                         row_status=None if row_status is None else row_status[d], prec=prec,
                         stream=stream)
     return factors
+
+
+def newton_als_sweep(p: "tc.Pattern", factors, loss: str, lam: float, inner_iters: int = 5,
+                     tol: float = 1e-3, prec: str = "fp32", stream=None):
+    """One general-loss ALS sweep in place (Sec. 2.2): Newton steps on each
+    factor in turn (tc_newton_als_mode).  Returns the steps taken per mode."""
+    return [tc.newton_als_mode(p, factors, d, loss, lam, inner_iters, tol, prec, stream)
+            for d in range(len(factors))]
 
 
 class GaussNewton:

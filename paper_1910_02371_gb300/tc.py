@@ -60,6 +60,7 @@ _SIGS = {
     "tc_set_solve_tuning": [_I, _I, _P],
     "tc_get_solve_tuning": [_I, _I, _P],
     "tc_autotune_solve": [_P, _I, _P, _I, _P, _I, _P, _D, _I, _P, _P, _P, _P],
+    "tc_newton_als_mode": [_P, _I, _I, _P, _I, _D, _I, _D, _I, _P, _P],
 }
 for _name, _args in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -366,3 +367,15 @@ def autotune_solve(p: Pattern, factors, mode: int, rhs: torch.Tensor, lam: float
                                   float(lam), PRECS[prec], _ptr(out), ctypes.byref(best),
                                   ctypes.byref(ms), _stream(stream)), "tc_autotune_solve")
     return (int(best.chunk_nnz), int(best.batch_bytes), int(best.chol_rows_per_warp)), float(ms.value)
+
+
+def newton_als_mode(p: Pattern, factors, mode: int, loss: str, lam: float, inner_iters: int = 5,
+                    tol: float = 1e-3, prec: str = "fp32", stream=None) -> int:
+    """tc_newton_als_mode: Newton steps on factors[mode] in place; returns the
+    number of steps taken."""
+    R = factors[0].shape[1]
+    steps = ctypes.c_int()
+    _check(_lib.tc_newton_als_mode(p.handle, LOSSES[loss], R, _ptrs(factors), int(mode), float(lam),
+                                   int(inner_iters), float(tol), PRECS[prec], ctypes.byref(steps),
+                                   _stream(stream)), "tc_newton_als_mode")
+    return int(steps.value)
