@@ -290,6 +290,26 @@ def objective(dims, idx, t, factors, loss, lam):
     return loss_grad(dims, idx, t, factors, loss, lam, want_grad=False)[0]
 
 
+def newton_matvec(dims, idx, t, factors, loss, lam, x):
+    """Full Newton Hessian-vector product (Sec. 2.5 before the Gauss-Newton
+    approximation; Appendix A): the Gauss-Newton product plus the phi' term.
+    The second derivative of m_e with respect to rows of two different modes p,
+    q is delta_rs prod_{n != p, q} a^(n) (zero within one mode), so the block of
+    output mode d is, for each other mode p, MTTKRP(phi', d) of the factors with
+    A^(p) replaced by x^(p)."""
+    y = ggn_matvec(dims, idx, t, factors, loss, lam, x)
+    d1, _ = loss_derivs(dims, idx, t, factors, loss)
+    N = len(dims)
+    for d in range(N):
+        for q in range(N):
+            if q == d:
+                continue
+            F = [_f64(a) for a in factors]
+            F[q] = _f64(x[q])
+            y[d] = y[d] + mttkrp(dims, idx, d1, F, d)
+    return y
+
+
 def loss_derivs(dims, idx, t, factors, loss):
     """phi' and phi'' at every observed entry (input order), at the model
     entries of `factors` (Table 1 notation, Sec. 2.1 / 5.7 losses)."""

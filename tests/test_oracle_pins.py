@@ -437,3 +437,40 @@ def test_newton_als_poisson_descends():
         f_new = oracle.objective(dims, idx, t, A, "poisson_log", lam)
         assert f_new <= f * (1 + 1e-12)
         f = f_new
+
+
+# ------------------------------------------------------------ full Newton product (Sec. 2.5)
+@pytest.mark.parametrize("loss", ["ls", "poisson_log"])
+def test_newton_matvec_is_gradient_difference(loss, rng):
+    """The full Hessian-vector product equals the central difference of the
+    gradient (pinned above) along x, away from an exact fit (phi' != 0)."""
+    dims = (9, 8, 7)
+    R = 3
+    idx, planted, _ = small_problem(dims, 250, R, seed=31, factor="uniform01", recipe="poisson")
+    t = synth.observe(oracle.model_entries(dims, idx, planted), "poisson", 31)
+    A = [0.9 * a for a in synth.perturb(planted, 31)]
+    x = [rng.standard_normal((I, R)) for I in dims]
+    lam = 0.05
+    eps = 1e-5
+    _, gp = oracle.loss_grad(dims, idx, t, [a + eps * v for a, v in zip(A, x)], loss, lam)
+    _, gm = oracle.loss_grad(dims, idx, t, [a - eps * v for a, v in zip(A, x)], loss, lam)
+    y = oracle.newton_matvec(dims, idx, t, A, loss, lam, x)
+    for d in range(3):
+        fd = (gp[d] - gm[d]) / (2 * eps)
+        assert np.linalg.norm(y[d] - fd) <= 1e-7 * np.linalg.norm(fd)
+    # and it differs from the Gauss-Newton product (the phi' term is present)
+    g = oracle.ggn_matvec(dims, idx, t, A, loss, lam, x)
+    assert sum(np.linalg.norm(a - b) for a, b in zip(y, g)) > 1e-3 * sum(np.linalg.norm(b) for b in g)
+
+
+def test_newton_matvec_symmetric(rng):
+    dims = (8, 7, 6)
+    idx, planted, t = small_problem(dims, 200, 3, seed=33, noise=0.3)
+    A = synth.init_factors(dims, 3, seed=33)
+    x = [rng.standard_normal((I, 3)) for I in dims]
+    z = [rng.standard_normal((I, 3)) for I in dims]
+    hx = oracle.newton_matvec(dims, idx, t, A, "ls", 0.1, x)
+    hz = oracle.newton_matvec(dims, idx, t, A, "ls", 0.1, z)
+    a = sum(np.vdot(u, v) for u, v in zip(z, hx))
+    b = sum(np.vdot(u, v) for u, v in zip(hz, x))
+    assert abs(a - b) <= 1e-11 * abs(a)
