@@ -50,7 +50,7 @@ METRIC = ("observed entries/s through one full step (pattern rebuild + TTTP + AL
 # to 1e7: three launches per product.
 NCU_TRAFFIC = {
     "ggn_matvec": {"bytes": 3 * 36.644e6 * 2.5, "file": "paper_1910_02371_gb300/csrc/sweep.cu",
-                   "src": "11efe21da58ccd68"},
+                   "src": "a83d9f1a4be9febe"},
 }
 
 

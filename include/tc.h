@@ -269,6 +269,17 @@ tc_status tc_newton_als_mode(const tc_pattern *p, tc_loss loss, int R, void *con
                              int mode, double lambda, int inner_iters, double tol, tc_prec prec,
                              int *steps_out, tc_stream_t stream);
 
+/* Full Newton Hessian-vector product (Sec. 2.5 before the Gauss-Newton
+ * approximation; Appendix A): the product of tc_ggn_matvec plus the phi'
+ * term sum_e phi'_e (d^2 m_e) x, whose block for output mode d is, for each
+ * other mode q, the pattern-restricted MTTKRP of phi' with x^(q) in place of
+ * A^(q) (the second derivative of m_e within one mode is zero).  The matrix
+ * is symmetric but may be indefinite.  Same arguments and layout as
+ * tc_ggn_matvec. */
+tc_status tc_newton_matvec(const tc_pattern *p, tc_loss loss, int R, const void *const *factors,
+                           const void *const *x, double lambda, void *const *y,
+                           tc_stream_t stream);
+
 /* ------------------------------------------------------------------ GGN / PCG */
 
 /* A preconditioned-CG solver for the Gauss-Newton system H dx = b at fixed
@@ -286,6 +297,16 @@ typedef struct tc_cg tc_cg;
 tc_status tc_cg_create(const tc_pattern *p, tc_loss loss, int R, const void *const *factors,
                        double lambda, int precondition, tc_cg **out);
 tc_status tc_cg_destroy(tc_cg *cg);
+
+/* Selects the matrix the solver iterates with: 0 = the Gauss-Newton matrix
+ * (the default), 1 = the full Hessian (tc_newton_matvec; Sec. 2.5, "Newton's
+ * method").  The block-diagonal preconditioner is the same for both: the
+ * full Hessian's phi' term has no block within a row.  The full Hessian may be
+ * indefinite; PCG then stops at the first direction with p^T H p <= 0 and
+ * reports TC_ERR_BREAKDOWN (the indefiniteness check).  Changing the choice
+ * discards the captured graph (the next tc_cg_solve captures again); it
+ * synchronizes the device. */
+tc_status tc_cg_set_hessian(tc_cg *cg, int full_newton);
 
 /* Builds (or rebuilds) the preconditioner at the current factor values. */
 tc_status tc_cg_setup(tc_cg *cg, tc_stream_t stream);

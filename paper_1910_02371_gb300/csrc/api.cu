@@ -182,8 +182,9 @@ tc_status tc_loss_grad(const tc_pattern *p, tc_loss loss, int R, const void *con
     return rc != TC_OK ? rc : launch_status();
 }
 
-tc_status tc_ggn_matvec(const tc_pattern *p, tc_loss loss, int R, const void *const *factors,
-                        const void *const *x, double lambda, void *const *y, tc_stream_t stream) {
+static tc_status hessian_matvec(const tc_pattern *p, tc_loss loss, int R,
+                                const void *const *factors, const void *const *x, double lambda,
+                                void *const *y, int full_newton, tc_stream_t stream) {
     if (!p || !rank_ok(R) || !factors_ok(factors, -1) || !factors_ok(x, -1) || !y)
         return TC_ERR_ARG;
     if (loss < TC_LOSS_LS || loss > TC_LOSS_POISSON_ID) return TC_ERR_ARG;
@@ -193,9 +194,20 @@ tc_status tc_ggn_matvec(const tc_pattern *p, tc_loss loss, int R, const void *co
         for (int m = 0; m < TC_ORDER; ++m)
             if (y[n] == x[m]) return TC_ERR_ARG;
     }
-    tc_status rc = launch_ggn_matvec(p, loss, R, factors, x, lambda, y, nullptr, 1,
+    tc_status rc = launch_ggn_matvec(p, loss, R, factors, x, lambda, y, nullptr, 1, full_newton,
                                      (cudaStream_t)stream);
     return rc != TC_OK ? rc : launch_status();
+}
+
+tc_status tc_ggn_matvec(const tc_pattern *p, tc_loss loss, int R, const void *const *factors,
+                        const void *const *x, double lambda, void *const *y, tc_stream_t stream) {
+    return hessian_matvec(p, loss, R, factors, x, lambda, y, 0, stream);
+}
+
+tc_status tc_newton_matvec(const tc_pattern *p, tc_loss loss, int R, const void *const *factors,
+                           const void *const *x, double lambda, void *const *y,
+                           tc_stream_t stream) {
+    return hessian_matvec(p, loss, R, factors, x, lambda, y, 1, stream);
 }
 
 }  // extern "C"

@@ -183,6 +183,7 @@ struct tc_cg {
     void *A[TC_ORDER] = {nullptr, nullptr, nullptr};
     double lambda = 0.0;
     int precond = 1;
+    int full_newton = 0;          // iterate with the full Hessian instead of Gauss-Newton
     void *pinv[TC_ORDER] = {nullptr, nullptr, nullptr};
     void *r[TC_ORDER] = {}, *z[TC_ORDER] = {}, *pv[TC_ORDER] = {}, *Ap[TC_ORDER] = {};
     void *grad[TC_ORDER] = {}, *dx[TC_ORDER] = {};
@@ -299,10 +300,10 @@ static tc_status enqueue_solve(tc_cg *cg, const void *const *b, void *const *dx,
     for (int it = 0; it < iters; ++it) {
         tc_status rc =
             cg->axv ? launch_ggn_matvec_ax(p, cg->loss, cg->R, (const void *const *)cg->ax, cg->lambda,
-                                           cg->Ap, cg->scal + S_PAP, 0, st)
+                                           cg->Ap, cg->scal + S_PAP, 0, cg->full_newton, st)
                     : launch_ggn_matvec(p, cg->loss, cg->R, (const void *const *)cg->A,
                                         (const void *const *)cg->pv, cg->lambda, cg->Ap,
-                                        cg->scal + S_PAP, 0, st);
+                                        cg->scal + S_PAP, 0, cg->full_newton, st);
         if (rc != TC_OK) return rc;
         launch_update<T>(1, cg->R, M, cg->scal, S_RZNEW, p->status, st);
         cg_scalar_kernel<<<1, 32, 0, st>>>(cg->scal, rz_out, it + 1, 0);
@@ -386,6 +387,19 @@ tc_status tc_cg_destroy(tc_cg *cg) {
     if (!cg) return TC_ERR_ARG;
     cudaDeviceSynchronize();
     free_cg(cg);
+    return TC_OK;
+}
+
+tc_status tc_cg_set_hessian(tc_cg *cg, int full_newton) {
+    if (!cg || (full_newton != 0 && full_newton != 1)) return TC_ERR_ARG;
+    if (cg->full_newton != full_newton) {
+        cudaDeviceSynchronize();
+        if (cg->exec) {                 // the captured iterations change: capture again
+            cudaGraphExecDestroy(cg->exec);
+            cg->exec = nullptr;
+        }
+        cg->full_newton = full_newton;
+    }
     return TC_OK;
 }
 
@@ -494,10 +508,10 @@ tc_status tc_cg_matvec(tc_cg *cg, const void *const *x, void *const *y, tc_strea
             enqueue_ax_fill<float>(cg, x, 1, st);
         }
         rc = launch_ggn_matvec_ax(cg->p, cg->loss, cg->R, (const void *const *)cg->ax, cg->lambda, y,
-                                  nullptr, 1, st);
+                                  nullptr, 1, cg->full_newton, st);
     } else {
         rc = launch_ggn_matvec(cg->p, cg->loss, cg->R, (const void *const *)cg->A, x, cg->lambda, y,
-                               nullptr, 1, st);
+                               nullptr, 1, cg->full_newton, st);
     }
     if (rc != TC_OK) return rc;
     return cudaGetLastError() == cudaSuccess ? TC_OK : TC_ERR_CUDA;

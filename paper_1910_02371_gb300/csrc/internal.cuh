@@ -107,16 +107,16 @@ tc_status launch_mttkrp(const tc_pattern *p, tc_weights w, const void *s, int R,
 tc_status launch_loss_grad(const tc_pattern *p, tc_loss loss, int R, const void *const *A,
                            double lambda, double *loss_out, void *const *grads, cudaStream_t st);
 // init: first set y = 2 lambda x (and add its share to *dot_out); otherwise y
-// already holds it.
+// already holds it.  full_newton: also the phi' term of the full Hessian.
 tc_status launch_ggn_matvec(const tc_pattern *p, tc_loss loss, int R, const void *const *A,
                             const void *const *x, double lambda, void *const *y,
-                            double *dot_out, int init, cudaStream_t st);
+                            double *dot_out, int init, int full_newton, cudaStream_t st);
 // The same on interleaved factor / direction buffers AX[n] (I_n x 2R: per lane
 // chunk of 16 bytes, the factor chunk then the direction chunk); needs the
 // vector path (vec_ok).
 tc_status launch_ggn_matvec_ax(const tc_pattern *p, tc_loss loss, int R, const void *const *AX,
                                double lambda, void *const *y, double *dot_out, int init,
-                               cudaStream_t st);
+                               int full_newton, cudaStream_t st);
 // Gram + FP64 Cholesky per row.  If pinv_out != null the inverse of each row
 // system, (G_i + lambda I)^-1, is formed in FP64 from the factor and stored
 // (pattern dtype, I_d x R x R) instead of solving.

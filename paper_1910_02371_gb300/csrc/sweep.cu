@@ -15,7 +15,9 @@
 
 namespace tc {
 
-enum { OP_MTTKRP = 0, OP_GRAD = 1, OP_GGN = 2 };
+// OP_NEWTON: the Gauss-Newton product plus the phi' term of the full Hessian
+// (a separate instantiation, so the Gauss-Newton kernel is untouched by it).
+enum { OP_MTTKRP = 0, OP_GRAD = 1, OP_GGN = 2, OP_NEWTON = 3 };
 
 template <typename T>
 struct SweepParams {
@@ -98,7 +100,7 @@ __device__ __forceinline__ void contribution(const SweepParams<T> &P, const Step
     const int R = VEC ? RT : P.R;
     T b[V], e[V];
     T xb[V], xc[V];
-    if constexpr (OP == OP_GGN) {
+    if constexpr (OP == OP_GGN || OP == OP_NEWTON) {
         load_pair<T, V, VEC, AXL>(b, xb, P.A1, P.X1, in.j, R, lg);
         load_pair<T, V, VEC, AXL>(e, xc, P.A2, P.X2, in.k, R, lg);
     } else {
@@ -127,15 +129,22 @@ __device__ __forceinline__ void contribution(const SweepParams<T> &P, const Step
             part += a[t] * be;
         }
         const T z = group_sum<G>(zp);
-        T d2 = T(2);
-        if (P.loss != TC_LOSS_LS) {   // (part is unused for least squares)
+        T d2 = T(2), d1 = T(0);
+        if (OP == OP_NEWTON || P.loss != TC_LOSS_LS) {   // (m is unused for the LS Gauss-Newton product)
             const T m = group_sum<G>(part);
-            T phi, d1;
+            T phi;
             loss_terms(P.loss, in.t, m, phi, d1, d2, dom_ok);
         }
         const T wz = d2 * z;
+        if constexpr (OP == OP_NEWTON) {
+            // phi' times the second derivatives of m_e: for this output mode
+            // and each other mode q, the product with x^(q) in place of a^(q)
 #pragma unroll
-        for (int t = 0; t < V; ++t) c[t] = wz * b[t] * e[t];
+            for (int t = 0; t < V; ++t) c[t] = wz * b[t] * e[t] + d1 * (xb[t] * e[t] + b[t] * xc[t]);
+        } else {
+#pragma unroll
+            for (int t = 0; t < V; ++t) c[t] = wz * b[t] * e[t];
+        }
     }
     if (!valid) {
 #pragma unroll
@@ -211,7 +220,8 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepParams<T> P) {
     };
     auto load_own = [&](int cr) {
         const int64_t row = __ldg(P.nz_rows + cr);
-        if constexpr (OP == OP_GGN) load_pair<T, V, VEC, AXL>(a, xa, P.Ad, P.Xd, row, R, lg);
+        if constexpr (OP == OP_GGN || OP == OP_NEWTON)
+            load_pair<T, V, VEC, AXL>(a, xa, P.Ad, P.Xd, row, R, lg);
         else load_slice<T, V, VEC>(a, P.Ad, row, R, lg);
     };
     // A step whose row boundaries fall inside it (off: first offset; last: its
@@ -658,7 +668,7 @@ tc_status launch_loss_grad(const tc_pattern *p, tc_loss loss, int R, const void 
 template <typename T>
 static tc_status ggn_t(const tc_pattern *p, tc_loss loss, int R, const void *const *A,
                        const void *const *x, double lambda, void *const *y, double *dot_out,
-                       int init, cudaStream_t st) {
+                       int init, int full_newton, cudaStream_t st) {
     const int tier = rank_tier(R);
     const bool vec = vec_ok(R, tier, sizeof(T)) && aligned16({A[0], A[1], A[2]}) &&
                      aligned16({x[0], x[1], x[2]}) && aligned16({y[0], y[1], y[2]});
@@ -681,7 +691,8 @@ static tc_status ggn_t(const tc_pattern *p, tc_loss loss, int R, const void *con
         P.accumulate = 1;
         P.dot_acc = dot_out;
         P.dot_with = (const T *)x[d];
-        launch_sweep_t<T, OP_GGN>(P, tier, vec, st);
+        if (full_newton) launch_sweep_t<T, OP_NEWTON>(P, tier, vec, st);
+        else launch_sweep_t<T, OP_GGN>(P, tier, vec, st);
     }
     return TC_OK;
 }
@@ -707,7 +718,7 @@ __global__ void scale_ax_kernel(T *__restrict__ y, const T *__restrict__ ax, T a
 // driver's layout; see load_pair).  Requires the vector path (R fills its tier).
 template <typename T>
 static tc_status ggn_ax_t(const tc_pattern *p, tc_loss loss, int R, const void *const *AX,
-                          double lambda, void *const *y, double *dot_out, int init,
+                          double lambda, void *const *y, double *dot_out, int init, int full_newton,
                           cudaStream_t st) {
     const int tier = rank_tier(R);
     constexpr int V = 16 / (int)sizeof(T);
@@ -743,11 +754,20 @@ static tc_status ggn_ax_t(const tc_pattern *p, tc_loss loss, int R, const void *
             kern<<<(unsigned)nb, threads, 0, st>>>(Q);
             count_launch();
         };
-        switch (tier) {
-            case 8: go(sweep_kernel<T, 8, true, OP_GGN, true>, Lay<T, 8, 16>::NG); break;
-            case 16: go(sweep_kernel<T, 16, true, OP_GGN, true>, Lay<T, 16, 16>::NG); break;
-            case 32: go(sweep_kernel<T, 32, true, OP_GGN, true>, Lay<T, 32, 16>::NG); break;
-            default: go(sweep_kernel<T, 64, true, OP_GGN, true>, Lay<T, 64, 16>::NG); break;
+        if (full_newton) {
+            switch (tier) {
+                case 8: go(sweep_kernel<T, 8, true, OP_NEWTON, true>, Lay<T, 8, 16>::NG); break;
+                case 16: go(sweep_kernel<T, 16, true, OP_NEWTON, true>, Lay<T, 16, 16>::NG); break;
+                case 32: go(sweep_kernel<T, 32, true, OP_NEWTON, true>, Lay<T, 32, 16>::NG); break;
+                default: go(sweep_kernel<T, 64, true, OP_NEWTON, true>, Lay<T, 64, 16>::NG); break;
+            }
+        } else {
+            switch (tier) {
+                case 8: go(sweep_kernel<T, 8, true, OP_GGN, true>, Lay<T, 8, 16>::NG); break;
+                case 16: go(sweep_kernel<T, 16, true, OP_GGN, true>, Lay<T, 16, 16>::NG); break;
+                case 32: go(sweep_kernel<T, 32, true, OP_GGN, true>, Lay<T, 32, 16>::NG); break;
+                default: go(sweep_kernel<T, 64, true, OP_GGN, true>, Lay<T, 64, 16>::NG); break;
+            }
         }
     }
     return TC_OK;
@@ -755,16 +775,18 @@ static tc_status ggn_ax_t(const tc_pattern *p, tc_loss loss, int R, const void *
 
 tc_status launch_ggn_matvec_ax(const tc_pattern *p, tc_loss loss, int R, const void *const *AX,
                                double lambda, void *const *y, double *dot_out, int init,
-                               cudaStream_t st) {
-    return p->dtype == TC_F64 ? ggn_ax_t<double>(p, loss, R, AX, lambda, y, dot_out, init, st)
-                              : ggn_ax_t<float>(p, loss, R, AX, lambda, y, dot_out, init, st);
+                               int full_newton, cudaStream_t st) {
+    return p->dtype == TC_F64
+               ? ggn_ax_t<double>(p, loss, R, AX, lambda, y, dot_out, init, full_newton, st)
+               : ggn_ax_t<float>(p, loss, R, AX, lambda, y, dot_out, init, full_newton, st);
 }
 
 tc_status launch_ggn_matvec(const tc_pattern *p, tc_loss loss, int R, const void *const *A,
                             const void *const *x, double lambda, void *const *y,
-                            double *dot_out, int init, cudaStream_t st) {
-    return p->dtype == TC_F64 ? ggn_t<double>(p, loss, R, A, x, lambda, y, dot_out, init, st)
-                              : ggn_t<float>(p, loss, R, A, x, lambda, y, dot_out, init, st);
+                            double *dot_out, int init, int full_newton, cudaStream_t st) {
+    return p->dtype == TC_F64
+               ? ggn_t<double>(p, loss, R, A, x, lambda, y, dot_out, init, full_newton, st)
+               : ggn_t<float>(p, loss, R, A, x, lambda, y, dot_out, init, full_newton, st);
 }
 
 }  // namespace tc

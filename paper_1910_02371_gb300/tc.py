@@ -61,6 +61,8 @@ _SIGS = {
     "tc_get_solve_tuning": [_I, _I, _P],
     "tc_autotune_solve": [_P, _I, _P, _I, _P, _I, _P, _D, _I, _P, _P, _P, _P],
     "tc_newton_als_mode": [_P, _I, _I, _P, _I, _D, _I, _D, _I, _P, _P],
+    "tc_newton_matvec": [_P, _I, _I, _P, _P, _D, _P, _P],
+    "tc_cg_set_hessian": [_P, _I],
 }
 for _name, _args in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -256,6 +258,16 @@ def loss_grad(p: Pattern, factors, loss: str, lam: float, want_loss=True, want_g
     return loss_t, (grads if want_grad else None)
 
 
+def newton_matvec(p: Pattern, factors, x, loss: str, lam: float, y=None, stream=None):
+    """tc_newton_matvec: y = (full Hessian) x, the Gauss-Newton product plus the phi' term."""
+    R = factors[0].shape[1]
+    if y is None:
+        y = [torch.empty_like(v) for v in x]
+    _check(_lib.tc_newton_matvec(p.handle, LOSSES[loss], R, _ptrs(factors), _ptrs(x), float(lam),
+                                 _ptrs(y), _stream(stream)), "tc_newton_matvec")
+    return y
+
+
 def ggn_matvec(p: Pattern, factors, x, loss: str, lam: float, y=None, stream=None):
     """tc_ggn_matvec: y = (J^T diag(phi'') J + 2 lam I) x."""
     R = factors[0].shape[1]
@@ -284,6 +296,11 @@ class CG:
         if h is not None and h.value:
             _lib.tc_cg_destroy(h)
             self.handle = None
+
+    def set_hessian(self, full_newton: bool):
+        """tc_cg_set_hessian: iterate with the full Hessian (True) or the
+        Gauss-Newton matrix (False, the default)."""
+        _check(_lib.tc_cg_set_hessian(self.handle, 1 if full_newton else 0), "tc_cg_set_hessian")
 
     def setup(self, stream=None):
         _check(_lib.tc_cg_setup(self.handle, _stream(stream)), "tc_cg_setup")
