@@ -18,6 +18,10 @@ routines the way the paper composes its kernels:
   MTTKRP(phi') + 2 lambda A, the row Hessians sum phi'' h h^T + 2 lambda I
   solved through Solve Factor with weights phi'' -- until the step is small
   relative to the factor or an iteration cap is reached.
+* Coordinate minimization, CCD++ order (Sec. 2.3): for each rank component r,
+  the residual rho^(r) = t - m + u_r v_r w_r, then column r of each factor in
+  turn set to MTTKRP(rho^(r)) / (lambda + sum of squared products), the
+  residual updated in between.
 * Gauss-Newton step (Sec. 2.5): gradient, block-diagonal preconditioner (the
   diagonal blocks of the Gauss-Newton matrix, applied through Solve Factor with
   weights phi'' and regularization 2 lambda), preconditioned CG from zero for a
@@ -344,4 +348,26 @@ def newton_als_sweep(dims, idx, t, factors, loss, lam, inner_iters=5, tol=1e-3):
     A = [_f64(a).copy() for a in factors]
     for d in range(len(dims)):
         A, _ = newton_als_mode(dims, idx, t, A, d, loss, lam, inner_iters, tol)
+    return A
+
+
+def ccd_sweep(dims, idx, t, factors, lam):
+    """One CCD++ sweep for least squares (Sec. 2.3): for r = 0 .. R-1, add the
+    rank-r term back into the residual, update column r of each factor in turn
+    (u_ir = sum_e v_jr w_kr rho_e / (lambda + sum_e v_jr^2 w_kr^2), the other
+    columns fixed, the previously updated ones used at once), then subtract the
+    updated rank-r term."""
+    A = [_f64(a).copy() for a in factors]
+    N = len(dims)
+    R = A[0].shape[1]
+    rho = _f64(t) - model_entries(dims, idx, A)
+    for r in range(R):
+        col = lambda n: A[n][:, r:r + 1].copy()
+        rho = rho + tttp(dims, idx, None, [col(n) for n in range(N)])
+        for d in range(N):
+            cols = [col(n) for n in range(N)]
+            num = mttkrp(dims, idx, rho, cols, d)[:, 0]
+            den = lam + mttkrp(dims, idx, None, [c * c for c in cols], d)[:, 0]
+            A[d][:, r] = num / den
+        rho = rho - tttp(dims, idx, None, [col(n) for n in range(N)])
     return A

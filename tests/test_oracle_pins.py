@@ -474,3 +474,46 @@ def test_newton_matvec_symmetric(rng):
     a = sum(np.vdot(u, v) for u, v in zip(z, hx))
     b = sum(np.vdot(u, v) for u, v in zip(hz, x))
     assert abs(a - b) <= 1e-11 * abs(a)
+
+
+# ------------------------------------------------------------ coordinate minimization (Sec. 2.3)
+def test_ccd_rank1_is_als_rank1():
+    """Sec. 2.3: for least squares a coordinate step is a rank-1 ALS step, so
+    with R = 1 a CCD++ sweep equals an ALS sweep."""
+    dims = (14, 12, 10)
+    idx, _, t = small_problem(dims, 600, 2, seed=41, noise=0.2)
+    A = synth.init_factors(dims, 1, seed=41)
+    c = oracle.ccd_sweep(dims, idx, t, A, 0.3)
+    a = oracle.als_sweep(dims, idx, t, A, 0.3)
+    for d in range(3):
+        np.testing.assert_allclose(c[d], a[d], rtol=1e-11, atol=1e-13)
+
+
+def test_ccd_each_coordinate_is_minimized(rng):
+    """Each column update is the exact minimizer of the LS objective along that
+    column, row by row: the partial derivatives of f (Table 1 gradient, pinned
+    by differences above) in column r of the factor just updated vanish."""
+    dims = (9, 8, 7)
+    idx, _, t = small_problem(dims, 300, 3, seed=43, noise=0.3)
+    A = synth.init_factors(dims, 3, seed=43)
+    lam = 0.2
+    out = oracle.ccd_sweep(dims, idx, t, A, lam)
+    # the last update of the sweep is column R-1 of the last factor: its partial
+    # derivatives are zero at the returned point (f uses lambda on ||A||^2 with the
+    # factor-2 convention of Table 1: grad = 2 sum h (m - t) + 2 lambda a)
+    _, g = oracle.loss_grad(dims, idx, t, out, "ls", lam)
+    G = np.abs(g[2][:, -1]).max()
+    assert G <= 1e-10 * np.abs(g[0]).max()
+
+
+def test_ccd_monotone():
+    dims = (20, 18, 16)
+    idx, _, t = small_problem(dims, 1200, 4, seed=45, noise=0.5)
+    A = synth.init_factors(dims, 4, seed=45)
+    lam = 0.05
+    f = oracle.objective(dims, idx, t, A, "ls", lam)
+    for _ in range(4):
+        A = oracle.ccd_sweep(dims, idx, t, A, lam)
+        f_new = oracle.objective(dims, idx, t, A, "ls", lam)
+        assert f_new <= f * (1 + 1e-12)
+        f = f_new
