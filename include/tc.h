@@ -280,6 +280,17 @@ tc_status tc_newton_matvec(const tc_pattern *p, tc_loss loss, int R, const void 
                            const void *const *x, double lambda, void *const *y,
                            tc_stream_t stream);
 
+/* Coordinate minimization for least squares in CCD++ order (Sec. 2.3): one
+ * sweep over r = 0 .. R-1; for each r the residual takes the rank-r term back
+ * (rho = t - <u, v, w> + u_r v_r w_r), column r of each factor in turn is set
+ * to sum_e v_jr w_kr rho_e / (lambda + sum_e v_jr^2 w_kr^2) (updated columns
+ * used at once), and the new rank-r term leaves the residual.  Factors are
+ * updated in place; the residual is formed from the pattern's values at the
+ * start of the sweep.  Made of rank-1 TTTP, MTTKRP and Solve Factor launches
+ * (2R passes over the nonzeros plus 3R rank-1 Solve Factors). */
+tc_status tc_ccd_sweep(const tc_pattern *p, int R, void *const *factors, double lambda,
+                       tc_stream_t stream);
+
 /* ------------------------------------------------------------------ GGN / PCG */
 
 /* A preconditioned-CG solver for the Gauss-Newton system H dx = b at fixed

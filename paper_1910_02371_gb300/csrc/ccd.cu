@@ -1,0 +1,120 @@
+// Coordinate minimization for least squares in CCD++ order (Sec. 2.3): for
+// each rank component r the residual gets the rank-r term back,
+//   rho = t - <u, v, w> + u_r v_r w_r,
+// then column r of each factor is set in turn to
+//   u_ir = sum_e v_jr w_kr rho_e / (lambda + sum_e v_jr^2 w_kr^2),
+// and the updated rank-r term is taken out of the residual again.  At rank 1
+// the numerator is a rank-1 MTTKRP of rho and the division is exactly a rank-1
+// Solve Factor, so a column update is two library kernels; the rank-1 TTTPs
+// move rho.  Columns are gathered from / scattered into the row-major factors
+// by two small kernels.
+#include "internal.cuh"
+
+namespace tc {
+
+template <typename T>
+__global__ void col_get_kernel(const T *__restrict__ A, int64_t I, int R, int r, T *__restrict__ c) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < I;
+         i += (int64_t)gridDim.x * blockDim.x)
+        c[i] = A[i * R + r];
+}
+
+template <typename T>
+__global__ void col_put_kernel(T *__restrict__ A, int64_t I, int R, int r, const T *__restrict__ c) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < I;
+         i += (int64_t)gridDim.x * blockDim.x)
+        A[i * R + r] = c[i];
+}
+
+// y += alpha x  (alpha = +1 / -1: the residual moves)
+template <typename T>
+__global__ void resid_axpy_kernel(int64_t n, T alpha, const T *__restrict__ x, T *__restrict__ y) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x)
+        y[e] += alpha * x[e];
+}
+
+// rho = t - m
+template <typename T>
+__global__ void resid_init_kernel(int64_t n, const T *__restrict__ t, const T *__restrict__ m,
+                                  T *__restrict__ rho) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x)
+        rho[e] = t[e] - m[e];
+}
+
+static unsigned grid_for(int64_t n) {
+    int64_t b = (n + 255) / 256;
+    if (b > 4096) b = 4096;
+    return (unsigned)(b < 1 ? 1 : b);
+}
+
+template <typename T>
+static tc_status ccd_t(const tc_pattern *p, int R, void *const *factors, double lambda,
+                       cudaStream_t st) {
+    const int64_t m = p->nnz;
+    const int64_t I0 = p->dims[0], I1 = p->dims[1], I2 = p->dims[2];
+    const int64_t Imax = I0 > I1 ? (I0 > I2 ? I0 : I2) : (I1 > I2 ? I1 : I2);
+    const int64_t mm = m > 0 ? m : 1;
+    T *buf = nullptr;
+    TC_CUDA(cudaMallocAsync((void **)&buf, sizeof(T) * (size_t)(2 * mm + I0 + I1 + I2 + Imax), st));
+    T *rho = buf, *x = rho + mm, *c0 = x + mm, *c1 = c0 + I0, *c2 = c1 + I1, *num = c2 + I2;
+    T *col[TC_ORDER] = {c0, c1, c2};
+    const void *cols[TC_ORDER] = {c0, c1, c2};
+    const int64_t I[TC_ORDER] = {I0, I1, I2};
+    const T *t = (const T *)p->md[0].vals;
+    tc_status rc = TC_OK;
+    if (m > 0) {
+        rc = launch_tttp(p, TC_W_ONE, nullptr, R, (const void *const *)factors, x, st);
+        if (rc == TC_OK) {
+            resid_init_kernel<T><<<grid_for(m), 256, 0, st>>>(m, t, x, rho);
+            count_launch();
+        }
+    }
+    for (int r = 0; r < R && rc == TC_OK; ++r) {
+        for (int n = 0; n < TC_ORDER; ++n) {
+            col_get_kernel<T><<<grid_for(I[n]), 256, 0, st>>>((const T *)factors[n], I[n], R, r, col[n]);
+            count_launch();
+        }
+        if (m > 0) {   // rho += u_r v_r w_r
+            rc = launch_tttp(p, TC_W_ONE, nullptr, 1, cols, x, st);
+            if (rc != TC_OK) break;
+            resid_axpy_kernel<T><<<grid_for(m), 256, 0, st>>>(m, T(1), x, rho);
+            count_launch();
+        }
+        for (int d = 0; d < TC_ORDER && rc == TC_OK; ++d) {
+            rc = launch_mttkrp(p, TC_W_ARRAY, rho, 1, cols, d, num, 0, st);
+            if (rc != TC_OK) break;
+            rc = launch_solve_factor(p, TC_W_ONE, nullptr, 1, cols, d, num, lambda, TC_PREC_FP32,
+                                     col[d], nullptr, 0, TC_LOSS_LS, nullptr, st);
+        }
+        if (rc != TC_OK) break;
+        if (m > 0) {   // rho -= (new) u_r v_r w_r
+            rc = launch_tttp(p, TC_W_ONE, nullptr, 1, cols, x, st);
+            if (rc != TC_OK) break;
+            resid_axpy_kernel<T><<<grid_for(m), 256, 0, st>>>(m, T(-1), x, rho);
+            count_launch();
+        }
+        for (int n = 0; n < TC_ORDER; ++n) {
+            col_put_kernel<T><<<grid_for(I[n]), 256, 0, st>>>((T *)factors[n], I[n], R, r, col[n]);
+            count_launch();
+        }
+    }
+    if (rc == TC_OK && cudaGetLastError() != cudaSuccess) rc = TC_ERR_CUDA;
+    cudaFreeAsync(buf, st);
+    return rc;
+}
+
+}  // namespace tc
+
+using namespace tc;
+
+extern "C" tc_status tc_ccd_sweep(const tc_pattern *p, int R, void *const *factors, double lambda,
+                                  tc_stream_t stream) {
+    if (!p || R < 1 || R > TC_MAX_RANK || !factors) return TC_ERR_ARG;
+    for (int n = 0; n < TC_ORDER; ++n)
+        if (!factors[n]) return TC_ERR_ARG;
+    if (!p->has_vals && p->nnz > 0) return TC_ERR_ARG;
+    if (p->dtype == TC_F64) return ccd_t<double>(p, R, factors, lambda, (cudaStream_t)stream);
+    return ccd_t<float>(p, R, factors, lambda, (cudaStream_t)stream);
+}

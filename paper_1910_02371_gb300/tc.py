@@ -63,6 +63,7 @@ _SIGS = {
     "tc_newton_als_mode": [_P, _I, _I, _P, _I, _D, _I, _D, _I, _P, _P],
     "tc_newton_matvec": [_P, _I, _I, _P, _P, _D, _P, _P],
     "tc_cg_set_hessian": [_P, _I],
+    "tc_ccd_sweep": [_P, _I, _P, _D, _P],
 }
 for _name, _args in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -396,3 +397,11 @@ def newton_als_mode(p: Pattern, factors, mode: int, loss: str, lam: float, inner
                                    int(inner_iters), float(tol), PRECS[prec], ctypes.byref(steps),
                                    _stream(stream)), "tc_newton_als_mode")
     return int(steps.value)
+
+
+def ccd_sweep(p: Pattern, factors, lam: float, stream=None):
+    """tc_ccd_sweep: one CCD++ sweep (least squares) on the factors in place."""
+    R = factors[0].shape[1]
+    _check(_lib.tc_ccd_sweep(p.handle, R, _ptrs(factors), float(lam), _stream(stream)),
+           "tc_ccd_sweep")
+    return factors
