@@ -195,7 +195,7 @@ def run_ours(args):
         for a, a0 in zip(A, A0):
             a.copy_(a0)
         tc.tttp(p, A, weights=None, out=xbuf)
-        drivers.als_sweep(p, A, w.lam, rhs=rhs)
+        drivers.als_sweep(p, A, w.lam, rhs=rhs, prec=args.prec)
         cg.ggn_step(CG_ITERS, loss_out=loss)
 
     for _ in range(args.warmup):
@@ -273,11 +273,37 @@ def run_ours(args):
     kern["precond_setup"] = timed(lambda: cg.setup())
     kern[f"pcg_{CG_ITERS}_iters_graph"] = timed(lambda: cg.solve(gb, CG_ITERS, dx=dxv))
     B = [a.clone() for a in A0]
-    kern["als_sweep"] = timed(lambda: drivers.als_sweep(p, B, w.lam, rhs=rhs))
+    kern["als_sweep"] = timed(lambda: drivers.als_sweep(p, B, w.lam, rhs=rhs, prec=args.prec))
     kern["ggn_step"] = timed(lambda: cg.ggn_step(CG_ITERS, loss_out=loss), reps=3)
     torch.cuda.synchronize()
     if tc.last_error(p) not in (tc.OK,):
         raise RuntimeError("device error in breakdown")
+
+    # ---- optional: one ALS sweep in each Solve Factor precision form, from the
+    # same start, with its time and its objective against the refined FP32 form
+    als_forms = None
+    if args.als_forms:
+        als_forms = {}
+        fval = {}
+        for form in ("fp32_refine", "fp32", "tf32_refine", "bf16_refine", "fp32_refine_chol32",
+                     "tf32_refine_chol32", "bf16_refine_chol32"):
+            B = [a.clone() for a in A0]
+
+            def sweep_from_start(form=form, B=B):
+                for b, a0 in zip(B, A0):     # (three factor copies, negligible)
+                    b.copy_(a0)
+                drivers.als_sweep(p, B, w.lam, rhs=rhs, prec=form)
+
+            ms = timed(sweep_from_start, reps=3)
+            sweep_from_start()
+            f_t, _ = tc.loss_grad(p, B, "ls", w.lam, want_grad=False)
+            fval[form] = f_t.item()
+            als_forms[form] = {"als_sweep_ms": ms}
+        for form in als_forms:
+            als_forms[form]["objective_rel_to_fp32_refine"] = abs(fval[form] - fval["fp32_refine"]) / \
+                abs(fval["fp32_refine"])
+        if tc.last_error(p) not in (tc.OK,):
+            raise RuntimeError("device error in the precision forms")
 
     # ---- roofline of the dominant kernel (Gauss-Newton matvec: 11 per step)
     share = {
@@ -387,6 +413,10 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "clocks": clocks.summary(),
     }
+    if args.prec != "fp32":
+        result["config"]["solve_factor_form"] = args.prec
+    if als_forms is not None:
+        result["als_sweep_forms"] = als_forms
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(w, idx_h, t_h.astype(np.float64), start_h,
                                               target_s=args.cpu_seconds)
@@ -487,6 +517,11 @@ def main():
                     help="setup, warm-up and the timed steps only (for profiler runs)")
     ap.add_argument("--nnz", type=int, default=0,
                     help="use the first NNZ coordinates of the workload (smaller profiling case)")
+    ap.add_argument("--prec", default="fp32",
+                    help="Solve Factor precision form of the ALS sweep (tc.PRECS; default fp32)")
+    ap.add_argument("--als-forms", action="store_true",
+                    help="also time one ALS sweep in every precision form and report the "
+                         "objective of each against the refined FP32 form")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
