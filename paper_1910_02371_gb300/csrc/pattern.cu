@@ -291,27 +291,16 @@ radix_scatter_p_kernel(SortSide src, SortSide dst, int64_t n, int shift, int64_t
     const int64_t tile0 = (int64_t)blockIdx.x * kTileP;
     const int64_t base = tile0 + (int64_t)w * 32 * kItemsP;
     const unsigned lt_mask = (1u << lane) - 1u;
-    int32_t key[kItemsP], c1[kItemsP], c2[kItemsP];
-    int64_t prm[kItemsP];
-    VT val[kItemsP];
+    // only the keys and ranks stay in registers through the ranking; the
+    // payload is read again (from L2) when the tile is staged, which keeps
+    // the register count, and so the blocks per SM, up
+    int32_t key[kItemsP];
     int pos[kItemsP];
 #pragma unroll
     for (int r = 0; r < kItemsP; ++r) {
         const int64_t q = base + (int64_t)r * 32 + lane;
         const bool valid = q < n;
         key[r] = valid ? src.key[q] : 0;
-        if (valid) {
-            if (first) {
-                prm[r] = q;
-                c1[r] = clamp_index(src.c1[q], I1);
-                c2[r] = clamp_index(src.c2[q], I2);
-            } else {
-                prm[r] = src.perm[q];
-                c1[r] = src.c1[q];
-                c2[r] = src.c2[q];
-            }
-            if constexpr (VB > 0) val[r] = reinterpret_cast<const VT *>(src.val)[q];
-        }
         const int dig = valid ? ((key[r] >> shift) & (kDigits - 1)) : kDigits;
         const unsigned peers = __match_any_sync(0xffffffffu, dig);
         const int rank = __popc(peers & lt_mask);
@@ -351,10 +340,16 @@ radix_scatter_p_kernel(SortSide src, SortSide dst, int64_t n, int shift, int64_t
             const int dig = (key[r] >> shift) & (kDigits - 1);
             const int l = toff[dig] + wcnt[w][dig] + pos[r];
             key_s[l] = key[r];
-            perm_s[l] = prm[r];
-            c1_s[l] = c1[r];
-            c2_s[l] = c2[r];
-            if constexpr (VB > 0) reinterpret_cast<VT *>(val_s)[l] = val[r];
+            if (first) {
+                perm_s[l] = q;
+                c1_s[l] = clamp_index(src.c1[q], I1);
+                c2_s[l] = clamp_index(src.c2[q], I2);
+            } else {
+                perm_s[l] = src.perm[q];
+                c1_s[l] = src.c1[q];
+                c2_s[l] = src.c2[q];
+            }
+            if constexpr (VB > 0) reinterpret_cast<VT *>(val_s)[l] = reinterpret_cast<const VT *>(src.val)[q];
         }
     }
     __syncthreads();
