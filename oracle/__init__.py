@@ -99,7 +99,9 @@ def _p(a):
 
 
 class _Ptrs:
-    """A C array of pointers plus the arrays it keeps alive."""
+    """A C array of pointers plus the arrays it keeps alive.  The object must
+    outlive the C call that reads `ptr` (hold it in a local variable): the
+    arrays it keeps may be converted copies that die with it."""
 
     def __init__(self, arrays):
         self.keep = list(arrays)
@@ -152,7 +154,8 @@ def tttp(dims, idx, s, factors):
     x = np.zeros(max(m, 1))
     ix = _idx(idx)
     sp = None if s is None else _f64(s)
-    _check(lib().orc_tttp(N, _p(_dims(dims)), m, ix.ptr, _p(sp), R, _Ptrs(fs).ptr, _p(x)), "tttp")
+    fp = _Ptrs(fs)
+    _check(lib().orc_tttp(N, _p(_dims(dims)), m, ix.ptr, _p(sp), R, fp.ptr, _p(x)), "tttp")
     return x[:m]
 
 
@@ -164,8 +167,9 @@ def mttkrp(dims, idx, s, factors, mode):
     fs = [None if a is None else _f64(a) for a in factors]
     out = np.zeros((int(dims[mode]), R))
     sp = None if s is None else _f64(s)
-    _check(lib().orc_mttkrp(N, _p(_dims(dims)), m, _idx(idx).ptr, _p(sp), R, _Ptrs(fs).ptr,
-                            mode, _p(out)), "mttkrp")
+    ix, fp = _idx(idx), _Ptrs(fs)
+    _check(lib().orc_mttkrp(N, _p(_dims(dims)), m, ix.ptr, _p(sp), R, fp.ptr, mode, _p(out)),
+           "mttkrp")
     return out
 
 
@@ -180,7 +184,8 @@ def solve_factor(dims, idx, s, factors, mode, rhs, lam, out=None):
     out = np.zeros_like(rhs) if out is None else _f64(out).copy()
     status = np.zeros(int(dims[mode]), np.int8)
     sp = None if s is None else _f64(s)
-    rc = lib().orc_solve_factor(N, _p(_dims(dims)), m, _idx(idx).ptr, _p(sp), R, _Ptrs(fs).ptr,
+    ix, fp = _idx(idx), _Ptrs(fs)
+    rc = lib().orc_solve_factor(N, _p(_dims(dims)), m, ix.ptr, _p(sp), R, fp.ptr,
                                 mode, _p(rhs), float(lam), _p(out), _p(status))
     _check(rc, "solve_factor", allow=(ERR_NOT_SPD,))
     return out, status, rc
@@ -205,9 +210,11 @@ def loss_grad(dims, idx, t, factors, loss, lam, want_grad=True):
     fs = [_f64(a) for a in factors]
     f = np.zeros(1)
     grads = [np.zeros((int(I), R)) for I in dims] if want_grad else None
-    gp = _Ptrs(grads).ptr if want_grad else None
-    _check(lib().orc_loss_grad(N, _p(_dims(dims)), m, _idx(idx).ptr, _p(_f64(t)), R,
-                               _Ptrs(fs).ptr, LOSSES[loss], float(lam), _p(f), gp), "loss_grad")
+    gh = _Ptrs(grads) if want_grad else None
+    ix, fp = _idx(idx), _Ptrs(fs)
+    _check(lib().orc_loss_grad(N, _p(_dims(dims)), m, ix.ptr, _p(_f64(t)), R, fp.ptr,
+                               LOSSES[loss], float(lam), _p(f), gh.ptr if gh else None),
+           "loss_grad")
     return float(f[0]), grads
 
 
@@ -219,9 +226,9 @@ def ggn_matvec(dims, idx, t, factors, loss, lam, x):
     fs = [_f64(a) for a in factors]
     xs = [_f64(a) for a in x]
     ys = [np.zeros((int(I), R)) for I in dims]
-    _check(lib().orc_ggn_matvec(N, _p(_dims(dims)), m, _idx(idx).ptr, _p(_f64(t)), R,
-                                _Ptrs(fs).ptr, LOSSES[loss], float(lam), _Ptrs(xs).ptr,
-                                _Ptrs(ys).ptr), "ggn_matvec")
+    ix, fp, xp, yp = _idx(idx), _Ptrs(fs), _Ptrs(xs), _Ptrs(ys)
+    _check(lib().orc_ggn_matvec(N, _p(_dims(dims)), m, ix.ptr, _p(_f64(t)), R, fp.ptr,
+                                LOSSES[loss], float(lam), xp.ptr, yp.ptr), "ggn_matvec")
     return ys
 
 

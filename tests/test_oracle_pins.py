@@ -517,3 +517,30 @@ def test_ccd_monotone():
         f_new = oracle.objective(dims, idx, t, A, "ls", lam)
         assert f_new <= f * (1 + 1e-12)
         f = f_new
+
+
+def test_oracle_index_dtype_does_not_matter():
+    """Index arrays of any integer type are converted for the C code; the
+    converted copies must live through the call (int64 indices once read
+    freed memory), so int64 and int32 inputs give identical results."""
+    rng = np.random.default_rng(77)
+    dims, R, m = (300, 200, 100), 4, 3000
+    i64 = [rng.integers(0, I, m) for I in dims]
+    i32 = [c.astype(np.int32) for c in i64]
+    t = rng.standard_normal(m)
+    A = [rng.standard_normal((I, R)) for I in dims]
+    x = [rng.standard_normal((I, R)) for I in dims]
+    for _ in range(3):     # repeated, so freed copies would be reused
+        assert np.array_equal(oracle.tttp(dims, i64, t, A), oracle.tttp(dims, i32, t, A))
+        for d in range(3):
+            assert np.array_equal(oracle.mttkrp(dims, i64, t, A, d), oracle.mttkrp(dims, i32, t, A, d))
+            rhs = rng.standard_normal((dims[d], R))
+            a = oracle.solve_factor(dims, i64, None, A, d, rhs, 0.1)[0]
+            b = oracle.solve_factor(dims, i32, None, A, d, rhs, 0.1)[0]
+            assert np.array_equal(a, b)
+        f1, g1 = oracle.loss_grad(dims, i64, t, A, "ls", 0.1)
+        f2, g2 = oracle.loss_grad(dims, i32, t, A, "ls", 0.1)
+        assert f1 == f2 and all(np.array_equal(u, v) for u, v in zip(g1, g2))
+        y1 = oracle.ggn_matvec(dims, i64, t, A, "ls", 0.1, x)
+        y2 = oracle.ggn_matvec(dims, i32, t, A, "ls", 0.1, x)
+        assert all(np.array_equal(u, v) for u, v in zip(y1, y2))
