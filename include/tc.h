@@ -111,6 +111,20 @@ typedef enum {
 #define TC_PATTERN_CHECK_DUPLICATES 1u  /* extra sort that rejects repeated coordinates */
 #define TC_PATTERN_REFILLABLE 2u        /* keep the builder's work space for tc_pattern_refill
                                            (about 24 bytes per nonzero) */
+/* A lean pattern keeps no positions (no perm, no mode-d -> mode-0 maps): 12
+ * bytes per nonzero per mode for FP32 values instead of 28 / 20.  Calls that
+ * need the maps -- TC_W_ARRAY weights in a mode d > 0 (tc_mttkrp,
+ * tc_solve_factor), and so tc_newton_als_mode and tc_ccd_sweep -- return
+ * TC_ERR_UNSUPPORTED; tc_pattern_view gives perm = NULL.  The build borrows
+ * its sort work space from the arrays of modes not yet built and needs 20
+ * extra bytes per nonzero, 8 with TC_PATTERN_CONSUME_INPUT.  Not combinable
+ * with TC_PATTERN_CHECK_DUPLICATES or TC_PATTERN_REFILLABLE (TC_ERR_ARG). */
+#define TC_PATTERN_LEAN 4u
+/* With TC_PATTERN_LEAN only (else TC_ERR_ARG): the build may overwrite the
+ * caller's idx and vals arrays, which hold no meaningful data once the call
+ * has launched its kernels (that is, unless it returns TC_ERR_ARG or
+ * TC_ERR_OOM). */
+#define TC_PATTERN_CONSUME_INPUT 8u
 
 typedef struct tc_pattern tc_pattern;
 
@@ -149,11 +163,20 @@ tc_status tc_pattern_destroy(tc_pattern *p);
 /* Read-only device views of mode `mode`, for tests and callers that want the
  * raw structure: row_ptr[I_mode + 1] (row i's nonzeros are sorted positions
  * row_ptr[i] .. row_ptr[i+1]-1); perm[nnz] (sorted position -> input position;
- * equal indices keep input order); nonempty_rows[n_nonempty] (ascending).
+ * equal indices keep input order; NULL for a lean pattern);
+ * nonempty_rows[n_nonempty] (ascending).
  * Any output pointer may be NULL.  Reading n_nonempty synchronizes the device. */
 tc_status tc_pattern_view(const tc_pattern *p, int mode, const int64_t **row_ptr,
                           const int64_t **perm, const int32_t **nonempty_rows,
                           int64_t *n_nonempty);
+
+/* Read-only device views of mode `mode`'s sorted copies: cols1[nnz] and
+ * cols2[nnz] hold the indices of the other two modes in ascending mode order
+ * (modes 1, 2 for mode 0; 0, 2 for mode 1; 0, 1 for mode 2), vals[nnz] the
+ * values (NULL if the pattern has none), all at the sorted positions of
+ * tc_pattern_view's row_ptr.  Any output pointer may be NULL. */
+tc_status tc_pattern_columns(const tc_pattern *p, int mode, const int32_t **cols1,
+                             const int32_t **cols2, const void **vals);
 
 /* nnz, order, dims and dtype of a pattern (host values). */
 tc_status tc_pattern_info(const tc_pattern *p, int64_t *nnz, int *order, int64_t *dims,

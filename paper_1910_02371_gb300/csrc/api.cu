@@ -57,7 +57,14 @@ tc_status tc_build_pattern(int order, const int64_t *dims, int64_t nnz, const in
     *out = nullptr;
     if (order != TC_ORDER) return order >= 1 ? TC_ERR_UNSUPPORTED : TC_ERR_ARG;
     if (!dims || nnz < 0 || (dtype != TC_F32 && dtype != TC_F64)) return TC_ERR_ARG;
-    if (flags & ~(TC_PATTERN_CHECK_DUPLICATES | TC_PATTERN_REFILLABLE)) return TC_ERR_ARG;
+    if (flags & ~(TC_PATTERN_CHECK_DUPLICATES | TC_PATTERN_REFILLABLE | TC_PATTERN_LEAN |
+                  TC_PATTERN_CONSUME_INPUT))
+        return TC_ERR_ARG;
+    // a lean pattern keeps no work space and no positions; consuming the input
+    // is a lean build's way to borrow its work space
+    if ((flags & TC_PATTERN_LEAN) && (flags & (TC_PATTERN_CHECK_DUPLICATES | TC_PATTERN_REFILLABLE)))
+        return TC_ERR_ARG;
+    if ((flags & TC_PATTERN_CONSUME_INPUT) && !(flags & TC_PATTERN_LEAN)) return TC_ERR_ARG;
     for (int d = 0; d < TC_ORDER; ++d)
         if (dims[d] < 1 || dims[d] > INT32_MAX) return TC_ERR_ARG;
     if (nnz > 0) {
@@ -108,6 +115,16 @@ tc_status tc_pattern_view(const tc_pattern *p, int mode, const int64_t **row_ptr
             cudaMemcpy(n_nonempty, m.n_ne_dev, sizeof(int64_t), cudaMemcpyDeviceToHost) != cudaSuccess)
             return TC_ERR_CUDA;
     }
+    return TC_OK;
+}
+
+tc_status tc_pattern_columns(const tc_pattern *p, int mode, const int32_t **cols1,
+                             const int32_t **cols2, const void **vals) {
+    if (!p || mode < 0 || mode >= p->order) return TC_ERR_ARG;
+    const ModeData &m = p->md[mode];
+    if (cols1) *cols1 = m.cols[0];
+    if (cols2) *cols2 = m.cols[1];
+    if (vals) *vals = m.vals;
     return TC_OK;
 }
 

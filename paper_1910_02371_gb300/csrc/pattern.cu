@@ -242,7 +242,8 @@ static_assert(kDigits == kSortThreads, "one thread per digit in the tile scan");
 
 struct SortSide {
     int32_t *key;
-    int64_t *perm;   // null on the first pass: the input position
+    int64_t *perm;   // null on the first pass: the input position; a null
+                     // destination perm drops the positions (lean patterns)
     int32_t *c1, *c2;
     void *val;
 };
@@ -341,11 +342,11 @@ radix_scatter_p_kernel(SortSide src, SortSide dst, int64_t n, int shift, int64_t
             const int l = toff[dig] + wcnt[w][dig] + pos[r];
             key_s[l] = key[r];
             if (first) {
-                perm_s[l] = q;
+                if (dst.perm) perm_s[l] = q;
                 c1_s[l] = clamp_index(src.c1[q], I1);
                 c2_s[l] = clamp_index(src.c2[q], I2);
             } else {
-                perm_s[l] = src.perm[q];
+                if (dst.perm) perm_s[l] = src.perm[q];
                 c1_s[l] = src.c1[q];
                 c2_s[l] = src.c2[q];
             }
@@ -359,7 +360,7 @@ radix_scatter_p_kernel(SortSide src, SortSide dst, int64_t n, int shift, int64_t
         const int dig = (k >> shift) & (kDigits - 1);
         const int64_t o = goff[dig] + (j - toff[dig]);
         dst.key[o] = k;
-        dst.perm[o] = perm_s[j];
+        if (dst.perm) dst.perm[o] = perm_s[j];
         dst.c1[o] = c1_s[j];
         dst.c2[o] = c2_s[j];
         if constexpr (VB > 0) reinterpret_cast<VT *>(dst.val)[o] = reinterpret_cast<const VT *>(val_s)[j];
@@ -373,7 +374,7 @@ __global__ void copy_p_kernel(SortSide src, SortSide dst, int64_t n, int64_t I1,
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
          q += (int64_t)gridDim.x * blockDim.x) {
         dst.key[q] = src.key[q];
-        dst.perm[q] = q;
+        if (dst.perm) dst.perm[q] = q;
         dst.c1[q] = clamp_index(src.c1[q], I1);
         dst.c2[q] = clamp_index(src.c2[q], I2);
         if constexpr (VB > 0) reinterpret_cast<VT *>(dst.val)[q] = reinterpret_cast<const VT *>(src.val)[q];
@@ -383,13 +384,18 @@ __global__ void copy_p_kernel(SortSide src, SortSide dst, int64_t n, int64_t I1,
 static int64_t sort_tiles_p(int64_t n) { return (n + kTileP - 1) / kTileP; }
 static size_t scatter_p_smem(int vb) { return (size_t)kTileP * (8 + 4 + 4 + 4 + vb); }
 
+// first_to_out: the first pass writes `out` (so `tmp` may alias `in`, whose
+// contents are dead after that pass); with an even number of digit passes one
+// more pass on the top digit, an identity on keys already sorted, brings the
+// result back to `out`.
 template <int VB>
 static void radix_sort_p_t(const SortSide &in, const SortSide &out, const SortSide &tmp, int64_t n,
                            int64_t max_key, int64_t I1, int64_t I2, int64_t *hist, int64_t *scan,
-                           cudaStream_t st) {
+                           bool first_to_out, cudaStream_t st) {
     int bits = 0;
     while (bits < 31 && (max_key >> bits) > 0) ++bits;
-    const int passes = (bits + kRadixBits - 1) / kRadixBits;
+    const int digit_passes = (bits + kRadixBits - 1) / kRadixBits;
+    const int passes = digit_passes + ((first_to_out && digit_passes % 2 == 0 && digit_passes > 0) ? 1 : 0);
     if (n == 0) return;
     if (passes == 0) {
         copy_p_kernel<VB><<<grid_for(n, 256), 256, 0, st>>>(in, out, n, I1, I2);
@@ -403,7 +409,7 @@ static void radix_sort_p_t(const SortSide &in, const SortSide &out, const SortSi
     SortSide src = in;
     for (int p = 0; p < passes; ++p) {
         const SortSide &dst = ((passes - 1 - p) % 2 == 0) ? out : tmp;
-        const int shift = p * kRadixBits;
+        const int shift = (p < digit_passes ? p : digit_passes - 1) * kRadixBits;
         radix_hist_p_kernel<<<(unsigned)num_tiles, kSortThreads, 0, st>>>(src.key, n, shift, num_tiles,
                                                                          hist);
         count_launch();
@@ -417,10 +423,10 @@ static void radix_sort_p_t(const SortSide &in, const SortSide &out, const SortSi
 
 static void radix_sort_p(int vb, const SortSide &in, const SortSide &out, const SortSide &tmp,
                          int64_t n, int64_t max_key, int64_t I1, int64_t I2, int64_t *hist,
-                         int64_t *scan, cudaStream_t st) {
-    if (vb == 8) radix_sort_p_t<8>(in, out, tmp, n, max_key, I1, I2, hist, scan, st);
-    else if (vb == 4) radix_sort_p_t<4>(in, out, tmp, n, max_key, I1, I2, hist, scan, st);
-    else radix_sort_p_t<0>(in, out, tmp, n, max_key, I1, I2, hist, scan, st);
+                         int64_t *scan, bool first_to_out, cudaStream_t st) {
+    if (vb == 8) radix_sort_p_t<8>(in, out, tmp, n, max_key, I1, I2, hist, scan, first_to_out, st);
+    else if (vb == 4) radix_sort_p_t<4>(in, out, tmp, n, max_key, I1, I2, hist, scan, first_to_out, st);
+    else radix_sort_p_t<0>(in, out, tmp, n, max_key, I1, I2, hist, scan, first_to_out, st);
 }
 
 // ------------------------------------------------------------------ pattern kernels
@@ -579,6 +585,20 @@ static tc_status alloc_scratch(tc_pattern *p) {
     int64_t scan_n = scan_scratch_elems(hist_n);
     const int64_t s2 = scan_scratch_elems(maxI);
     if (s2 > scan_n) scan_n = s2;
+    if (p->flags & TC_PATTERN_LEAN) {
+        // sorted keys and one key buffer; the payload's work space is borrowed
+        // (fill_pattern) unless the input may not be overwritten
+        const bool own_tmp = !(p->flags & TC_PATTERN_CONSUME_INPUT);
+        const bool ok = dalloc((void **)&w.kbuf, sizeof(int32_t) * n) &&
+                        dalloc((void **)&w.ktmp, sizeof(int32_t) * n) &&
+                        dalloc((void **)&w.hist, sizeof(int64_t) * hist_n) &&
+                        dalloc((void **)&w.scan, sizeof(int64_t) * (scan_n + 1)) &&
+                        dalloc((void **)&w.flags, sizeof(int64_t) * maxI) &&
+                        (!own_tmp || (dalloc((void **)&w.c1tmp, sizeof(int32_t) * n) &&
+                                      dalloc((void **)&w.c2tmp, sizeof(int32_t) * n) &&
+                                      (!p->has_vals || dalloc(&w.valtmp, tsize(p->dtype) * n))));
+        return ok ? TC_OK : TC_ERR_OOM;
+    }
     bool ok = dalloc((void **)&w.kbuf, sizeof(int32_t) * n) &&
               dalloc((void **)&w.ktmp, sizeof(int32_t) * n) &&
               dalloc((void **)&w.vtmp, sizeof(int64_t) * n) &&
@@ -598,6 +618,7 @@ static tc_status alloc_scratch(tc_pattern *p) {
 static tc_status alloc_pattern(tc_pattern *p) {
     const int64_t n = p->nnz;
     const size_t es = tsize(p->dtype);
+    const bool lean = (p->flags & TC_PATTERN_LEAN) != 0;
     bool ok = dalloc((void **)&p->status, sizeof(int)) &&
               dalloc((void **)&p->counts, sizeof(int64_t) * TC_ORDER) &&
               dalloc((void **)&p->dscratch, sizeof(double) * kScratchDoubles);
@@ -605,13 +626,13 @@ static tc_status alloc_pattern(tc_pattern *p) {
         ModeData &m = p->md[d];
         const int64_t I = p->dims[d];
         ok = dalloc((void **)&m.row_ptr, sizeof(int64_t) * (I + 1)) &&
-             dalloc((void **)&m.perm, sizeof(int64_t) * n) &&
+             (lean || dalloc((void **)&m.perm, sizeof(int64_t) * n)) &&
              dalloc((void **)&m.nz_rows, sizeof(int32_t) * I) &&
              dalloc((void **)&m.nz_ptr, sizeof(int64_t) * (I + 1)) &&
              dalloc((void **)&m.cols[0], sizeof(int32_t) * n) &&
              dalloc((void **)&m.cols[1], sizeof(int32_t) * n) &&
              (!p->has_vals || dalloc(&m.vals, es * n)) &&
-             (d == 0 || dalloc((void **)&m.to0, sizeof(int64_t) * n));
+             (d == 0 || lean || dalloc((void **)&m.to0, sizeof(int64_t) * n));
         m.n_ne_dev = p->counts ? p->counts + d : nullptr;
     }
     if (!ok) return TC_ERR_OOM;
@@ -631,6 +652,8 @@ static void fill_pattern(tc_pattern *p, const int32_t *const *idx, const void *v
             count_launch();
         }
     }
+    const bool lean = (p->flags & TC_PATTERN_LEAN) != 0;
+    const bool consume = (p->flags & TC_PATTERN_CONSUME_INPUT) != 0;
     for (int d = 0; d < TC_ORDER; ++d) {
         ModeData &m = p->md[d];
         const int64_t I = p->dims[d];
@@ -642,11 +665,27 @@ static void fill_pattern(tc_pattern *p, const int32_t *const *idx, const void *v
                     const_cast<int32_t *>(idx[o2]), const_cast<void *>(vals)};
         SortSide out{w.kbuf, m.perm, m.cols[0], m.cols[1], m.vals};
         SortSide tmp{w.ktmp, w.vtmp, w.c1tmp, w.c2tmp, w.valtmp};
+        bool first_to_out = false;
+        if (lean) {
+            // work space of a lean build: mode 0 sorts through the arrays of
+            // modes 1 and 2 (not yet built), mode 1 through those of mode 2,
+            // and mode 2 through the consumed input (or its own buffers)
+            const ModeData &m1 = p->md[1], &m2 = p->md[2];
+            if (d == 0) {
+                out.key = m1.cols[0];
+                tmp = SortSide{m1.cols[1], nullptr, m2.cols[0], m2.cols[1], m2.vals};
+            } else if (d == 1) {
+                tmp = SortSide{w.ktmp, nullptr, m2.cols[0], m2.cols[1], m2.vals};
+            } else if (consume) {
+                tmp = in;
+                first_to_out = true;
+            }
+        }
         radix_sort_p(p->has_vals ? (int)tsize(p->dtype) : 0, in, out, tmp, n, I - 1, p->dims[o1],
-                     p->dims[o2], w.hist, w.scan, st);
+                     p->dims[o2], w.hist, w.scan, first_to_out, st);
         cudaMemsetAsync(m.row_ptr, 0, sizeof(int64_t) * (I + 1), st);
         if (n > 0) {
-            row_ptr_kernel<<<grid_for(n, 256), 256, 0, st>>>(w.kbuf, n, I, m.row_ptr);
+            row_ptr_kernel<<<grid_for(n, 256), 256, 0, st>>>(out.key, n, I, m.row_ptr);
             count_launch();
         }
         nonempty_flags_kernel<<<grid_for(I, 256), 256, 0, st>>>(m.row_ptr, I, w.flags);
@@ -718,6 +757,7 @@ tc_status build_pattern_impl(int order, const int64_t *dims, int64_t nnz,
 tc_status ensure_to0(const tc_pattern *pc, cudaStream_t st) {
     tc_pattern *p = const_cast<tc_pattern *>(pc);
     if (p->to0_valid || p->nnz == 0) return TC_OK;
+    if (p->flags & TC_PATTERN_LEAN) return TC_ERR_UNSUPPORTED;   // no positions kept
     const int64_t n = p->nnz;
     int64_t *inv0 = p->work.inv0;
     const bool temp = inv0 == nullptr;

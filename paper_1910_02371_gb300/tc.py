@@ -27,6 +27,8 @@ CHOL32 = 0x100
 PRECS.update({k + "_chol32": v | CHOL32 for k, v in list(PRECS.items()) if k.endswith("_refine")})
 CHECK_DUPLICATES = 1
 REFILLABLE = 2
+LEAN = 4
+CONSUME_INPUT = 8
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is not built: run paper_1910_02371_gb300.build.build()")
@@ -42,6 +44,7 @@ _SIGS = {
     "tc_pattern_refill": [_P, _P, _P, _P],
     "tc_pattern_destroy": [_P],
     "tc_pattern_view": [_P, _I, _P, _P, _P, _P],
+    "tc_pattern_columns": [_P, _I, _P, _P, _P],
     "tc_pattern_info": [_P, _P, _P, _P, _P],
     "tc_last_error": [_P, _P],
     "tc_tttp": [_P, _I, _P, _I, _P, _P, _P],
@@ -145,8 +148,30 @@ class Pattern:
                 _cuda_memcpy_d2d(out.data_ptr(), ptr.value, nbytes)
             return out
 
-        return (grab(rp, I + 1, torch.int64), grab(pm, self.nnz, torch.int64),
-                grab(nz, nne.value, torch.int32))
+        perm = grab(pm, self.nnz, torch.int64) if pm.value else None   # None: lean pattern
+        return grab(rp, I + 1, torch.int64), perm, grab(nz, nne.value, torch.int32)
+
+    def columns(self, mode: int, lo: int = 0, hi: Optional[int] = None):
+        """tc_pattern_columns as tensors (copies of sorted positions lo..hi-1):
+        the other two modes' indices (ascending mode order) and the values
+        (None if the pattern has none)."""
+        hi = self.nnz if hi is None else hi
+        if not 0 <= lo <= hi <= self.nnz:
+            raise ValueError("0 <= lo <= hi <= nnz required")
+        c1, c2, v = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+        _check(_lib.tc_pattern_columns(self.handle, mode, ctypes.byref(c1), ctypes.byref(c2),
+                                       ctypes.byref(v)), "tc_pattern_columns")
+        torch.cuda.current_stream().synchronize()
+        n = hi - lo
+
+        def grab(ptr, dt):
+            out = torch.empty(n, dtype=dt, device=self.device)
+            if n:
+                es = out.element_size()
+                _cuda_memcpy_d2d(out.data_ptr(), ptr.value + lo * es, n * es)
+            return out
+
+        return grab(c1, torch.int32), grab(c2, torch.int32), (grab(v, self.dtype) if v.value else None)
 
 
 def _cuda_memcpy_d2d(dst: int, src: int, nbytes: int):
@@ -170,9 +195,12 @@ def _raw_tensor(ptr: int, nbytes: int):
 
 def build_pattern(idx: Sequence[torch.Tensor], dims: Sequence[int], vals: Optional[torch.Tensor] = None,
                   dtype: torch.dtype = torch.float32, check_duplicates: bool = False,
-                  refillable: bool = False, stream=None) -> Pattern:
+                  refillable: bool = False, lean: bool = False, consume_input: bool = False,
+                  stream=None) -> Pattern:
     """tc_build_pattern.  idx: `order` int32 CUDA tensors of length nnz (input
-    order); vals: nnz values of `dtype` or None."""
+    order); vals: nnz values of `dtype` or None.  lean: keep no positions
+    (TC_PATTERN_LEAN); consume_input: the build may overwrite idx and vals
+    (TC_PATTERN_CONSUME_INPUT, lean builds only)."""
     order = len(idx)
     nnz = int(idx[0].numel())
     for c in idx:
@@ -182,7 +210,8 @@ def build_pattern(idx: Sequence[torch.Tensor], dims: Sequence[int], vals: Option
         raise ValueError("vals must be contiguous, of the pattern dtype and length nnz")
     dims_arr = (ctypes.c_int64 * order)(*[int(d) for d in dims])
     out = ctypes.c_void_p()
-    flags = (CHECK_DUPLICATES if check_duplicates else 0) | (REFILLABLE if refillable else 0)
+    flags = ((CHECK_DUPLICATES if check_duplicates else 0) | (REFILLABLE if refillable else 0) |
+             (LEAN if lean else 0) | (CONSUME_INPUT if consume_input else 0))
     _check(_lib.tc_build_pattern(order, dims_arr, nnz, _ptrs(idx), _ptr(vals), _dtype_code(dtype),
                                  flags, _stream(stream), ctypes.byref(out)), "tc_build_pattern")
     return Pattern(out.value, dims, nnz, dtype, idx[0].device)

@@ -23,6 +23,11 @@ Workloads (the order-3 problems the method is benchmarked on):
                           rows in modes 0 and 1, rank 64, values round(model)
                           clamped to 1..5, lambda 0.05 (a synthetic stand-in with
                           the shape of the Netflix ratings tensor).
+* ``cp3_4M_m4B_r16``     2^22 cubed, 4e9 uniform coordinates, rank 16, FP32,
+                          planted N(0,1) factors + N(0, 0.1^2) noise, lambda 1e-2
+                          (the paper's 1e10-nonzero synthetic scaled to one GPU).
+                          Too large for host generation: its coordinates come
+                          from ``feistel_coords``, evaluated where they are used.
 """
 from __future__ import annotations
 
@@ -34,7 +39,7 @@ import numpy as np
 
 __all__ = [
     "Workload", "WORKLOADS", "stream", "distinct_coords", "zipf_ids",
-    "factor_matrices", "observe", "make_coords", "scaled",
+    "factor_matrices", "observe", "make_coords", "scaled", "feistel_keys", "feistel_coords",
 ]
 
 # Purposes of the independent random streams drawn from one seed.
@@ -80,8 +85,59 @@ WORKLOADS = {
         Workload("cp3_netflix_m100M_r64", (480_189, 17_770, 2_182), 100_000_000, 64, "f32",
                  0.05, "ls", ("zipf", "zipf", "uniform"), "uniform_c", "round15",
                  seed=1910023714),
+        Workload("cp3_4M_m4B_r16", (1 << 22,) * 3, 4_000_000_000, 16, "f32", 1e-2, "ls",
+                 ("uniform",) * 3, "normal", "noise", noise=0.1, seed=1910023715),
     ]
 }
+
+
+# ------------------------------------------------------------------ keyed permutation
+# Distinct uniform coordinates without a dedup pass, for tensors too large to
+# draw on the host: entry e (e = 0, 1, ...) gets the image of e under a keyed
+# permutation of the 3b-bit index space [0, 2^(3b)) (b bits per mode, all dims
+# 2^b), so distinct entries get distinct coordinates and the coordinates look
+# uniform.  The permutation is a balanced Feistel network (Luby & Rackoff,
+# SIAM J. Comput. 17(2), 1988) of 4 rounds on two 3b/2-bit halves, with a
+# multiply-xorshift round function.  Every intermediate stays below 2^63, so
+# the same code runs on numpy int64 arrays and on torch int64 tensors (on any
+# device) with identical results.
+FEISTEL_ROUNDS = 4
+
+
+def feistel_keys(seed: int):
+    """Round keys: (xor key, odd multiplier, odd multiplier) per round, each
+    below 2^30, from the coordinate stream of ``seed``."""
+    rng = stream(seed, _S_COORD)
+    k = rng.integers(1, 1 << 30, size=(FEISTEL_ROUNDS, 3), dtype=np.int64)
+    k[:, 1:] |= 1
+    return [tuple(int(v) for v in row) for row in k]
+
+
+def _feistel_f(x, key, m1, m2, mask):
+    y = (x ^ key) & mask
+    y = (y * m1) & mask
+    y = y ^ (y >> 16)
+    y = (y * m2) & mask
+    return y ^ (y >> 13)
+
+
+def feistel_coords(e, bits: int, keys):
+    """Coordinates (i_0, i_1, i_2) of entries e (int64 array or tensor, values
+    in [0, 2^min(63, 3 bits))) for dims (2^bits,) * 3; bits even, 2..22.
+    Returns three int64 arrays/tensors of e's type."""
+    if bits % 2 or not 2 <= bits <= 22:
+        raise ValueError("bits must be even, 2..22")
+    h = 3 * bits // 2
+    mask = (1 << h) - 1
+    left, right = e >> h, e & mask
+    for key, m1, m2 in keys:
+        left, right = right, left ^ _feistel_f(right, key, m1, m2, mask)
+    bmask = (1 << bits) - 1
+    lo = bits // 2               # bits of i_1 held in `right`
+    i0 = right & bmask
+    i1 = (right >> bits) | ((left & ((1 << lo) - 1)) << (h - bits))
+    i2 = left >> lo
+    return i0, i1, i2
 
 
 def scaled(w: Workload, nnz: int, dims: Optional[Sequence[int]] = None, **kw) -> Workload:

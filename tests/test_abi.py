@@ -55,6 +55,10 @@ def test_argument_errors_without_device(lib):
     assert lib.tc_build_pattern(3, dims, 10, None, None, 0, 0, None, ctypes.byref(out)) == 1
     assert lib.tc_build_pattern(3, dims, 0, None, None, 7, 0, None, ctypes.byref(out)) == 1
     assert lib.tc_build_pattern(3, dims, 0, None, None, 0, 0, None, None) == 1
+    # flags: unknown bits, consuming the input without a lean build, lean with
+    # the refill work space or the duplicate check
+    for flags in (16, 8, 4 | 2, 4 | 1):
+        assert lib.tc_build_pattern(3, dims, 0, None, None, 0, flags, None, ctypes.byref(out)) == 1
     bad = (ctypes.c_int64 * 3)(4, 0, 6)
     assert lib.tc_build_pattern(3, bad, 0, None, None, 0, 0, None, ctypes.byref(out)) == 1
     lib.tc_tttp.argtypes = [P, ctypes.c_int, P, ctypes.c_int, P, P, P]

@@ -1,0 +1,224 @@
+"""Full-size parity at 4e9 nonzeros: the order-3 tensor 2^22 x 2^22 x 2^22 with
+4e9 uniform coordinates, rank 16, FP32 (the paper's 1e10-nonzero synthetic
+problem, Sec. 5, scaled to one GPU), held in a lean pattern built from the
+consumed input.
+
+The host can neither hold nor draw this tensor quickly, so it is generated on
+the device chunk by chunk: coordinates from synth.feistel_coords (distinct by
+construction), values from the planted N(0,1) factors (the CP model evaluated
+in FP64 with plain torch ops) plus N(0, 0.1^2) noise.  The nonzeros of a few
+sampled rows per mode are copied to the host as they are generated.
+
+Checked:
+* every mode's row offsets against per-row counts, and the sorted copies of
+  the sampled rows against those rows' input entries in input order (exact);
+* TTTP, MTTKRP, Solve Factor (FP32 + refinement and TF32 + refinement) and the
+  Gauss-Newton product on the sampled rows, against the oracle run on those
+  rows' nonzeros (the per-row results are the same as on the whole tensor);
+* one ALS sweep in the plain FP32 form and in the mixed TF32 + refinement
+  form, each followed by 5 Gauss-Newton steps of 10 CG iterations: the two
+  objectives agree to 1e-6 after the sweep, the last updated factor's
+  gradient vanishes (an exact row solve makes it zero at any size), and the
+  Gauss-Newton steps do not raise the objective."""
+import gc
+import time
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from helpers import TOL, host, rel, to_dev
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+W = synth.WORKLOADS["cp3_4M_m4B_r16"]
+BITS = 22
+CHUNK = 1 << 24
+ROWS_PER_MODE = 10
+FORM_TOL = {"fp32_refine": TOL["f32"], "tf32_refine": 2e-4}
+# input + lean pattern + build work space (8 + ~1 bytes per nonzero), with margin
+NEED_BYTES = W.nnz * (16 + 36 + 9) + (12 << 30)
+
+
+def _sampled_rows(rng):
+    out = []
+    for I in W.dims:
+        r = rng.choice(I, size=ROWS_PER_MODE, replace=False)
+        out.append(np.unique(np.concatenate([r, [0, I - 1]])).astype(np.int64))
+    return out
+
+
+@pytest.fixture(scope="module")
+def big():
+    gc.collect()
+    torch.cuda.empty_cache()
+    free, _ = torch.cuda.mem_get_info()
+    if free < NEED_BYTES:
+        pytest.skip(f"needs {NEED_BYTES / 1e9:.0f} GB of free device memory, {free / 1e9:.0f} GB free")
+    from paper_1910_02371_gb300 import build as b
+    b.build()
+    from paper_1910_02371_gb300 import tc
+
+    planted = synth.factor_matrices(W.dims, W.rank, W.factor_dist, W.seed)
+    start = [a.astype(np.float32).astype(np.float64) for a in synth.perturb(planted, W.seed)]
+    planted_dev = [torch.as_tensor(a, device="cuda") for a in planted]
+    del planted
+    rows = _sampled_rows(np.random.default_rng(W.seed % 1000))
+    rows_dev = [torch.as_tensor(r, device="cuda") for r in rows]
+    keys = synth.feistel_keys(W.seed)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(W.seed)
+
+    idx = [torch.empty(W.nnz, dtype=torch.int32, device="cuda") for _ in range(3)]
+    vals = torch.empty(W.nnz, dtype=torch.float32, device="cuda")
+    counts = [torch.zeros(I, dtype=torch.int64, device="cuda") for I in W.dims]
+    parts = [[] for _ in range(3)]
+    t0 = time.time()
+    for s in range(0, W.nnz, CHUNK):
+        n = min(CHUNK, W.nnz - s)
+        e = torch.arange(s, s + n, dtype=torch.int64, device="cuda")
+        c = synth.feistel_coords(e, BITS, keys)
+        # the CP model at these coordinates (FP64), plus noise
+        m = planted_dev[0][c[0]]
+        m *= planted_dev[1][c[1]]
+        m *= planted_dev[2][c[2]]
+        t = m.sum(1)
+        del m
+        t += W.noise * torch.randn(n, dtype=torch.float64, device="cuda", generator=gen)
+        t32 = t.to(torch.float32)
+        vals[s:s + n] = t32
+        for d in range(3):
+            idx[d][s:s + n] = c[d].to(torch.int32)
+            counts[d] += torch.bincount(c[d], minlength=W.dims[d])
+            hit = torch.isin(c[d], rows_dev[d]).nonzero().squeeze(1)
+            if hit.numel():
+                parts[d].append(torch.stack([c[0][hit], c[1][hit], c[2][hit]]).cpu().numpy())
+                parts[d].append(t32[hit].double().cpu().numpy()[None, :])
+        del e, c, t, t32
+    gen_s = time.time() - t0
+    del planted_dev
+    sub = []
+    for d in range(3):
+        ci = np.concatenate(parts[d][0::2], axis=1)
+        tv = np.concatenate(parts[d][1::2], axis=1)[0]
+        sub.append(([ci[0].copy(), ci[1].copy(), ci[2].copy()], tv))
+    del parts
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    p = tc.build_pattern(idx, W.dims, vals, lean=True, consume_input=True)
+    ev1.record()
+    torch.cuda.synchronize()
+    build_ms = ev0.elapsed_time(ev1)
+    del idx, vals
+    torch.cuda.empty_cache()
+    print(f"\n[4e9] generated in {gen_s:.1f} s; lean build {build_ms:.0f} ms; "
+          f"device memory in use after the build {torch.cuda.mem_get_info()[1] / 1e9 - torch.cuda.mem_get_info()[0] / 1e9:.0f} GB")
+    return dict(tc=tc, p=p, rows=rows, sub=sub, counts=counts, start=start)
+
+
+def test_4b_pattern(big):
+    tc, p = big["tc"], big["p"]
+    for d in range(3):
+        o1, o2 = [m for m in range(3) if m != d]
+        row_ptr, perm, nz = p.view(d)
+        assert perm is None
+        cnt = big["counts"][d]
+        expect = torch.zeros(W.dims[d] + 1, dtype=torch.int64, device="cuda")
+        expect[1:] = torch.cumsum(cnt, 0)
+        assert torch.equal(row_ptr, expect), d
+        assert torch.equal(nz, torch.nonzero(cnt).squeeze(1).to(torch.int32)), d
+        ci, tv = big["sub"][d]
+        rp = row_ptr.cpu().numpy()
+        for i in big["rows"][d]:
+            mine = ci[d] == i
+            c1, c2, v = p.columns(d, int(rp[i]), int(rp[i + 1]))
+            assert np.array_equal(c1.cpu().numpy(), ci[o1][mine]), (d, i)
+            assert np.array_equal(c2.cpu().numpy(), ci[o2][mine]), (d, i)
+            assert np.array_equal(v.double().cpu().numpy(), tv[mine]), (d, i)
+    assert tc.last_error(p) == tc.OK
+
+
+def test_4b_kernels_on_sampled_rows(big):
+    tc, p, A = big["tc"], big["p"], big["start"]
+    Ad = [to_dev(a, "f32") for a in A]
+    rng = np.random.default_rng(3)
+    x = [rng.standard_normal((I, W.rank)).astype(np.float32).astype(np.float64) for I in W.dims]
+    y = [host(v) for v in tc.ggn_matvec(p, Ad, [to_dev(v, "f32") for v in x], "ls", W.lam)]
+    # TTTP with the values, on the mode-0 sampled rows (pattern order)
+    xt = tc.tttp(p, Ad, weights="values")
+    rp0 = p.view(0)[0].cpu().numpy()
+    ci0, tv0 = big["sub"][0]
+    for i in big["rows"][0]:
+        mine = ci0[0] == i
+        got = xt[int(rp0[i]):int(rp0[i + 1])].double().cpu().numpy()
+        ref = oracle.tttp(W.dims, [c[mine] for c in ci0], tv0[mine], A)
+        assert rel(got, ref) <= TOL["f32"], i
+    del xt
+    for d in range(3):
+        ci, tv = big["sub"][d]
+        rows = big["rows"][d]
+        m = host(tc.mttkrp(p, Ad, d))
+        mo = oracle.mttkrp(W.dims, ci, tv, A, d)
+        assert rel(m[rows], mo[rows]) <= TOL["f32"], d
+        yo = oracle.ggn_matvec(W.dims, ci, tv, A, "ls", W.lam, x)[d]
+        assert rel(y[d][rows], yo[rows]) <= TOL["f32"], d
+        rhs = mo.astype(np.float32).astype(np.float64)
+        ref, _, rc = oracle.solve_factor(W.dims, ci, None, A, d, rhs, W.lam)
+        assert rc == 0
+        rhs_d = to_dev(rhs, "f32")
+        for prec, tol in FORM_TOL.items():
+            out = host(tc.solve_factor(p, Ad, d, rhs_d, W.lam, prec=prec))
+            assert rel(out[rows], ref[rows]) <= tol, (d, prec, rel(out[rows], ref[rows]))
+    assert tc.last_error(p) == tc.OK
+
+
+def test_4b_als_and_gauss_newton_forms(big):
+    from paper_1910_02371_gb300 import drivers
+    tc, p = big["tc"], big["p"]
+
+    def objective(B):
+        f, _ = tc.loss_grad(p, B, "ls", W.lam, want_grad=False)
+        return f.item()
+
+    f0 = objective([to_dev(a, "f32") for a in big["start"]])
+    res = {}
+    for prec in ("fp32", "tf32_refine"):
+        B = [to_dev(a, "f32") for a in big["start"]]
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record()
+        drivers.als_sweep(p, B, W.lam, prec=prec)
+        ev[1].record()
+        f_als = objective(B)
+        # the last updated factor solves its row systems: its gradient is zero
+        _, g = tc.loss_grad(p, B, "ls", W.lam, want_loss=False)
+        g2 = host(g[2])
+        scale = 2.0 * np.linalg.norm(host(tc.mttkrp(p, B, 2)))
+        ev[1].synchronize()
+        gn = drivers.GaussNewton(p, B, "ls", W.lam)
+        ev[2].record()
+        for _ in range(5):
+            gn.step(10)
+        ev_end = torch.cuda.Event(enable_timing=True)
+        ev_end.record()
+        torch.cuda.synchronize()
+        f_gn = objective(B)
+        res[prec] = dict(f_als=f_als, f_gn=f_gn, grad_rel=float(np.linalg.norm(g2) / scale),
+                         als_ms=ev[0].elapsed_time(ev[1]), gn_ms=ev[2].elapsed_time(ev_end))
+        del gn, B
+    print(f"\n[4e9] start objective {f0:.6e}; " +
+          "; ".join(f"{k}: ALS sweep {v['als_ms']:.0f} ms -> {v['f_als']:.9e} (grad rel "
+                    f"{v['grad_rel']:.1e}), 5 GGN steps {v['gn_ms']:.0f} ms -> {v['f_gn']:.9e}"
+                    for k, v in res.items()))
+    assert tc.last_error(p) == tc.OK
+    plain, mixed = res["fp32"], res["tf32_refine"]
+    for r in res.values():
+        assert r["f_als"] < f0
+        assert r["grad_rel"] <= 1e-4
+        assert r["f_gn"] <= r["f_als"] * (1 + 1e-6)
+    assert abs(mixed["f_als"] - plain["f_als"]) <= 1e-6 * plain["f_als"]
+    assert abs(mixed["f_gn"] - plain["f_gn"]) <= 1e-5 * plain["f_gn"]
