@@ -189,26 +189,29 @@ def run_ours(args):
     xbuf = torch.empty(m, dtype=f32, device=dev)
     loss = torch.zeros(1, dtype=torch.float64, device=dev)
     if args.solve_probe is not None:
-        # one Solve Factor call on one mode (right-hand side: the MTTKRP of the
-        # values), timed alone: the command the Solve Factor profiles use
+        # Solve Factor on one mode (right-hand side: the MTTKRP of the values),
+        # timed alone in each form of --prec (comma-separated, in that order:
+        # one untimed call, then --steps timed calls per form): the command the
+        # Solve Factor profiles use
         d = args.solve_probe
         b = tc.mttkrp(p, A, d)
         out = torch.empty_like(b)
-        tc.solve_factor(p, A, d, b, w.lam, out=out, prec=args.prec)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(args.steps):
-            tc.solve_factor(p, A, d, b, w.lam, out=out, prec=args.prec)
-        e1.record()
-        e1.synchronize()
+        ms = {}
+        for form in args.prec.split(","):
+            tc.solve_factor(p, A, d, b, w.lam, out=out, prec=form)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(args.steps):
+                tc.solve_factor(p, A, d, b, w.lam, out=out, prec=form)
+            e1.record()
+            e1.synchronize()
+            ms[form] = e0.elapsed_time(e1) / args.steps
         if tc.last_error(p) != tc.OK:
             raise RuntimeError("device error in the Solve Factor probe")
         if rank == 0:
             print(json.dumps({"solve_probe": {"workload": w.name, "nnz": w.nnz, "mode": d,
-                                              "rows": w.dims[d], "prec": args.prec,
-                                              "ms_per_call": e0.elapsed_time(e1) / args.steps}}),
-                  flush=True)
+                                              "rows": w.dims[d], "ms_per_call": ms}}), flush=True)
         if world > 1:
             dist.destroy_process_group()
         return
@@ -545,7 +548,8 @@ def main():
     ap.add_argument("--prec", default="fp32",
                     help="Solve Factor precision form of the ALS sweep (tc.PRECS; default fp32)")
     ap.add_argument("--solve-probe", type=int, default=None, metavar="MODE",
-                    help="time one Solve Factor call on MODE (--steps calls, form --prec) and exit")
+                    help="time Solve Factor on MODE (--steps calls per form of --prec, "
+                         "comma-separated) and exit")
     ap.add_argument("--als-forms", action="store_true",
                     help="also time one ALS sweep in every precision form and report the "
                          "objective of each against the refined FP32 form")
