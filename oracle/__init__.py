@@ -22,6 +22,10 @@ routines the way the paper composes its kernels:
   the residual rho^(r) = t - m + u_r v_r w_r, then column r of each factor in
   turn set to MTTKRP(rho^(r)) / (lambda + sum of squared products), the
   residual updated in between.
+* Coordinate minimization for a general loss (Sec. 2.3, last paragraph; the
+  inner tolerances of Sec. 5.7): in the same order, Newton steps on each
+  column with the rest fixed; the column's elements are decoupled, so a step
+  is the gradient over the diagonal second derivative, element by element.
 * Gauss-Newton step (Sec. 2.5): gradient, block-diagonal preconditioner (the
   diagonal blocks of the Gauss-Newton matrix, applied through Solve Factor with
   weights phi'' and regularization 2 lambda), preconditioned CG from zero for a
@@ -378,3 +382,37 @@ def ccd_sweep(dims, idx, t, factors, lam):
             A[d][:, r] = num / den
         rho = rho - tttp(dims, idx, None, [col(n) for n in range(N)])
     return A
+
+
+def ccd_newton_sweep(dims, idx, t, factors, loss, lam, inner_iters=5, tol=1e-3):
+    """Coordinate minimization for a general loss (Sec. 2.3, last paragraph),
+    CCD++ order: for r = 0 .. R-1 and each mode d in turn, Newton steps on
+    column r of A^(d) with everything else fixed.  Each nonzero involves one
+    row of A^(d), so the column's elements are decoupled and one step is, per
+    row i (Table 1 scaling: f = sum phi + lam sum ||A||^2),
+      delta_i = -(sum_e phi'_e h_e + 2 lam u_ir) / (sum_e phi''_e h_e^2 + 2 lam),
+      h_e = prod_{n != d} A^(n)[i_n(e), r],
+    with phi', phi'' at the current model entries.  A column stops after
+    inner_iters steps or once ||delta||_2 <= tol ||column||_2 (after the step;
+    one test per column, the reading used for general-loss ALS).  For least
+    squares one step is the CCD++ update.  Returns (factors, steps), steps[r, d]
+    the Newton steps taken on that column."""
+    A = [_f64(a).copy() for a in factors]
+    N = len(dims)
+    R = A[0].shape[1]
+    steps = np.zeros((R, N), dtype=np.int64)
+    for r in range(R):
+        for d in range(N):
+            for _ in range(inner_iters):
+                d1, d2 = loss_derivs(dims, idx, t, A, loss)
+                cols = [A[n][:, r:r + 1].copy() for n in range(N)]
+                g = mttkrp(dims, idx, d1, cols, d)[:, 0] + 2.0 * lam * A[d][:, r]
+                h = mttkrp(dims, idx, d2, [c * c for c in cols], d)[:, 0] + 2.0 * lam
+                if not np.all(h > 0.0):
+                    raise OracleError(ERR_NOT_SPD, "ccd_newton_sweep")
+                delta = -g / h
+                A[d][:, r] = A[d][:, r] + delta
+                steps[r, d] += 1
+                if np.linalg.norm(delta) <= tol * np.linalg.norm(A[d][:, r]):
+                    break
+    return A, steps

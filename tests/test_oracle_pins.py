@@ -519,6 +519,78 @@ def test_ccd_monotone():
         f = f_new
 
 
+# ------------------------------------------- coordinate minimization, general loss (Sec. 2.3)
+def _poisson_small(dims, nnz, R, seed):
+    idx, planted, t = small_problem(dims, nnz, R, seed, factor="uniform01", recipe="poisson")
+    return idx, t, [0.8 * a for a in planted]
+
+
+def test_ccd_newton_ls_one_step_is_ccd():
+    """Sec. 2.3: for least squares one Newton step per column is the CCD++
+    update (pinned above), and a second step finds nothing left to do."""
+    dims = (14, 12, 10)
+    idx, _, t = small_problem(dims, 700, 3, seed=51, noise=0.2)
+    A = synth.init_factors(dims, 3, seed=51)
+    ref = oracle.ccd_sweep(dims, idx, t, A, 0.3)
+    one, steps = oracle.ccd_newton_sweep(dims, idx, t, A, "ls", 0.3, inner_iters=1)
+    assert (steps == 1).all()
+    two, steps2 = oracle.ccd_newton_sweep(dims, idx, t, A, "ls", 0.3, inner_iters=5, tol=1e-6)
+    assert (steps2 == 2).all()
+    for d in range(3):
+        np.testing.assert_allclose(one[d], ref[d], rtol=1e-11, atol=1e-13)
+        np.testing.assert_allclose(two[d], ref[d], rtol=1e-11, atol=1e-13)
+
+
+def test_ccd_newton_step_is_the_coordinate_newton_step():
+    """One step on column r = 0 of A^(0) is, for every row i, -f'/f'' of the
+    objective along u_i0, with both derivatives taken by central differences
+    of the objective itself (the first update of the sweep)."""
+    dims = (7, 6, 5)
+    idx, t, A = _poisson_small(dims, 150, 2, seed=53)
+    lam = 0.4
+    out, _ = oracle.ccd_newton_sweep(dims, idx, t, A, "poisson_log", lam, inner_iters=1)
+    got = out[0][:, 0] - A[0][:, 0]
+    h = 1e-4
+    for i in range(dims[0]):
+        def f(delta):
+            B = [a.copy() for a in A]
+            B[0][i, 0] += delta
+            return oracle.objective(dims, idx, t, B, "poisson_log", lam)
+        f0, fp, fm = f(0.0), f(h), f(-h)
+        d1 = (fp - fm) / (2 * h)
+        d2 = (fp - 2 * f0 + fm) / (h * h)
+        assert abs(got[i] - (-d1 / d2)) <= 1e-5 * max(1.0, abs(d1 / d2)), i
+
+
+def test_ccd_newton_converges_to_column_stationarity():
+    """With many steps each column reaches its minimizer: the gradient (Table 1,
+    pinned above) in the last updated column vanishes at the end of the sweep."""
+    dims = (9, 8, 7)
+    idx, t, A = _poisson_small(dims, 300, 3, seed=55)
+    lam = 1.0
+    out, steps = oracle.ccd_newton_sweep(dims, idx, t, A, "poisson_log", lam, inner_iters=60,
+                                         tol=1e-13)
+    assert steps.max() < 60
+    _, g = oracle.loss_grad(dims, idx, t, out, "poisson_log", lam)
+    assert np.abs(g[2][:, -1]).max() <= 1e-9 * np.abs(g[0]).max()
+
+
+def test_ccd_newton_poisson_monotone():
+    """Columns minimized exactly (convex in each coordinate for the log link)
+    make every sweep non-increasing; lambda = 1 as for coordinate minimization
+    in Sec. 5.7."""
+    dims = (16, 14, 12)
+    idx, t, A = _poisson_small(dims, 900, 4, seed=57)
+    lam = 1.0
+    f = oracle.objective(dims, idx, t, A, "poisson_log", lam)
+    for _ in range(3):
+        A, _ = oracle.ccd_newton_sweep(dims, idx, t, A, "poisson_log", lam, inner_iters=40,
+                                       tol=1e-12)
+        f_new = oracle.objective(dims, idx, t, A, "poisson_log", lam)
+        assert f_new <= f * (1 + 1e-12)
+        f = f_new
+
+
 def test_oracle_index_dtype_does_not_matter():
     """Index arrays of any integer type are converted for the C code; the
     converted copies must live through the call (int64 indices once read
