@@ -114,7 +114,8 @@ typedef enum {
 /* A lean pattern keeps no positions (no perm, no mode-d -> mode-0 maps): 12
  * bytes per nonzero per mode for FP32 values instead of 28 / 20.  Calls that
  * need the maps -- TC_W_ARRAY weights in a mode d > 0 (tc_mttkrp,
- * tc_solve_factor), and so tc_newton_als_mode and tc_ccd_sweep -- return
+ * tc_solve_factor), and so tc_newton_als_mode, tc_ccd_sweep and
+ * tc_ccd_newton_sweep -- return
  * TC_ERR_UNSUPPORTED; tc_pattern_view gives perm = NULL.  The build borrows
  * its sort work space from the arrays of modes not yet built and needs 20
  * extra bytes per nonzero, 8 with TC_PATTERN_CONSUME_INPUT.  Not combinable
@@ -313,6 +314,23 @@ tc_status tc_newton_matvec(const tc_pattern *p, tc_loss loss, int R, const void 
  * (2R passes over the nonzeros plus 3R rank-1 Solve Factors). */
 tc_status tc_ccd_sweep(const tc_pattern *p, int R, void *const *factors, double lambda,
                        tc_stream_t stream);
+
+/* Coordinate minimization for a general loss (Sec. 2.3, last paragraph;
+ * tolerances as in Sec. 5.7), in the same CCD++ order: for r = 0 .. R-1 and
+ * each mode d in turn, Newton steps on column r of A^(d) with the rest fixed.
+ * The column's elements are decoupled, so one step is, per row i,
+ *   delta_i = -(sum_e phi'_e h_e + 2 lambda u_ir) / (sum_e phi''_e h_e^2 + 2 lambda),
+ * h_e = prod_{n != d} A^(n)[i_n(e), r], phi', phi'' at the current model
+ * entries (Table 1 scaling, as tc_loss_grad).  A column stops after
+ * inner_iters steps or once ||delta||_2 <= tol ||column||_2.  For least
+ * squares one step is the tc_ccd_sweep update.  Factors are updated in place;
+ * needs the pattern's values and lambda >= 0; a domain error or a zero
+ * denominator (lambda = 0 and an empty row) is recorded for tc_last_error.
+ * steps_out: host int[R * order] (entry r * order + d: the steps taken on that
+ * column) or NULL.  Synchronizes `stream` once per step. */
+tc_status tc_ccd_newton_sweep(const tc_pattern *p, tc_loss loss, int R, void *const *factors,
+                              double lambda, int inner_iters, double tol, int *steps_out,
+                              tc_stream_t stream);
 
 /* ------------------------------------------------------------------ GGN / PCG */
 

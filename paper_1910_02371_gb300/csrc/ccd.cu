@@ -105,6 +105,90 @@ static tc_status ccd_t(const tc_pattern *p, int R, void *const *factors, double 
     return rc;
 }
 
+// Coordinate minimization for a general loss (Sec. 2.3, last paragraph), same
+// order: Newton steps on column r of A^(d) with the rest fixed.  A nonzero
+// involves one row of A^(d), so the column's elements are decoupled and a step
+// is, per row i,
+//   (sum_e phi''_e h_e^2 + 2 lambda) delta_i = -(sum_e phi'_e h_e + 2 lambda u_ir),
+// h_e the product of the other columns: a rank-1 MTTKRP of phi' and a rank-1
+// Solve Factor with weights phi''.  The model entries m_e (pattern order) are
+// kept current by rank-1 TTTPs of (delta, other columns); phi', phi'' are
+// formed from them before every step.  The stop test (Sec. 5.7 tolerances)
+// reads two norms per step.
+template <typename T>
+static tc_status ccd_newton_t(const tc_pattern *p, tc_loss loss, int R, void *const *factors,
+                              double lambda, int inner_iters, double tol, int *steps_out,
+                              cudaStream_t st) {
+    const int64_t m = p->nnz;
+    const int64_t I[TC_ORDER] = {p->dims[0], p->dims[1], p->dims[2]};
+    const int64_t Imax = I[0] > I[1] ? (I[0] > I[2] ? I[0] : I[2]) : (I[1] > I[2] ? I[1] : I[2]);
+    const int64_t mm = m > 0 ? m : 1;
+    T *buf = nullptr;
+    double *sums = nullptr;
+    // model, phi', phi'', rank-1 TTTP (nnz each); columns; g, rhs, delta (Imax each)
+    TC_CUDA(cudaMallocAsync((void **)&buf,
+                            sizeof(T) * (size_t)(4 * mm + I[0] + I[1] + I[2] + 3 * Imax), st));
+    if (cudaMallocAsync((void **)&sums, 2 * sizeof(double), st) != cudaSuccess) {
+        cudaFreeAsync(buf, st);
+        return TC_ERR_OOM;
+    }
+    T *mv = buf, *d1 = mv + mm, *d2 = d1 + mm, *x = d2 + mm, *c0 = x + mm, *c1 = c0 + I[0],
+      *c2 = c1 + I[1], *g = c2 + I[2], *rhs = g + Imax, *delta = rhs + Imax;
+    T *col[TC_ORDER] = {c0, c1, c2};
+    const T *t = (const T *)p->md[0].vals;
+    tc_status rc = TC_OK;
+    if (m > 0) rc = launch_tttp(p, TC_W_ONE, nullptr, R, (const void *const *)factors, mv, st);
+    for (int r = 0; r < R && rc == TC_OK; ++r) {
+        for (int n = 0; n < TC_ORDER; ++n) {
+            col_get_kernel<T><<<grid_for(I[n]), 256, 0, st>>>((const T *)factors[n], I[n], R, r, col[n]);
+            count_launch();
+        }
+        for (int d = 0; d < TC_ORDER && rc == TC_OK; ++d) {
+            const void *cols[TC_ORDER] = {c0, c1, c2};
+            const void *dcols[TC_ORDER] = {c0, c1, c2};
+            dcols[d] = delta;
+            int taken = 0;
+            for (int it = 0; it < inner_iters; ++it) {
+                launch_loss_derivs<T>(m, (int)loss, t, mv, d1, d2, p->status, st);
+                rc = launch_mttkrp(p, TC_W_ARRAY, d1, 1, cols, d, g, 0, st);
+                if (rc != TC_OK) break;
+                launch_newton_rhs<T>(I[d], g, col[d], 2.0 * lambda, rhs, st);
+                rc = launch_solve_factor(p, TC_W_ARRAY, d2, 1, cols, d, rhs, 2.0 * lambda,
+                                         TC_PREC_FP32, delta, nullptr, 0, TC_LOSS_LS, nullptr, st);
+                if (rc != TC_OK) break;
+                if (m > 0) {   // m_e += delta_i h_e
+                    rc = launch_tttp(p, TC_W_ONE, nullptr, 1, dcols, x, st);
+                    if (rc != TC_OK) break;
+                    resid_axpy_kernel<T><<<grid_for(m), 256, 0, st>>>(m, T(1), x, mv);
+                    count_launch();
+                }
+                if (cudaMemsetAsync(sums, 0, 2 * sizeof(double), st) != cudaSuccess) {
+                    rc = TC_ERR_CUDA;
+                    break;
+                }
+                launch_newton_update<T>(I[d], col[d], delta, sums, st);
+                ++taken;
+                double h[2] = {0.0, 0.0};
+                if (cudaMemcpyAsync(h, sums, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                    cudaStreamSynchronize(st) != cudaSuccess) {
+                    rc = TC_ERR_CUDA;
+                    break;
+                }
+                if (sqrt(h[0]) <= tol * sqrt(h[1])) break;
+            }
+            if (steps_out) steps_out[r * TC_ORDER + d] = taken;
+        }
+        for (int n = 0; n < TC_ORDER; ++n) {
+            col_put_kernel<T><<<grid_for(I[n]), 256, 0, st>>>((T *)factors[n], I[n], R, r, col[n]);
+            count_launch();
+        }
+    }
+    if (rc == TC_OK && cudaGetLastError() != cudaSuccess) rc = TC_ERR_CUDA;
+    cudaFreeAsync(sums, st);
+    cudaFreeAsync(buf, st);
+    return rc;
+}
+
 }  // namespace tc
 
 using namespace tc;
@@ -117,4 +201,23 @@ extern "C" tc_status tc_ccd_sweep(const tc_pattern *p, int R, void *const *facto
     if (!p->has_vals && p->nnz > 0) return TC_ERR_ARG;
     if (p->dtype == TC_F64) return ccd_t<double>(p, R, factors, lambda, (cudaStream_t)stream);
     return ccd_t<float>(p, R, factors, lambda, (cudaStream_t)stream);
+}
+
+extern "C" tc_status tc_ccd_newton_sweep(const tc_pattern *p, tc_loss loss, int R,
+                                         void *const *factors, double lambda, int inner_iters,
+                                         double tol, int *steps_out, tc_stream_t stream) {
+    if (!p || R < 1 || R > TC_MAX_RANK || !factors) return TC_ERR_ARG;
+    for (int n = 0; n < TC_ORDER; ++n)
+        if (!factors[n]) return TC_ERR_ARG;
+    if (loss != TC_LOSS_LS && loss != TC_LOSS_POISSON_LOG && loss != TC_LOSS_POISSON_ID)
+        return TC_ERR_ARG;
+    if (inner_iters < 1 || !(tol >= 0.0) || !(lambda >= 0.0)) return TC_ERR_ARG;
+    if (!p->has_vals && p->nnz > 0) return TC_ERR_ARG;
+    if (steps_out)
+        for (int q = 0; q < R * TC_ORDER; ++q) steps_out[q] = 0;
+    if (p->dtype == TC_F64)
+        return ccd_newton_t<double>(p, loss, R, factors, lambda, inner_iters, tol, steps_out,
+                                    (cudaStream_t)stream);
+    return ccd_newton_t<float>(p, loss, R, factors, lambda, inner_iters, tol, steps_out,
+                               (cudaStream_t)stream);
 }

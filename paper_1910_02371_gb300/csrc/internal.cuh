@@ -132,6 +132,20 @@ tc_status refill_pattern_impl(tc_pattern *p, const int32_t *const *idx, const vo
 // Builds the mode-d -> mode-0 position maps (for caller weight arrays in
 // pattern order) if the current contents do not have them yet.
 tc_status ensure_to0(const tc_pattern *p, cudaStream_t st);
+
+// Newton-step helpers (newton.cu), float and double:
+//   loss_derivs: d1 = phi'(t, m), d2 = phi''(t, m) over n entries (domain
+//                errors recorded in status);
+//   newton_rhs:  rhs = -(g + two_lambda A);
+//   newton_update: A += step, sums[0] += ||step||^2, sums[1] += ||A||^2 (FP64).
+template <typename T>
+void launch_loss_derivs(int64_t n, int loss, const T *t, const T *m, T *d1, T *d2, int *status,
+                        cudaStream_t st);
+template <typename T>
+void launch_newton_rhs(int64_t n, const T *g, const T *A, double two_lambda, T *rhs,
+                       cudaStream_t st);
+template <typename T>
+void launch_newton_update(int64_t n, T *A, const T *step, double *sums, cudaStream_t st);
 void free_pattern(tc_pattern *p);
 
 }  // namespace tc

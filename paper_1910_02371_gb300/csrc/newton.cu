@@ -53,6 +53,43 @@ __global__ void newton_update_kernel(int64_t n, T *__restrict__ A, const T *__re
     block_add(a2, sums + 1);
 }
 
+static unsigned newton_grid(int64_t n) {
+    const int64_t b = (n + 255) / 256;
+    return (unsigned)(b < 1 ? 1 : (b > 4096 ? 4096 : b));
+}
+
+template <typename T>
+void launch_loss_derivs(int64_t n, int loss, const T *t, const T *m, T *d1, T *d2, int *status,
+                        cudaStream_t st) {
+    if (n <= 0) return;
+    loss_derivs_kernel<T><<<newton_grid(n), 256, 0, st>>>(n, loss, t, m, d1, d2, status);
+    count_launch();
+}
+
+template <typename T>
+void launch_newton_rhs(int64_t n, const T *g, const T *A, double two_lambda, T *rhs,
+                       cudaStream_t st) {
+    if (n <= 0) return;
+    newton_rhs_kernel<T><<<newton_grid(n), 256, 0, st>>>(n, g, A, two_lambda, rhs);
+    count_launch();
+}
+
+template <typename T>
+void launch_newton_update(int64_t n, T *A, const T *step, double *sums, cudaStream_t st) {
+    if (n <= 0) return;
+    newton_update_kernel<T><<<newton_grid(n), 256, 0, st>>>(n, A, step, sums);
+    count_launch();
+}
+
+#define TC_NEWTON_LAUNCHERS(T)                                                                  \
+    template void launch_loss_derivs<T>(int64_t, int, const T *, const T *, T *, T *, int *,    \
+                                        cudaStream_t);                                         \
+    template void launch_newton_rhs<T>(int64_t, const T *, const T *, double, T *, cudaStream_t); \
+    template void launch_newton_update<T>(int64_t, T *, const T *, double *, cudaStream_t);
+TC_NEWTON_LAUNCHERS(float)
+TC_NEWTON_LAUNCHERS(double)
+#undef TC_NEWTON_LAUNCHERS
+
 template <typename T>
 static tc_status newton_t(const tc_pattern *p, tc_loss loss, int R, void *const *factors, int mode,
                           double lambda, int inner_iters, double tol, tc_prec prec, int *steps_out,
@@ -71,24 +108,17 @@ static tc_status newton_t(const tc_pattern *p, tc_loss loss, int R, void *const 
     T *g = d2 + (m > 0 ? m : 1), *rhs = g + n, *step = rhs + n;
     T *Ad = (T *)factors[mode];
     const void *const *A = (const void *const *)factors;
-    const unsigned blocks_m = (unsigned)((m + 255) / 256 < 4096 ? (m + 255) / 256 : 4096);
-    const unsigned blocks_n = (unsigned)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
     tc_status rc = TC_OK;
     int taken = 0;
     for (int it = 0; it < inner_iters && rc == TC_OK; ++it) {
         if (m > 0) {
             rc = launch_tttp(p, TC_W_ONE, nullptr, R, A, mv, st);
             if (rc != TC_OK) break;
-            loss_derivs_kernel<T><<<blocks_m, 256, 0, st>>>(m, (int)loss, (const T *)p->md[0].vals,
-                                                           mv, d1, d2, p->status);
-            count_launch();
+            launch_loss_derivs<T>(m, (int)loss, (const T *)p->md[0].vals, mv, d1, d2, p->status, st);
         }
         rc = launch_mttkrp(p, TC_W_ARRAY, d1, R, A, mode, g, 0, st);
         if (rc != TC_OK) break;
-        if (n > 0) {
-            newton_rhs_kernel<T><<<blocks_n, 256, 0, st>>>(n, g, Ad, 2.0 * lambda, rhs);
-            count_launch();
-        }
+        launch_newton_rhs<T>(n, g, Ad, 2.0 * lambda, rhs, st);
         rc = launch_solve_factor(p, TC_W_ARRAY, d2, R, A, mode, rhs, 2.0 * lambda, prec, step,
                                  nullptr, 0, TC_LOSS_LS, nullptr, st);
         if (rc != TC_OK) break;
@@ -96,10 +126,7 @@ static tc_status newton_t(const tc_pattern *p, tc_loss loss, int R, void *const 
             rc = TC_ERR_CUDA;
             break;
         }
-        if (n > 0) {
-            newton_update_kernel<T><<<blocks_n, 256, 0, st>>>(n, Ad, step, sums);
-            count_launch();
-        }
+        launch_newton_update<T>(n, Ad, step, sums, st);
         ++taken;
         double h[2] = {0.0, 0.0};
         if (cudaMemcpyAsync(h, sums, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess ||

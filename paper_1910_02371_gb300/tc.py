@@ -67,6 +67,7 @@ _SIGS = {
     "tc_newton_matvec": [_P, _I, _I, _P, _P, _D, _P, _P],
     "tc_cg_set_hessian": [_P, _I],
     "tc_ccd_sweep": [_P, _I, _P, _D, _P],
+    "tc_ccd_newton_sweep": [_P, _I, _I, _P, _D, _I, _D, _P, _P],
 }
 for _name, _args in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -434,3 +435,17 @@ def ccd_sweep(p: Pattern, factors, lam: float, stream=None):
     _check(_lib.tc_ccd_sweep(p.handle, R, _ptrs(factors), float(lam), _stream(stream)),
            "tc_ccd_sweep")
     return factors
+
+
+def ccd_newton_sweep(p: Pattern, factors, loss: str, lam: float, inner_iters: int = 5,
+                     tol: float = 1e-3, stream=None):
+    """tc_ccd_newton_sweep: one coordinate-minimization sweep for a general loss
+    on the factors in place.  Returns the Newton steps taken per column as a
+    list of R lists (one entry per mode)."""
+    R = factors[0].shape[1]
+    steps = (ctypes.c_int * (R * len(factors)))()
+    _check(_lib.tc_ccd_newton_sweep(p.handle, LOSSES[loss], R, _ptrs(factors), float(lam),
+                                    int(inner_iters), float(tol), steps, _stream(stream)),
+           "tc_ccd_newton_sweep")
+    N = len(factors)
+    return [[int(steps[r * N + d]) for d in range(N)] for r in range(R)]
