@@ -127,6 +127,26 @@ def make_inputs(w, seed_offset=0):
     return seed, idx, planted, start
 
 
+# ------------------------------------------------------------------ replicas
+# Under torchrun every rank runs an independent replica on its own seeded batch
+# of the same shape (no data-path collective); the job's time is the slowest
+# rank's and its throughput counts every rank's nonzeros.
+def job_time_ms(local_ms, world, device=None):
+    """The maximum of the ranks' times (an all-reduce when world > 1)."""
+    if world <= 1:
+        return local_ms
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_value(world, nnz, steps, job_ms):
+    """Whole-job throughput: the nonzeros all ranks processed over the job's time."""
+    return world * nnz * steps / (job_ms / 1e3)
+
+
 def algorithmic_bytes(kind, w, es=4):
     """Compulsory DRAM bytes of one call: every nonzero stream read once, factor
     matrices read once, outputs written once (random-gather reuse not credited)."""
@@ -253,11 +273,8 @@ def run_ours(args):
     launches = tc.launch_count() - launches0
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
-    if world > 1:
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = tt.item()
-    value = world * m * args.steps / (total_ms / 1e3)
+    total_ms = job_time_ms(total_ms, world, dev)
+    value = job_value(world, m, args.steps, total_ms)
     if args.quick:      # timed steps only (for profiler runs)
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": "nnz/s",
@@ -400,14 +417,16 @@ def run_ours(args):
     for _ in range(2):
         e2e_step()
     torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(st)
     for _ in range(args.steps):
         e2e_step()
     e1.record(st)
     e1.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
-    e2e_val = world * m * args.steps / (e2e_ms / 1e3)
+    e2e_ms = job_time_ms(e0.elapsed_time(e1), world, dev)
+    e2e_val = job_value(world, m, args.steps, e2e_ms)
 
     result = {
         "metric": METRIC,
