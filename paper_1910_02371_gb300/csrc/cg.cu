@@ -192,6 +192,9 @@ struct tc_cg {
     double *scal = nullptr;
     cudaStream_t own = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    // the preconditioner's blocks are factored concurrently, one mode per stream
+    cudaStream_t side[TC_ORDER] = {};
+    cudaEvent_t ev_fork = nullptr, ev_join[TC_ORDER] = {};
     // cached graph
     cudaGraphExec_t exec = nullptr;
     const void *key_b[TC_ORDER] = {}, *key_dx[TC_ORDER] = {};
@@ -330,7 +333,38 @@ static void free_cg(tc_cg *cg) {
     if (cg->own) cudaStreamDestroy(cg->own);
     if (cg->ev_in) cudaEventDestroy(cg->ev_in);
     if (cg->ev_out) cudaEventDestroy(cg->ev_out);
+    for (int d = 0; d < TC_ORDER; ++d) {
+        if (cg->side[d]) cudaStreamDestroy(cg->side[d]);
+        if (cg->ev_join[d]) cudaEventDestroy(cg->ev_join[d]);
+    }
+    if (cg->ev_fork) cudaEventDestroy(cg->ev_fork);
     delete cg;
+}
+
+// The preconditioner's three diagonal blocks are independent and each leaves
+// most of the GPU idle (the R <= 32 factorization keeps a few warps per SM),
+// so mode d is factored on side[d], forked from `st` and joined back into it;
+// `work` runs on `st` meanwhile (the gradient, in a Gauss-Newton step).
+template <typename F>
+static tc_status setup_forked(tc_cg *cg, cudaStream_t st, F &&work) {
+    if (!cg->precond) return work();
+    TC_CUDA(cudaEventRecord(cg->ev_fork, st));
+    for (int d = 0; d < TC_ORDER; ++d) TC_CUDA(cudaStreamWaitEvent(cg->side[d], cg->ev_fork, 0));
+    tc_status rc = TC_OK;
+    for (int d = 0; d < TC_ORDER && rc == TC_OK; ++d)
+        rc = launch_solve_factor(cg->p, TC_W_ONE, nullptr, cg->R, (const void *const *)cg->A, d,
+                                 nullptr, 2.0 * cg->lambda, TC_PREC_FP32, nullptr, nullptr, 1,
+                                 cg->loss, cg->pinv[d], cg->side[d]);
+    const tc_status rw = rc == TC_OK ? work() : TC_OK;
+    // join every side stream, whatever happened above
+    for (int d = 0; d < TC_ORDER; ++d) {
+        if (cudaEventRecord(cg->ev_join[d], cg->side[d]) != cudaSuccess ||
+            cudaStreamWaitEvent(st, cg->ev_join[d], 0) != cudaSuccess)
+            rc = rc == TC_OK ? TC_ERR_CUDA : rc;
+    }
+    if (rc != TC_OK) return rc;
+    if (rw != TC_OK) return rw;
+    return cudaGetLastError() == cudaSuccess ? TC_OK : TC_ERR_CUDA;
 }
 
 }  // namespace tc
@@ -375,6 +409,11 @@ tc_status tc_cg_create(const tc_pattern *p, tc_loss loss, int R, const void *con
     ok = ok && cudaStreamCreateWithFlags(&cg->own, cudaStreamNonBlocking) == cudaSuccess;
     ok = ok && cudaEventCreateWithFlags(&cg->ev_in, cudaEventDisableTiming) == cudaSuccess;
     ok = ok && cudaEventCreateWithFlags(&cg->ev_out, cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&cg->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int d = 0; d < TC_ORDER && ok; ++d) {
+        ok = cudaStreamCreateWithFlags(&cg->side[d], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&cg->ev_join[d], cudaEventDisableTiming) == cudaSuccess;
+    }
     if (!ok) {
         free_cg(cg);
         return TC_ERR_OOM;
@@ -405,16 +444,7 @@ tc_status tc_cg_set_hessian(tc_cg *cg, int full_newton) {
 
 tc_status tc_cg_setup(tc_cg *cg, tc_stream_t stream) {
     if (!cg) return TC_ERR_ARG;
-    if (!cg->precond) return TC_OK;
-    for (int d = 0; d < TC_ORDER; ++d) {
-        tc_status rc = launch_solve_factor(cg->p, TC_W_ONE, nullptr, cg->R,
-                                           (const void *const *)cg->A, d, nullptr,
-                                           2.0 * cg->lambda, TC_PREC_FP32, nullptr, nullptr, 1,
-                                           cg->loss,
-                                           cg->pinv[d], (cudaStream_t)stream);
-        if (rc != TC_OK) return rc;
-    }
-    return cudaGetLastError() == cudaSuccess ? TC_OK : TC_ERR_CUDA;
+    return setup_forked(cg, (cudaStream_t)stream, [] { return TC_OK; });
 }
 
 tc_status tc_cg_precond_apply(tc_cg *cg, const void *const *r, void *const *z,
@@ -521,23 +551,26 @@ tc_status tc_ggn_step(tc_cg *cg, int iters, double *loss_out, tc_stream_t stream
     if (!cg || iters < 0) return TC_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     const tc_pattern *p = cg->p;
-    tc_status rc = launch_loss_grad(p, cg->loss, cg->R, (const void *const *)cg->A, cg->lambda,
-                                    loss_out, cg->grad, st);
-    if (rc != TC_OK) return rc;
-    // b = -grad (in place)
-    for (int d = 0; d < TC_ORDER; ++d) {
-        const int64_t n = p->dims[d] * cg->R;
-        int64_t blocks = (n + 255) / 256;
-        if (blocks > 8LL * sms()) blocks = 8LL * sms();
-        if (p->dtype == TC_F64)
-            axpby_kernel<double><<<(unsigned)blocks, 256, 0, st>>>(n, 0.0, (const double *)cg->grad[d],
-                                                                  -1.0, (double *)cg->grad[d]);
-        else
-            axpby_kernel<float><<<(unsigned)blocks, 256, 0, st>>>(n, 0.0f, (const float *)cg->grad[d],
-                                                                 -1.0f, (float *)cg->grad[d]);
-        count_launch();
-    }
-    rc = tc_cg_setup(cg, stream);
+    // the gradient (and b = -grad, in place) on `st` while the preconditioner
+    // blocks are factored on the side streams
+    tc_status rc = setup_forked(cg, st, [&]() -> tc_status {
+        const tc_status rg = launch_loss_grad(p, cg->loss, cg->R, (const void *const *)cg->A,
+                                              cg->lambda, loss_out, cg->grad, st);
+        if (rg != TC_OK) return rg;
+        for (int d = 0; d < TC_ORDER; ++d) {
+            const int64_t n = p->dims[d] * cg->R;
+            int64_t blocks = (n + 255) / 256;
+            if (blocks > 8LL * sms()) blocks = 8LL * sms();
+            if (p->dtype == TC_F64)
+                axpby_kernel<double><<<(unsigned)blocks, 256, 0, st>>>(
+                    n, 0.0, (const double *)cg->grad[d], -1.0, (double *)cg->grad[d]);
+            else
+                axpby_kernel<float><<<(unsigned)blocks, 256, 0, st>>>(
+                    n, 0.0f, (const float *)cg->grad[d], -1.0f, (float *)cg->grad[d]);
+            count_launch();
+        }
+        return TC_OK;
+    });
     if (rc != TC_OK) return rc;
     // the solution goes to the solver's own buffer dx, then A += dx
     void *dxb[TC_ORDER];
