@@ -9,7 +9,7 @@ import numpy as np
 import oracle
 import synth
 
-# Spec tolerances: FP32 kernel outputs within 1e-5 relative (normwise per
+# Tolerances: FP32 kernel outputs within 1e-5 relative (normwise per
 # output array) of the FP64 oracle; FP64 kernels to 1e-12.
 TOL = {"f32": 1e-5, "f64": 1e-12}
 
