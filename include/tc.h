@@ -114,7 +114,7 @@ typedef enum {
 /* A lean pattern keeps no positions (no perm, no mode-d -> mode-0 maps): 12
  * bytes per nonzero per mode for FP32 values instead of 28 / 20.  Calls that
  * need the maps -- TC_W_ARRAY weights in a mode d > 0 (tc_mttkrp,
- * tc_solve_factor), and so tc_newton_als_mode, tc_ccd_sweep and
+ * tc_solve_factor), and so tc_newton_als_mode on modes d > 0, tc_ccd_sweep and
  * tc_ccd_newton_sweep -- return
  * TC_ERR_UNSUPPORTED; tc_pattern_view gives perm = NULL.  The build borrows
  * its sort work space from the arrays of modes not yet built and needs 20
