@@ -418,6 +418,7 @@ tc_status tc_cg_create(const tc_pattern *p, tc_loss loss, int R, const void *con
         free_cg(cg);
         return TC_ERR_OOM;
     }
+    prepare_ggn_matvec_ax();
     *out = cg;
     return TC_OK;
 }

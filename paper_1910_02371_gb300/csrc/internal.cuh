@@ -114,6 +114,10 @@ tc_status launch_ggn_matvec(const tc_pattern *p, tc_loss loss, int R, const void
 // The same on interleaved factor / direction buffers AX[n] (I_n x 2R: per lane
 // chunk of 16 bytes, the factor chunk then the direction chunk); needs the
 // vector path (vec_ok).
+// Queries (and caches) the launch geometry of the interleaved product's
+// kernels; call outside any stream capture, before the first
+// launch_ggn_matvec_ax.
+tc_status prepare_ggn_matvec_ax();
 tc_status launch_ggn_matvec_ax(const tc_pattern *p, tc_loss loss, int R, const void *const *AX,
                                double lambda, void *const *y, double *dot_out, int init,
                                int full_newton, cudaStream_t st);

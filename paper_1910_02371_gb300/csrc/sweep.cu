@@ -13,6 +13,9 @@
 // chunks may share, are added atomically.
 #include "internal.cuh"
 
+#include <mutex>
+#include <unordered_map>
+
 namespace tc {
 
 // OP_NEWTON: the Gauss-Newton product plus the phi' term of the full Hessian
@@ -458,14 +461,35 @@ static int sm_count() {
     return g_sm_count;
 }
 
-static int64_t pick_chunk(int64_t nnz, int NG) {
-    // about 8 steps per warp at least, and enough warps to fill the GPU
-    const int64_t min_chunk = (int64_t)NG * 8;
-    const int64_t target_warps = (int64_t)sm_count() * 64;
-    int64_t c = (nnz + target_warps - 1) / target_warps;
+// Blocks of `kern` (256 threads, no dynamic shared memory) resident per SM,
+// queried once per kernel.
+static int resident_blocks(const void *kern) {
+    static std::mutex mu;
+    static std::unordered_map<const void *, int> cache;
+    std::lock_guard<std::mutex> lock(mu);
+    const auto it = cache.find(kern);
+    if (it != cache.end()) return it->second;
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, 0) != cudaSuccess || occ < 1) {
+        cudaGetLastError();
+        occ = 1;
+    }
+    cache[kern] = occ;
+    return occ;
+}
+
+// Nonzeros per warp: 8 to 64 warp steps, and the grid a whole number of waves
+// of resident blocks, so no last partial wave leaves most SMs idle while a few
+// blocks finish (every warp's chunk costs about the same on these sweeps).
+template <typename K>
+static int64_t pick_chunk(int64_t nnz, int NG, K kern) {
+    const int64_t min_chunk = (int64_t)NG * 8, max_chunk = (int64_t)NG * 64;
+    const int64_t slot_warps = (int64_t)sm_count() * resident_blocks((const void *)kern) * (256 / 32);
+    int64_t waves = (nnz + slot_warps * max_chunk - 1) / (slot_warps * max_chunk);
+    if (waves < 1) waves = 1;
+    int64_t c = (nnz + waves * slot_warps - 1) / (waves * slot_warps);
     c = ((c + NG - 1) / NG) * NG;
     if (c < min_chunk) c = min_chunk;
-    if (c > (int64_t)NG * 64) c = (int64_t)NG * 64;
     return c;
 }
 
@@ -485,7 +509,7 @@ static void launch_sweep_t(const SweepParams<T> &P, int tier, bool vec, cudaStre
     const int threads = 256;
     auto go = [&](auto kern, int NG) {
         SweepParams<T> Q = P;
-        Q.chunk = pick_chunk(P.nnz, NG);
+        Q.chunk = pick_chunk(P.nnz, NG, kern);
         const int64_t warps = (P.nnz + Q.chunk - 1) / Q.chunk;
         const int64_t blocks = (warps * 32 + threads - 1) / threads;
         kern<<<(unsigned)blocks, threads, 0, st>>>(Q);
@@ -564,7 +588,7 @@ static tc_status tttp_t(const tc_pattern *p, tc_weights w, const void *s, int R,
     const int threads = 256;
     auto go = [&](auto kern, int NG) {
         TttpParams<T> Q = P;
-        Q.chunk = pick_chunk(P.nnz, NG);
+        Q.chunk = pick_chunk(P.nnz, NG, kern);
         const int64_t warps = (P.nnz + Q.chunk - 1) / Q.chunk;
         const int64_t blocks = (warps * 32 + threads - 1) / threads;
         kern<<<(unsigned)blocks, threads, 0, st>>>(Q);
@@ -748,7 +772,7 @@ static tc_status ggn_ax_t(const tc_pattern *p, tc_loss loss, int R, const void *
         const int threads = 256;
         auto go = [&](auto kern, int NG) {
             SweepParams<T> Q = P;
-            Q.chunk = pick_chunk(P.nnz, NG);
+            Q.chunk = pick_chunk(P.nnz, NG, kern);
             const int64_t warps = (P.nnz + Q.chunk - 1) / Q.chunk;
             const int64_t nb = (warps * 32 + threads - 1) / threads;
             kern<<<(unsigned)nb, threads, 0, st>>>(Q);
@@ -770,6 +794,16 @@ static tc_status ggn_ax_t(const tc_pattern *p, tc_loss loss, int R, const void *
             }
         }
     }
+    return TC_OK;
+}
+
+tc_status prepare_ggn_matvec_ax() {
+#define TC_WARM(T, RT)                                                              \
+    resident_blocks((const void *)sweep_kernel<T, RT, true, OP_GGN, true>);         \
+    resident_blocks((const void *)sweep_kernel<T, RT, true, OP_NEWTON, true>);
+    TC_WARM(float, 8) TC_WARM(float, 16) TC_WARM(float, 32) TC_WARM(float, 64)
+    TC_WARM(double, 8) TC_WARM(double, 16) TC_WARM(double, 32) TC_WARM(double, 64)
+#undef TC_WARM
     return TC_OK;
 }
 
