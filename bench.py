@@ -49,8 +49,8 @@ METRIC = ("observed entries/s through one full step (pattern rebuild + TTTP + AL
 # keeps multi-pass ncu runs off the full workload) and scaled by the nonzeros
 # to 1e7: three launches per product.
 NCU_TRAFFIC = {
-    "ggn_matvec": {"bytes": 3 * 36.644e6 * 2.5, "file": "paper_1910_02371_gb300/csrc/sweep.cu",
-                   "src": "a83d9f1a4be9febe"},
+    "ggn_matvec": {"bytes": 3 * 36.65e6 * 2.5, "file": "paper_1910_02371_gb300/csrc/sweep.cu",
+                   "src": "1d03ab541fb6d2df"},
 }
 
 
