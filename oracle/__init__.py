@@ -42,7 +42,6 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "liboracle.so")
-_lib = None
 
 LOSSES = {"ls": 0, "poisson_log": 1, "poisson_id": 2}
 
@@ -55,26 +54,55 @@ class OracleError(RuntimeError):
         self.rc = rc
 
 
-def build(force: bool = False) -> str:
-    """Compile oracle.c into liboracle.so with the host gcc."""
+_SO_OMP = os.path.join(_HERE, "liboracle_omp.so")
+_libs = {}
+_parallel = False
+
+
+def _compile(out, extra):
     src = os.path.join(_HERE, "oracle.c")
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < max(
-            os.path.getmtime(src), os.path.getmtime(os.path.join(_HERE, "oracle.h"))):
-        tmp = _SO + f".{os.getpid()}.tmp"
+    hdr = os.path.join(_HERE, "oracle.h")
+    if not os.path.exists(out) or os.path.getmtime(out) < max(os.path.getmtime(src),
+                                                               os.path.getmtime(hdr)):
+        tmp = out + f".{os.getpid()}.tmp"
         subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
-                               "-std=c11", "-o", tmp, src, "-lm"])
-        os.replace(tmp, _SO)
-    return _SO
+                               "-std=c11", *extra, "-o", tmp, src, "-lm"])
+        os.replace(tmp, out)
+    return out
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so (plain, the parity checker) and
+    liboracle_omp.so (the same loops split by OpenMP, the timed CPU baseline)
+    with the host gcc."""
+    if force:
+        for f in (_SO, _SO_OMP):
+            if os.path.exists(f):
+                os.remove(f)
+    _compile(_SO_OMP, ["-fopenmp"])
+    return _compile(_SO, [])
+
+
+def set_parallel(on: bool, threads: int = 0) -> int:
+    """Route every oracle call through the OpenMP build (bit-identical results)
+    or back through the plain one; returns the thread count in use."""
+    global _parallel
+    _parallel = bool(on)
+    L = lib()
+    if _parallel and threads > 0:
+        L.orc_threads(int(threads))
+    return int(L.orc_threads(0))
 
 
 def lib():
-    global _lib
-    if _lib is None:
+    key = "omp" if _parallel else "plain"
+    if key not in _libs:
         build()
-        L = ctypes.CDLL(_SO)
+        L = ctypes.CDLL(_SO_OMP if _parallel else _SO)
         P = ctypes.c_void_p
         i64 = ctypes.c_int64
         for name, args in {
+            "orc_threads": [ctypes.c_int],
             "orc_counting_sort": [i64, P, i64, P, P],
             "orc_tttp": [ctypes.c_int, P, i64, P, P, ctypes.c_int, P, P],
             "orc_mttkrp": [ctypes.c_int, P, i64, P, P, ctypes.c_int, P, ctypes.c_int, P],
@@ -89,8 +117,8 @@ def lib():
             fn = getattr(L, name)
             fn.argtypes = args
             fn.restype = ctypes.c_int
-        _lib = L
-    return _lib
+        _libs[key] = L
+    return _libs[key]
 
 
 # ---------------------------------------------------------------- marshalling

@@ -2,12 +2,35 @@
  * FP64 CPU oracle for sparse CP tensor completion (arXiv:1910.02371).
  * TEST INFRASTRUCTURE ONLY -- see oracle.h.  Compiled with -O2
  * -ffp-contract=off so that every product and sum is rounded as written.
+ *
+ * The same source is compiled twice: without OpenMP (liboracle.so, the parity
+ * checker) and with -fopenmp (liboracle_omp.so, the timed CPU baseline).  The
+ * OpenMP pragmas only split independent loops -- nonzeros for TTTP and the
+ * per-nonzero model terms, rows of the mode-sorted segments for MTTKRP and
+ * Solve Factor -- and every sum keeps its order (each row sums its nonzeros in
+ * input order; the objective's sum over nonzeros stays serial), so both
+ * builds give bit-identical results.
  */
 #include "oracle.h"
 
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Number of threads the OpenMP build uses (1 without OpenMP). */
+int orc_threads(int set)
+{
+#ifdef _OPENMP
+    if (set > 0) omp_set_num_threads(set);
+    return omp_get_max_threads();
+#else
+    (void)set;
+    return 1;
+#endif
+}
 
 static int check_common(int N, const int64_t *dims, int64_t m, const int32_t *const *idx, int R)
 {
@@ -49,6 +72,7 @@ int orc_tttp(int N, const int64_t *dims, int64_t m, const int32_t *const *idx,
     int provided = 0;
     for (int n = 0; n < N; ++n) provided += (A && A[n]) ? 1 : 0;
     if (!provided || (m > 0 && !x)) return ORC_ERR_ARG;
+#pragma omp parallel for schedule(static)
     for (int64_t e = 0; e < m; ++e) {
         double acc = 0.0;
         for (int r = 0; r < R; ++r) {
@@ -71,17 +95,30 @@ int orc_mttkrp(int N, const int64_t *dims, int64_t m, const int32_t *const *idx,
     if (mode < 0 || mode >= N || !out || !A) return ORC_ERR_ARG;
     for (int n = 0; n < N; ++n)
         if (n != mode && !A[n]) return ORC_ERR_ARG;
-    for (int64_t q = 0; q < dims[mode] * R; ++q) out[q] = 0.0;
-    for (int64_t e = 0; e < m; ++e) {
-        double *o = out + (int64_t)idx[mode][e] * R;
-        double se = s ? s[e] : 1.0;
-        for (int r = 0; r < R; ++r) {
-            double p = se;
-            for (int n = 0; n < N; ++n)
-                if (n != mode) p = p * A[n][(int64_t)idx[n][e] * R + r];
-            o[r] = o[r] + p;
+    const int64_t I = dims[mode];
+    int64_t *perm = (int64_t *)malloc(sizeof(int64_t) * (size_t)(m > 0 ? m : 1));
+    int64_t *row_ptr = (int64_t *)malloc(sizeof(int64_t) * (size_t)(I + 1));
+    if (!perm || !row_ptr) { free(perm); free(row_ptr); return ORC_ERR_ARG; }
+    /* the rows' nonzeros in input order (the counting sort is stable), so
+     * each out[i, r] sums its terms in input order */
+    orc_counting_sort(m, m > 0 ? idx[mode] : NULL, I, perm, row_ptr);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < I; ++i) {
+        double *o = out + i * R;
+        for (int r = 0; r < R; ++r) o[r] = 0.0;
+        for (int64_t q = row_ptr[i]; q < row_ptr[i + 1]; ++q) {
+            const int64_t e = perm[q];
+            double se = s ? s[e] : 1.0;
+            for (int r = 0; r < R; ++r) {
+                double p = se;
+                for (int n = 0; n < N; ++n)
+                    if (n != mode) p = p * A[n][(int64_t)idx[n][e] * R + r];
+                o[r] = o[r] + p;
+            }
         }
     }
+    free(perm);
+    free(row_ptr);
     return ORC_OK;
 }
 
@@ -133,51 +170,57 @@ int orc_solve_factor(int N, const int64_t *dims, int64_t m, const int32_t *const
     const int64_t I = dims[mode];
     int64_t *perm = (int64_t *)malloc(sizeof(int64_t) * (size_t)(m > 0 ? m : 1));
     int64_t *row_ptr = (int64_t *)malloc(sizeof(int64_t) * (size_t)(I + 1));
-    double *G = (double *)malloc(sizeof(double) * (size_t)R * R);
-    double *L = (double *)malloc(sizeof(double) * (size_t)R * R);
-    double *h = (double *)malloc(sizeof(double) * (size_t)R);
-    double *a = (double *)malloc(sizeof(double) * (size_t)R);
-    double *d = (double *)malloc(sizeof(double) * (size_t)R);
-    if (!perm || !row_ptr || !G || !L || !h || !a || !d) {
-        free(perm); free(row_ptr); free(G); free(L); free(h); free(a); free(d);
-        return ORC_ERR_ARG;
-    }
+    if (!perm || !row_ptr) { free(perm); free(row_ptr); return ORC_ERR_ARG; }
     orc_counting_sort(m, m > 0 ? idx[mode] : NULL, I, perm, row_ptr);
-    int bad = 0;
-    for (int64_t i = 0; i < I; ++i) {
-        /* G_i = sum_{e in row i} s_e h_e h_e^T, then + lambda I */
-        for (int q = 0; q < R * R; ++q) G[q] = 0.0;
-        for (int64_t q = row_ptr[i]; q < row_ptr[i + 1]; ++q) {
-            int64_t e = perm[q];
-            double se = s ? s[e] : 1.0;
-            for (int r = 0; r < R; ++r) {
-                double p = 1.0;
-                for (int n = 0; n < N; ++n)
-                    if (n != mode) p = p * A[n][(int64_t)idx[n][e] * R + r];
-                h[r] = p;
+    int bad = 0, oom = 0;
+#pragma omp parallel reduction(| : bad, oom)
+    {
+        double *G = (double *)malloc(sizeof(double) * (size_t)R * R);
+        double *L = (double *)malloc(sizeof(double) * (size_t)R * R);
+        double *h = (double *)malloc(sizeof(double) * (size_t)R);
+        double *a = (double *)malloc(sizeof(double) * (size_t)R);
+        double *d = (double *)malloc(sizeof(double) * (size_t)R);
+        const int ok = G && L && h && a && d;
+        if (!ok) oom = 1;
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t i = 0; i < I; ++i) {
+            if (!ok) continue;
+            /* G_i = sum_{e in row i} s_e h_e h_e^T, then + lambda I */
+            for (int q = 0; q < R * R; ++q) G[q] = 0.0;
+            for (int64_t q = row_ptr[i]; q < row_ptr[i + 1]; ++q) {
+                int64_t e = perm[q];
+                double se = s ? s[e] : 1.0;
+                for (int r = 0; r < R; ++r) {
+                    double p = 1.0;
+                    for (int n = 0; n < N; ++n)
+                        if (n != mode) p = p * A[n][(int64_t)idx[n][e] * R + r];
+                    h[r] = p;
+                }
+                for (int r = 0; r < R; ++r)
+                    for (int c = 0; c < R; ++c) G[r * R + c] = G[r * R + c] + se * h[r] * h[c];
             }
-            for (int r = 0; r < R; ++r)
-                for (int c = 0; c < R; ++c) G[r * R + c] = G[r * R + c] + se * h[r] * h[c];
+            for (int r = 0; r < R; ++r) G[r * R + r] = G[r * R + r] + lambda;
+            if (!cholesky(R, G, L)) {
+                bad = 1;
+                if (status) status[i] = 1;
+                continue;
+            }
+            if (status) status[i] = 0;
+            for (int r = 0; r < R; ++r) a[r] = rhs[i * R + r];
+            chol_solve(R, L, a);
+            /* one refinement step: d = rhs - (G + lambda I) a in long double */
+            for (int r = 0; r < R; ++r) {
+                long double v = (long double)rhs[i * R + r];
+                for (int c = 0; c < R; ++c) v -= (long double)G[r * R + c] * (long double)a[c];
+                d[r] = (double)v;
+            }
+            chol_solve(R, L, d);
+            for (int r = 0; r < R; ++r) out[i * R + r] = a[r] + d[r];
         }
-        for (int r = 0; r < R; ++r) G[r * R + r] = G[r * R + r] + lambda;
-        if (!cholesky(R, G, L)) {
-            bad = 1;
-            if (status) status[i] = 1;
-            continue;
-        }
-        if (status) status[i] = 0;
-        for (int r = 0; r < R; ++r) a[r] = rhs[i * R + r];
-        chol_solve(R, L, a);
-        /* one refinement step: d = rhs - (G + lambda I) a in long double */
-        for (int r = 0; r < R; ++r) {
-            long double v = (long double)rhs[i * R + r];
-            for (int c = 0; c < R; ++c) v -= (long double)G[r * R + c] * (long double)a[c];
-            d[r] = (double)v;
-        }
-        chol_solve(R, L, d);
-        for (int r = 0; r < R; ++r) out[i * R + r] = a[r] + d[r];
+        free(G); free(L); free(h); free(a); free(d);
     }
-    free(perm); free(row_ptr); free(G); free(L); free(h); free(a); free(d);
+    free(perm); free(row_ptr);
+    if (oom) return ORC_ERR_ARG;
     return bad ? ORC_ERR_NOT_SPD : ORC_OK;
 }
 
@@ -190,6 +233,8 @@ int orc_loss_terms(int loss, int64_t m, const double *t, const double *model,
 {
     if (m < 0 || (m > 0 && (!t || !model))) return ORC_ERR_ARG;
     if (loss < ORC_LOSS_LS || loss > ORC_LOSS_POISSON_ID) return ORC_ERR_ARG;
+    int dom = 0;
+#pragma omp parallel for schedule(static) reduction(| : dom)
     for (int64_t e = 0; e < m; ++e) {
         double te = t[e], me = model[e], p, g, hh;
         if (loss == ORC_LOSS_LS) {
@@ -203,7 +248,10 @@ int orc_loss_terms(int loss, int64_t m, const double *t, const double *model,
             g = ex - te;
             hh = ex;
         } else {
-            if (!(me > 0.0)) return ORC_ERR_DOMAIN;
+            if (!(me > 0.0)) {
+                dom = 1;
+                continue;
+            }
             p = me - te * log(me);
             g = 1.0 - te / me;
             hh = te / (me * me);
@@ -212,7 +260,7 @@ int orc_loss_terms(int loss, int64_t m, const double *t, const double *model,
         if (d1) d1[e] = g;
         if (d2) d2[e] = hh;
     }
-    return ORC_OK;
+    return dom ? ORC_ERR_DOMAIN : ORC_OK;
 }
 
 static double frob2(int64_t rows, int R, const double *a)
@@ -272,7 +320,9 @@ int orc_ggn_matvec(int N, const int64_t *dims, int64_t m, const int32_t *const *
     if (!model || !d2 || !w) { free(model); free(d2); free(w); return ORC_ERR_ARG; }
     rc = orc_tttp(N, dims, m, idx, NULL, R, A, model);
     if (!rc) rc = orc_loss_terms(loss, m, t, model, NULL, NULL, d2);
-    for (int64_t e = 0; !rc && e < m; ++e) {
+#pragma omp parallel for schedule(static) if (!rc)
+    for (int64_t e = 0; e < m; ++e) {
+        if (rc) continue;
         /* z_e = sum_p sum_r x^(p)_{i_p r} prod_{n != p} a^(n)_{i_n r} */
         double z = 0.0;
         for (int p = 0; p < N; ++p)

@@ -29,6 +29,11 @@ enum { ORC_OK = 0, ORC_ERR_ARG = 1, ORC_ERR_RANGE = 2, ORC_ERR_NOT_SPD = 6,
        ORC_ERR_DOMAIN = 7 };
 enum { ORC_LOSS_LS = 0, ORC_LOSS_POISSON_LOG = 1, ORC_LOSS_POISSON_ID = 2 };
 
+/* Threads of the OpenMP build of this file (liboracle_omp.so): sets the count
+ * if set > 0, returns the count in use; the plain build returns 1.  Both
+ * builds give bit-identical results (see oracle.c). */
+int orc_threads(int set);
+
 /* Counting sort of the nonzeros by key (Sec. 3.4, Solve Factor: the local data
  * is sorted by the mode-n index with a counting sort).  perm[q] = input position
  * of the q-th nonzero in sorted order; equal keys keep input order.

@@ -616,3 +616,40 @@ def test_oracle_index_dtype_does_not_matter():
         y1 = oracle.ggn_matvec(dims, i64, t, A, "ls", 0.1, x)
         y2 = oracle.ggn_matvec(dims, i32, t, A, "ls", 0.1, x)
         assert all(np.array_equal(u, v) for u, v in zip(y1, y2))
+
+
+# ---------------------------------------------------------------- OpenMP build
+def test_openmp_build_is_bit_identical():
+    """The OpenMP build of the oracle (the timed CPU baseline) only splits
+    independent loops; every routine must give bit-identical results to the
+    plain build, which the pins above check against the mathematics."""
+    dims = (37, 29, 23)
+    idx, planted, t = small_problem(dims, 3000, 4, 91, noise=0.05)
+    A = [a * 1.03 for a in planted]
+    rng = np.random.default_rng(5)
+    x = [rng.standard_normal(a.shape) for a in A]
+    s = rng.uniform(0.5, 1.5, len(t))
+
+    def run():
+        out = [oracle.tttp(dims, idx, t, A), oracle.tttp(dims, idx, None, [A[0], None, A[2]])]
+        for d in range(3):
+            out.append(oracle.mttkrp(dims, idx, s, A, d))
+            rhs = oracle.mttkrp(dims, idx, t, A, d)
+            out.append(oracle.solve_factor(dims, idx, s, A, d, rhs, 0.05)[0])
+        for loss in ("ls", "poisson_log"):
+            f, g = oracle.loss_grad(dims, idx, t, A, loss, 0.1)
+            out += [np.array([f])] + g
+            out += oracle.ggn_matvec(dims, idx, t, A, loss, 0.1, x)
+        out += oracle.ggn_step(dims, idx, t, A, "ls", 0.1, 4)
+        return out
+
+    oracle.set_parallel(False)
+    plain = run()
+    try:
+        assert oracle.set_parallel(True, 4) == 4
+        par = run()
+    finally:
+        oracle.set_parallel(False)
+    assert len(plain) == len(par)
+    for a, b in zip(plain, par):
+        assert np.array_equal(a, b)
