@@ -1,28 +1,39 @@
 """Benchmark of the sparse CP-completion hot path on GB300.
 
-One step = one pass of every hot-path kernel over one batch of synthetic
-input, all through the C ABI of libtc:
-  1. rebuild the per-mode sorted pattern of the batch (tc_pattern_refill),
-  2. TTTP of the current model at the observed entries (tc_tttp),
-  3. one ALS sweep: per mode MTTKRP of the tensor, then Solve Factor (Sec. 2.2),
-  4. one generalized Gauss-Newton step: objective and gradient, block-diagonal
+Default workload: order-3 tensor 2^22 x 2^22 x 2^22 with 4e9 distinct uniform
+coordinates (the paper's 1e10-nonzero synthetic problem of Sec. 5 scaled to one
+GPU), values from a planted rank-16 CP model plus N(0, 0.1^2) noise, FP32
+factors, int32 indices, R = 16, lambda = 1e-2, least squares.  The tensor is
+generated on the device (keyed-permutation coordinates) and held in a lean
+pattern built from the consumed input; the build is timed once and reported
+beside the step (the consumed input cannot be sorted twice).
+
+One step = one pass of every hot-path kernel over the tensor, all through the
+C ABI of libtc:
+  1. TTTP of the current model at the observed entries (tc_tttp),
+  2. one ALS sweep: per mode MTTKRP of the tensor, then Solve Factor (Sec. 2.2),
+  3. one generalized Gauss-Newton step: objective and gradient, block-diagonal
      preconditioner, 10 PCG iterations replayed from a CUDA graph, update (Sec. 2.5).
+Workloads small enough to draw on the host (``--workload cp3_10k_m10M_r16``)
+also rebuild the pattern in every step (tc_pattern_refill).
 The headline value is observed entries per second through that step.
 
-Default workload: order-3 tensor 10^4 x 10^4 x 10^4 with 10^7 distinct uniform
-coordinates, values from a planted rank-16 CP model plus N(0, 0.1^2) noise,
-FP32 factors, int32 indices, R = 16, lambda = 1e-2, least squares.
+``e2e`` runs the same step end to end from host buffers: per step the host
+coordinates and values are copied to the device, the pattern is rebuilt, the
+step runs, and the factors and objective are copied back.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 ``--impl reference`` times the FP64 CPU oracle (the only reference this method
-has) on a bounded sample of the same workload on the host cores.
+has), OpenMP build on every host core, on the workload's CPU sample (the same
+input as the ``cpu_baseline`` leg).
 """
 from __future__ import annotations
 
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -37,20 +48,31 @@ sys.path.insert(0, ROOT)
 
 import synth  # noqa: E402
 
-WORKLOAD = "cp3_10k_m10M_r16"
+WORKLOAD = "cp3_4M_m4B_r16"
 CG_ITERS = 10
-METRIC = ("observed entries/s through one full step (pattern rebuild + TTTP + ALS sweep + "
-          "Gauss-Newton step with 10 graph-captured PCG iterations)")
+GEN_CHUNK = 1 << 24
+
+
+def metric_of(w):
+    if w.coords == "feistel":
+        return ("observed entries/s through one step (TTTP + ALS sweep + Gauss-Newton step with "
+                "10 graph-captured PCG iterations) on the lean pattern, built once (build timed "
+                "beside)")
+    return ("observed entries/s through one full step (pattern rebuild + TTTP + ALS sweep + "
+            "Gauss-Newton step with 10 graph-captured PCG iterations)")
+
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant
-# kernel from one ncu capture, keyed by the hash of the source file it was
-# measured on; a stale hash reports null.  The Gauss-Newton sweep was captured
-# at 4e6 nonzeros (36.64 MB read, ~0 written per launch; the capture size rule
-# keeps multi-pass ncu runs off the full workload) and scaled by the nonzeros
-# to 1e7: three launches per product.
+# kernel per workload, from ncu captures, keyed by the hash of the source file
+# it was measured on; a stale hash reports null.  Each entry gives the bytes of
+# one Gauss-Newton product (three launches of the sweep kernel, one per output
+# mode) at the bench's full size, scaled from a smaller capture by the
+# nonzero count (the capture size rule keeps multi-pass ncu runs off the full
+# workload).
 NCU_TRAFFIC = {
-    "ggn_matvec": {"bytes": 3 * 36.65e6 * 2.5, "file": "paper_1910_02371_gb300/csrc/sweep.cu",
-                   "src": "1d03ab541fb6d2df"},
+    ("cp3_10k_m10M_r16", "ggn_matvec"): {"bytes": 3 * 36.65e6 * 2.5,
+                                         "file": "paper_1910_02371_gb300/csrc/sweep.cu",
+                                         "src": "1d03ab541fb6d2df"},
 }
 
 
@@ -118,13 +140,104 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ data
 def make_inputs(w, seed_offset=0):
-    """Coordinates, planted and starting factors (host); values are made on the
-    device by the caller from the planted model."""
+    """Host-drawn coordinates, planted and starting factors; values are made
+    on the device by the caller from the planted model."""
     seed = w.seed + seed_offset
     idx = synth.distinct_coords(w.dims, w.nnz, w.coord_dist, seed, w.zipf_s)
     planted = synth.factor_matrices(w.dims, w.rank, w.factor_dist, seed, dtype=np.float64)
     start = synth.perturb(planted, seed)
     return seed, idx, planted, start
+
+
+def make_device_inputs(w, seed, dev):
+    """The tensor of a "feistel" workload generated on the device chunk by
+    chunk: coordinates of entries 0 .. nnz-1 from synth.feistel_coords
+    (distinct by construction), values = the planted CP model at them
+    (plain torch FP64 ops) plus N(0, noise^2) from a seeded torch generator.
+    Returns (idx, vals, start factors on the host)."""
+    import torch
+    planted = synth.factor_matrices(w.dims, w.rank, w.factor_dist, seed)
+    start = [a.astype(np.float32).astype(np.float64) for a in synth.perturb(planted, seed)]
+    pd = [torch.as_tensor(a, device=dev) for a in planted]
+    del planted
+    keys = synth.feistel_keys(seed)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(seed)
+    idx = [torch.empty(w.nnz, dtype=torch.int32, device=dev) for _ in range(3)]
+    vals = torch.empty(w.nnz, dtype=torch.float32, device=dev)
+    for s in range(0, w.nnz, GEN_CHUNK):
+        n = min(GEN_CHUNK, w.nnz - s)
+        e = torch.arange(s, s + n, dtype=torch.int64, device=dev)
+        c = synth.feistel_coords(e, w.feistel_bits, keys)
+        m = pd[0][c[0]]
+        m *= pd[1][c[1]]
+        m *= pd[2][c[2]]
+        t = m.sum(1)
+        del m
+        t += w.noise * torch.randn(n, dtype=torch.float64, device=dev, generator=gen)
+        vals[s:s + n] = t.to(torch.float32)
+        for d in range(3):
+            idx[d][s:s + n] = c[d].to(torch.int32)
+        del e, c, t
+    del pd
+    torch.cuda.synchronize()
+    return idx, vals, start
+
+
+# ------------------------------------------------------------------ CPU sample
+def cpu_sample(w):
+    """The input both oracle legs time (deterministic): the workload's recipe
+    scaled to at most 2^10 rows per mode with the workload's nonzeros per row
+    and its rank, so that the per-row and per-nonzero work keep their ratio.
+    Returns (dims, idx, t, start factors, description)."""
+    import oracle
+    f = min(1.0, 1024.0 / max(w.dims))
+    dims = tuple(max(1, int(round(I * f))) for I in w.dims)
+    n = int(round(w.nnz * f))
+    if w.coords == "feistel":
+        bits = 10
+        dims = (1 << bits,) * 3
+        n = int(round(w.nnz / w.dims[0] * dims[0]))
+        c = synth.feistel_coords(np.arange(n, dtype=np.int64), bits, synth.feistel_keys(w.seed))
+        idx = [np.ascontiguousarray(x.astype(np.int32)) for x in c]
+    else:
+        idx = synth.distinct_coords(dims, n, w.coord_dist, w.seed, w.zipf_s)
+    planted = synth.factor_matrices(dims, w.rank, w.factor_dist, w.seed)
+    t = synth.observe(oracle.model_entries(dims, idx, planted), w.values, w.seed, w.noise)
+    start = synth.perturb(planted, w.seed)
+    desc = (f"the workload's recipe scaled to {dims[0]}x{dims[1]}x{dims[2]} with its "
+            f"{w.nnz / w.dims[0]:.0f} nonzeros per row: {n} nonzeros, rank {w.rank}; one "
+            f"oracle step (3 counting sorts, TTTP, ALS sweep, GGN step with {CG_ITERS} PCG "
+            f"iterations; the oracle's preconditioner re-solves its rows each iteration)")
+    return dims, idx, t, start, desc
+
+
+def oracle_step(dims, idx, t, A, lam, loss):
+    """The same step on the FP64 oracle: patterns, TTTP, ALS sweep, GGN step."""
+    import oracle
+    for d in range(3):
+        oracle.counting_sort(idx[d], dims[d])
+    oracle.tttp(dims, idx, None, A)
+    B = oracle.als_sweep(dims, idx, t, A, lam)
+    return oracle.ggn_step(dims, idx, t, B, loss, lam, CG_ITERS)
+
+
+def cpu_baseline(w, steps=1):
+    """The OpenMP oracle on every host core, timed on the CPU sample."""
+    import oracle
+    oracle.build()
+    cores = oracle.set_parallel(True, os.cpu_count() or 1)
+    try:
+        dims, idx, t, start, desc = cpu_sample(w)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            oracle_step(dims, idx, t, start, w.lam, w.loss)
+        dt = (time.perf_counter() - t0) / steps
+    finally:
+        oracle.set_parallel(False)
+    return {"value": len(idx[0]) / dt, "unit": "nnz/s", "cores": cores, "kind": "oracle",
+            "sample": f"subsample: {desc}; {dt:.1f} s per step, OpenMP build on {cores} cores "
+                      f"(nproc {os.cpu_count()})"}
 
 
 # ------------------------------------------------------------------ replicas
@@ -185,28 +298,50 @@ def run_ours(args):
     w = synth.WORKLOADS[args.workload]
     if args.nnz:
         w = synth.scaled(w, args.nnz)
-    # independent replicas: each rank its own seeded batch of the same shape
-    seed, idx_h, planted_h, start_h = make_inputs(w, seed_offset=rank)
     m = w.nnz
     f32 = torch.float32
-    idx = [torch.as_tensor(c).to(dev) for c in idx_h]
-    planted = [torch.as_tensor(a, dtype=f32).to(dev) for a in planted_h]
-    # values: planted model at the observed entries (TTTP on a value-less
-    # pattern, mapped back to input order) plus seeded noise
-    p0 = tc.build_pattern(idx, w.dims, None, dtype=f32)
-    x = tc.tttp(p0, planted)
-    perm0 = p0.view(0)[1]
-    model = torch.empty(m, dtype=f32, device=dev)
-    model[perm0] = x
-    t_h = synth.observe(model.double().cpu().numpy(), w.values, seed, w.noise).astype(np.float32)
-    del p0, x, perm0, model
-    t = torch.as_tensor(t_h).to(dev)
-
-    p = tc.build_pattern(idx, w.dims, t, dtype=f32, refillable=True)
+    lean = w.coords == "feistel"
+    seed = w.seed + rank          # independent replicas: each rank its own seeded batch
+    build_ms = None
+    if lean:
+        idx, t, start_h = make_device_inputs(w, seed, dev)
+        idx_h = t_h = None
+        # host copies for the end-to-end leg, taken before the build consumes them
+        idx_pin = t_pin = None
+        if not args.quick and not args.solve_probe:
+            idx_pin = [torch.empty(m, dtype=torch.int32).pin_memory() for _ in range(3)]
+            t_pin = torch.empty(m, dtype=f32).pin_memory()
+            for dst, src in zip(idx_pin, idx):
+                dst.copy_(src)
+            t_pin.copy_(t)
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        p = tc.build_pattern(idx, w.dims, t, dtype=f32, lean=True, consume_input=True)
+        e1.record()
+        e1.synchronize()
+        build_ms = e0.elapsed_time(e1)
+        xbuf = t                  # the consumed values buffer holds TTTP's output
+    else:
+        seed, idx_h, planted_h, start_h = make_inputs(w, seed_offset=rank)
+        idx = [torch.as_tensor(c).to(dev) for c in idx_h]
+        planted = [torch.as_tensor(a, dtype=f32).to(dev) for a in planted_h]
+        # values: planted model at the observed entries (TTTP on a value-less
+        # pattern, mapped back to input order) plus seeded noise
+        p0 = tc.build_pattern(idx, w.dims, None, dtype=f32)
+        x = tc.tttp(p0, planted)
+        perm0 = p0.view(0)[1]
+        model = torch.empty(m, dtype=f32, device=dev)
+        model[perm0] = x
+        t_h = synth.observe(model.double().cpu().numpy(), w.values, seed, w.noise).astype(np.float32)
+        del p0, x, perm0, model
+        t = torch.as_tensor(t_h).to(dev)
+        p = tc.build_pattern(idx, w.dims, t, dtype=f32, refillable=True)
+        xbuf = torch.empty(m, dtype=f32, device=dev)
     A0 = [torch.as_tensor(a, dtype=f32).to(dev) for a in start_h]
     A = [a.clone() for a in A0]
     rhs = [torch.empty_like(a) for a in A0]
-    xbuf = torch.empty(m, dtype=f32, device=dev)
     loss = torch.zeros(1, dtype=torch.float64, device=dev)
     if args.solve_probe is not None:
         # Solve Factor on one mode (right-hand side: the MTTKRP of the values),
@@ -236,14 +371,16 @@ def run_ours(args):
             dist.destroy_process_group()
         return
 
-    cg = tc.CG(p, A, w.loss, w.lam)
+    state = {"p": p, "cg": tc.CG(p, A, w.loss, w.lam)}
 
     def step():
-        tc.refill_pattern(p, idx, t)
+        pp, cg = state["p"], state["cg"]
+        if not lean:
+            tc.refill_pattern(pp, idx, t)
         for a, a0 in zip(A, A0):
             a.copy_(a0)
-        tc.tttp(p, A, weights=None, out=xbuf)
-        drivers.als_sweep(p, A, w.lam, rhs=rhs, prec=args.prec)
+        tc.tttp(pp, A, weights=None, out=xbuf)
+        drivers.als_sweep(pp, A, w.lam, rhs=rhs, prec=args.prec)
         cg.ggn_step(CG_ITERS, loss_out=loss)
 
     for _ in range(args.warmup):
@@ -275,18 +412,26 @@ def run_ours(args):
     total_ms = sum(step_ms)
     total_ms = job_time_ms(total_ms, world, dev)
     value = job_value(world, m, args.steps, total_ms)
+    if tc.last_error(p) != tc.OK:
+        raise RuntimeError("device error in the timed steps")
     if args.quick:      # timed steps only (for profiler runs)
         if rank == 0:
-            print(json.dumps({"metric": METRIC, "value": value, "unit": "nnz/s",
+            print(json.dumps({"metric": metric_of(w), "value": value, "unit": "nnz/s",
                               "ms_per_step": total_ms / args.steps, "gpu_launches": int(launches),
+                              "build_ms": build_ms,
                               "config": {"workload": w.name, "nnz": w.nnz}}), flush=True)
         if world > 1:
             dist.destroy_process_group()
         return
 
     # ---- per-kernel breakdown (same inputs, events around each call)
+    big = m > 500_000_000
+
     def timed(fn, reps=5):
-        fn()
+        if big:
+            reps = 1
+        else:
+            fn()
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(st)
@@ -296,16 +441,17 @@ def run_ours(args):
         b.synchronize()
         return a.elapsed_time(b) / reps
 
+    cg = state["cg"]
     for a, a0 in zip(A, A0):
         a.copy_(a0)
     xv = [torch.randn_like(a) for a in A]
     yv = [torch.empty_like(a) for a in A]
     gb = [torch.empty_like(a) for a in A]
     dxv = [torch.empty_like(a) for a in A]
-    kern = {
-        "pattern_rebuild": timed(lambda: tc.refill_pattern(p, idx, t)),
-        "tttp": timed(lambda: tc.tttp(p, A, weights="values", out=xbuf)),
-    }
+    kern = {}
+    if not lean:
+        kern["pattern_rebuild"] = timed(lambda: tc.refill_pattern(p, idx, t))
+    kern["tttp"] = timed(lambda: tc.tttp(p, A, weights="values", out=xbuf))
     for d in range(3):
         kern[f"mttkrp_mode{d}"] = timed(lambda d=d: tc.mttkrp(p, A, d, out=rhs[d]))
     for d in range(3):
@@ -320,6 +466,7 @@ def run_ours(args):
     B = [a.clone() for a in A0]
     kern["als_sweep"] = timed(lambda: drivers.als_sweep(p, B, w.lam, rhs=rhs, prec=args.prec))
     kern["ggn_step"] = timed(lambda: cg.ggn_step(CG_ITERS, loss_out=loss), reps=3)
+    del B
     torch.cuda.synchronize()
     if tc.last_error(p) not in (tc.OK,):
         raise RuntimeError("device error in breakdown")
@@ -350,15 +497,16 @@ def run_ours(args):
         if tc.last_error(p) not in (tc.OK,):
             raise RuntimeError("device error in the precision forms")
 
-    # ---- roofline of the dominant kernel (Gauss-Newton matvec: 11 per step)
+    # ---- roofline of the dominant kernel
     share = {
         "ggn_matvec": CG_ITERS * kern["ggn_matvec_pcg"],
         "solve_factor": sum(kern[f"solve_factor_mode{d}"] for d in range(3)) + kern["precond_setup"],
         "mttkrp": sum(kern[f"mttkrp_mode{d}"] for d in range(3)),
         "tttp": kern["tttp"],
-        "pattern_rebuild": kern["pattern_rebuild"],
         "loss_grad": kern["loss_grad"],
     }
+    if not lean:
+        share["pattern_rebuild"] = kern["pattern_rebuild"]
     dominant = max(share, key=share.get)
     peaks = {}
     try:
@@ -382,7 +530,7 @@ def run_ours(args):
         "solve_factor": roof("solve_factor", sum(kern[f"solve_factor_mode{d}"] for d in range(3)) / 3),
     }
     main_kind = dominant if dominant in roofs else "ggn_matvec"
-    traffic = NCU_TRAFFIC.get(main_kind)
+    traffic = NCU_TRAFFIC.get((w.name, main_kind))
     roofline = dict(roofs[main_kind])
     roofline["kernel"] = main_kind
     if main_kind == "ggn_matvec":
@@ -394,8 +542,9 @@ def run_ours(args):
                            else None)
 
     # ---- end to end through the C ABI with host buffers
-    idx_pin = [torch.as_tensor(c).pin_memory() for c in idx_h]
-    t_pin = torch.as_tensor(t_h).pin_memory()
+    if not lean:
+        idx_pin = [torch.as_tensor(c).pin_memory() for c in idx_h]
+        t_pin = torch.as_tensor(t_h).pin_memory()
     A0_pin = [a.cpu().pin_memory() for a in A0]
     out_pin = [torch.empty_like(a, device="cpu").pin_memory() for a in A0]
     loss_pin = torch.empty(1, dtype=torch.float64).pin_memory()
@@ -404,32 +553,43 @@ def run_ours(args):
     d2h = sum(a.numel() * 4 for a in out_pin) + 8
 
     def e2e_step():
+        if lean:
+            # the lean pattern cannot be refilled: free it (and its solver),
+            # copy the input, build again from the consumed input
+            state["cg"] = None
+            state["p"] = None
         for dst, src in zip(idx, idx_pin):
             dst.copy_(src, non_blocking=True)
         t.copy_(t_pin, non_blocking=True)
         for dst, src in zip(A0, A0_pin):
             dst.copy_(src, non_blocking=True)
+        if lean:
+            state["p"] = tc.build_pattern(idx, w.dims, t, dtype=f32, lean=True, consume_input=True)
+            state["cg"] = tc.CG(state["p"], A, w.loss, w.lam)
         step()
         for dst, src in zip(out_pin, A):
             dst.copy_(src, non_blocking=True)
         loss_pin.copy_(loss, non_blocking=True)
 
-    for _ in range(2):
+    del cg, p, xv, yv, gb, dxv
+    torch.cuda.empty_cache()
+    e2e_steps = min(args.steps, 3) if lean else args.steps
+    for _ in range(1 if lean else 2):
         e2e_step()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(st)
-    for _ in range(args.steps):
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
         e2e_step()
-    e1.record(st)
-    e1.synchronize()
-    e2e_ms = job_time_ms(e0.elapsed_time(e1), world, dev)
-    e2e_val = job_value(world, m, args.steps, e2e_ms)
+    torch.cuda.synchronize()
+    e2e_ms = job_time_ms((time.perf_counter() - t0) * 1e3, world, dev)
+    e2e_val = job_value(world, m, e2e_steps, e2e_ms)
+    if tc.last_error(state["p"]) != tc.OK:
+        raise RuntimeError("device error in the end-to-end steps")
 
     result = {
-        "metric": METRIC,
+        "metric": metric_of(w),
         "value": value,
         "unit": "nnz/s",
         "n_gpus": world,
@@ -440,12 +600,16 @@ def run_ours(args):
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f32",
-        "data": "synthetic (seeded Philox): coordinates, planted CP factors, noise",
+        "data": ("synthetic (seeded keyed-permutation coordinates, planted CP factors, noise), "
+                 "generated on the device" if lean else
+                 "synthetic (seeded Philox): coordinates, planted CP factors, noise"),
         "config": {
             "workload": w.name, "dims": list(w.dims), "nnz": w.nnz, "rank": w.rank,
             "lambda": w.lam, "loss": w.loss, "cg_iters": CG_ITERS,
+            "pattern": "lean, built once from the consumed input" if lean else
+                       "full, rebuilt in every step",
             "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-            "l2": "inputs larger than L2 (per-step nonzero streams ~%.0f MB)" % (m * 32 / 1e6),
+            "l2": "inputs larger than L2 (per-step nonzero streams ~%.0f MB)" % (m * 36 / 1e6),
         },
         "wall_s_timed": wall,
         "kernels_ms": kern,
@@ -456,17 +620,27 @@ def run_ours(args):
         "roofline": roofline,
         "rooflines": roofs,
         "e2e": {"value": e2e_val, "unit": "nnz/s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms / args.steps},
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms / e2e_steps,
+                "steps": e2e_steps,
+                "includes": ("host-to-device copy of the coordinates, values and starting "
+                             "factors, pattern build, the step, copy of the factors and "
+                             "objective back (host clock)" if lean else
+                             "host-to-device copy of the coordinates, values and starting "
+                             "factors, the step (with its rebuild), copy of the factors and "
+                             "objective back (CUDA events)")},
         "gpu_launches": int(launches),
         "clocks": clocks.summary(),
     }
+    if build_ms is not None:
+        result["build_ms"] = build_ms
+        result["build_nnz_per_s"] = m / (build_ms / 1e3)
     if args.prec != "fp32":
         result["config"]["solve_factor_form"] = args.prec
     if als_forms is not None:
         result["als_sweep_forms"] = als_forms
+    del state
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        result["cpu_baseline"] = cpu_baseline(w, idx_h, t_h.astype(np.float64), start_h,
-                                              target_s=args.cpu_seconds)
+        result["cpu_baseline"] = cpu_baseline(w)
     if world > 1:
         dist.destroy_process_group()
     if rank == 0:
@@ -474,50 +648,6 @@ def run_ours(args):
 
 
 # ------------------------------------------------------------------ oracle arm
-def oracle_step(dims, idx, t, A, lam, loss):
-    """The same step on the FP64 oracle: patterns, TTTP, ALS sweep, GGN step."""
-    import oracle
-    for d in range(3):
-        oracle.counting_sort(idx[d], dims[d])
-    oracle.tttp(dims, idx, None, A)
-    B = oracle.als_sweep(dims, idx, t, A, lam)
-    return oracle.ggn_step(dims, idx, t, B, loss, lam, CG_ITERS)
-
-
-def sample_sizes(w, target_s, steps=1):
-    """Prefix sample size whose oracle step takes about target_s seconds: the
-    step time is fitted as a + b n from two small samples (the per-row solves
-    give a fixed part)."""
-    import oracle  # noqa: F401
-    A = synth.init_factors(w.dims, w.rank, w.seed)
-    rng = np.random.default_rng(0)
-    sizes = (20_000, 80_000)
-    idx = synth.distinct_coords(w.dims, sizes[-1], w.coord_dist, w.seed)
-    times = []
-    for n in sizes:
-        t0 = time.perf_counter()
-        oracle_step(w.dims, [c[:n] for c in idx], rng.standard_normal(n), A, w.lam, w.loss)
-        times.append(time.perf_counter() - t0)
-    b = max((times[1] - times[0]) / (sizes[1] - sizes[0]), 1e-9)
-    a = max(times[0] - b * sizes[0], 0.0)
-    n = int((target_s / steps - a) / b)
-    return max(sizes[0], min(w.nnz, n))
-
-
-def cpu_baseline(w, idx, t, A, target_s=15.0):
-    import oracle
-    oracle.build()
-    n = sample_sizes(w, target_s)
-    sub = [c[:n] for c in idx]
-    t0 = time.perf_counter()
-    oracle_step(w.dims, sub, t[:n], A, w.lam, w.loss)
-    dt = time.perf_counter() - t0
-    return {"value": n / dt, "unit": "nnz/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {n} of {w.nnz} coordinates (draw order), full dims and rank, "
-                      f"one oracle step (3 counting sorts, TTTP, ALS sweep, GGN step with "
-                      f"{CG_ITERS} PCG iterations) in {dt:.1f} s"}
-
-
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -525,27 +655,26 @@ def run_reference(args):
     import oracle
     oracle.build()
     w = synth.WORKLOADS[args.workload]
-    budget = 150.0
-    n = sample_sizes(w, budget / max(1, args.steps + args.warmup))
-    seed, idx, planted, start = make_inputs(synth.scaled(w, n))
-    t = synth.observe(oracle.model_entries(w.dims, idx, planted), w.values, seed, w.noise)
+    cores = oracle.set_parallel(True, os.cpu_count() or 1)
+    dims, idx, t, start, desc = cpu_sample(w)
+    n = len(idx[0])
     for _ in range(args.warmup):
-        oracle_step(w.dims, idx, t, start, w.lam, w.loss)
+        oracle_step(dims, idx, t, start, w.lam, w.loss)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle_step(w.dims, idx, t, start, w.lam, w.loss)
+        oracle_step(dims, idx, t, start, w.lam, w.loss)
     dt = time.perf_counter() - t0
     value = n * args.steps / dt
-    sample = (f"{n} coordinates of workload {w.name} (full dims and rank) per step; FP64 "
-              f"oracle, single thread")
+    sample = f"subsample: {desc}; FP64 oracle, OpenMP build on {cores} cores (nproc {os.cpu_count()})"
     print(json.dumps({
-        "impl": "reference", "metric": METRIC, "value": value, "unit": "nnz/s", "n_gpus": 0,
+        "impl": "reference", "metric": metric_of(w), "value": value, "unit": "nnz/s", "n_gpus": 0,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic (seeded Philox)",
+        "data": "synthetic (seeded)",
         "config": {"workload": w.name, "dims": list(w.dims), "nnz": w.nnz, "rank": w.rank,
-                   "lambda": w.lam, "loss": w.loss, "cg_iters": CG_ITERS},
-        "cpu_baseline": {"value": value, "unit": "nnz/s", "cores": 1, "kind": "oracle",
+                   "lambda": w.lam, "loss": w.loss, "cg_iters": CG_ITERS,
+                   "sample_dims": list(dims), "sample_nnz": n},
+        "cpu_baseline": {"value": value, "unit": "nnz/s", "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "nnz/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -554,11 +683,10 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=WORKLOAD)
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true",
                     help="setup, warm-up and the timed steps only (for profiler runs)")

@@ -72,6 +72,12 @@ class Workload:
     noise: float = 0.0
     zipf_s: float = 1.1
     seed: int = 1910023710
+    coords: str = "draw"  # "draw": distinct_coords on the host; "feistel": feistel_coords
+
+    @property
+    def feistel_bits(self) -> int:
+        """Bits per mode of a "feistel" workload (all dims 2^bits)."""
+        return int(self.dims[0]).bit_length() - 1
 
 
 WORKLOADS = {
@@ -86,7 +92,8 @@ WORKLOADS = {
                  0.05, "ls", ("zipf", "zipf", "uniform"), "uniform_c", "round15",
                  seed=1910023714),
         Workload("cp3_4M_m4B_r16", (1 << 22,) * 3, 4_000_000_000, 16, "f32", 1e-2, "ls",
-                 ("uniform",) * 3, "normal", "noise", noise=0.1, seed=1910023715),
+                 ("uniform",) * 3, "normal", "noise", noise=0.1, seed=1910023715,
+                 coords="feistel"),
     ]
 }
 
