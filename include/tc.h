@@ -45,6 +45,19 @@
  *
  * Threading.  Calls on different patterns are independent.  Calls on one
  * pattern from several host threads must be serialized by the caller.
+ *
+ * Work space.  Calls that need device memory beyond their outputs (Solve
+ * Factor's Gram batch, cut-row slots, refinement residuals and right-hand-side
+ * copy; the work arrays of tc_newton_als_mode, tc_ccd_sweep and
+ * tc_ccd_newton_sweep) take it from buffers the pattern keeps: Solve Factor
+ * one set per mode, the others one set each.  A buffer is allocated the first
+ * time a size is needed and kept until tc_pattern_destroy, so repeated calls
+ * of the same shape allocate nothing (and may then be captured in a CUDA
+ * graph); a call that needs a larger buffer synchronizes the device, frees the
+ * old one and allocates anew.  Because the buffers are shared, two calls on
+ * one pattern that use the same mode's Solve Factor buffers (or both the
+ * Newton or coordinate-descent buffers) must be ordered on the device -- one
+ * stream, or events; calls on different modes may overlap.
  */
 #ifndef TC_H
 #define TC_H
@@ -104,7 +117,11 @@ typedef enum {
      * refinement step corrects the factorization's rounding like the Gram's
      * (its convergence factor is kappa_i times the larger unit roundoff), and
      * FP32 runs far faster than FP64 on this GPU.  Ignored without refinement. */
-    TC_PREC_CHOL32 = 0x100
+    TC_PREC_CHOL32 = 0x100,
+    /* OR-ed into a *_REFINE form: a second refinement step (the residual with
+     * the corrected a_i, then a second correction), which shrinks the error by
+     * the same factor again.  Ignored without refinement. */
+    TC_PREC_REFINE2 = 0x200
 } tc_prec;
 
 /* tc_build_pattern flags */
@@ -233,7 +250,9 @@ tc_status tc_solve_factor(const tc_pattern *p, tc_weights w, const void *s, int 
  *                warps (0: automatic).
  * Settings are process-wide, per dtype and rank tier (the tier of R: 1..8,
  * 9..16, 17..32, 33..64; R = 0 sets every tier).  t == NULL restores the
- * automatic choice.  Not synchronized with calls in flight on other threads. */
+ * automatic choice.  Reads and writes of the setting are locked, and each
+ * Solve Factor call copies the setting once when it starts, so a change made
+ * on another host thread applies to later calls only. */
 typedef struct {
     int64_t chunk_nnz;
     int64_t batch_bytes;
@@ -249,10 +268,12 @@ tc_status tc_get_solve_tuning(tc_dtype dtype, int R, tc_solve_tuning *t);
  * the rank tier of R -- chunk_nnz in {automatic, 256, 1024, 4096, 16384} times
  * chol_rows_per_warp in {8, 16, 32} (R <= 16) or {4, 8, 16} (R <= 32) -- once
  * untimed and once timed with CUDA events on `stream`, and installs the
- * fastest for the pattern's dtype (batch_bytes is kept).  `out` is
- * overwritten with a solution; the stream is synchronized.  best, ms_out (may
- * be NULL) receive the chosen tuning and its time in milliseconds.  On an
- * error the previous tuning is restored. */
+ * fastest for the pattern's dtype (batch_bytes is kept).  Each candidate is
+ * handed to the timed calls directly: the process-wide setting that other
+ * threads' calls read changes only once, to the winner, and not at all on an
+ * error.  `out` is overwritten with a solution; the stream is synchronized.
+ * best, ms_out (may be NULL) receive the chosen tuning and its time in
+ * milliseconds. */
 tc_status tc_autotune_solve(const tc_pattern *p, tc_weights w, const void *s, int R,
                             const void *const *factors, int mode, const void *rhs,
                             double lambda, tc_prec prec, void *out, tc_solve_tuning *best,
@@ -384,6 +405,19 @@ tc_status tc_cg_matvec(tc_cg *cg, const void *const *x, void *const *y, tc_strea
  * `iters` PCG iterations on H dx = -grad, then A^(n) += dx^(n) in place.
  * loss_out (device double, may be NULL) receives f before the step. */
 tc_status tc_ggn_step(tc_cg *cg, int iters, double *loss_out, tc_stream_t stream);
+
+/* The vector steps of PCG (Sec. 2.5) for drivers that run the iteration
+ * themselves, e.g. over row blocks held by several processes, where the inner
+ * products are summed across processes between the steps.
+ *   tc_axpby: y = alpha x + beta y over n elements of dtype (device x, y; y
+ *             may alias x).
+ *   tc_dot:   *out = sum_i x_i y_i (accumulate = 0) or *out += it (1), summed
+ *             in FP64 (device double out; the order of the partial sums is
+ *             not fixed). */
+tc_status tc_axpby(tc_dtype dtype, int64_t n, double alpha, const void *x, double beta, void *y,
+                   tc_stream_t stream);
+tc_status tc_dot(tc_dtype dtype, int64_t n, const void *x, const void *y, double *out,
+                 int accumulate, tc_stream_t stream);
 
 /* ------------------------------------------------------------------ allocation-free sort */
 

@@ -180,7 +180,7 @@ tc_status tc_solve_factor(const tc_pattern *p, tc_weights w, const void *s, int 
                           tc_prec prec, void *out, int8_t *row_status, tc_stream_t stream) {
     if (!p || !rank_ok(R) || !out || !rhs || mode < 0 || mode >= p->order) return TC_ERR_ARG;
     if (!factors_ok(factors, mode) || check_weights(p, w, s) != TC_OK) return TC_ERR_ARG;
-    const int form = prec & ~TC_PREC_CHOL32;
+    const int form = prec & ~(TC_PREC_CHOL32 | TC_PREC_REFINE2);
     if (form != TC_PREC_FP32 && form != TC_PREC_TF32_REFINE && form != TC_PREC_BF16_REFINE &&
         form != TC_PREC_FP32_REFINE)
         return TC_ERR_ARG;

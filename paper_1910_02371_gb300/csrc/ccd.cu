@@ -56,8 +56,10 @@ static tc_status ccd_t(const tc_pattern *p, int R, void *const *factors, double 
     const int64_t I0 = p->dims[0], I1 = p->dims[1], I2 = p->dims[2];
     const int64_t Imax = I0 > I1 ? (I0 > I2 ? I0 : I2) : (I1 > I2 ? I1 : I2);
     const int64_t mm = m > 0 ? m : 1;
-    T *buf = nullptr;
-    TC_CUDA(cudaMallocAsync((void **)&buf, sizeof(T) * (size_t)(2 * mm + I0 + I1 + I2 + Imax), st));
+    // residual, rank-1 TTTP (nnz each); columns; right-hand side: the
+    // pattern's work space (allocated once per size)
+    T *buf = (T *)work_buffer(p, WS_CCD, sizeof(T) * (size_t)(2 * mm + I0 + I1 + I2 + Imax));
+    if (!buf) return TC_ERR_OOM;
     T *rho = buf, *x = rho + mm, *c0 = x + mm, *c1 = c0 + I0, *c2 = c1 + I1, *num = c2 + I2;
     T *col[TC_ORDER] = {c0, c1, c2};
     const void *cols[TC_ORDER] = {c0, c1, c2};
@@ -101,7 +103,6 @@ static tc_status ccd_t(const tc_pattern *p, int R, void *const *factors, double 
         }
     }
     if (rc == TC_OK && cudaGetLastError() != cudaSuccess) rc = TC_ERR_CUDA;
-    cudaFreeAsync(buf, st);
     return rc;
 }
 
@@ -123,15 +124,11 @@ static tc_status ccd_newton_t(const tc_pattern *p, tc_loss loss, int R, void *co
     const int64_t I[TC_ORDER] = {p->dims[0], p->dims[1], p->dims[2]};
     const int64_t Imax = I[0] > I[1] ? (I[0] > I[2] ? I[0] : I[2]) : (I[1] > I[2] ? I[1] : I[2]);
     const int64_t mm = m > 0 ? m : 1;
-    T *buf = nullptr;
-    double *sums = nullptr;
-    // model, phi', phi'', rank-1 TTTP (nnz each); columns; g, rhs, delta (Imax each)
-    TC_CUDA(cudaMallocAsync((void **)&buf,
-                            sizeof(T) * (size_t)(4 * mm + I[0] + I[1] + I[2] + 3 * Imax), st));
-    if (cudaMallocAsync((void **)&sums, 2 * sizeof(double), st) != cudaSuccess) {
-        cudaFreeAsync(buf, st);
-        return TC_ERR_OOM;
-    }
+    // model, phi', phi'', rank-1 TTTP (nnz each); columns; g, rhs, delta (Imax
+    // each): the pattern's work space (allocated once per size)
+    T *buf = (T *)work_buffer(p, WS_CCD, sizeof(T) * (size_t)(4 * mm + I[0] + I[1] + I[2] + 3 * Imax));
+    double *sums = (double *)work_buffer(p, WS_CCD_SUMS, 2 * sizeof(double));
+    if (!buf || !sums) return TC_ERR_OOM;
     T *mv = buf, *d1 = mv + mm, *d2 = d1 + mm, *x = d2 + mm, *c0 = x + mm, *c1 = c0 + I[0],
       *c2 = c1 + I[1], *g = c2 + I[2], *rhs = g + Imax, *delta = rhs + Imax;
     T *col[TC_ORDER] = {c0, c1, c2};
@@ -184,8 +181,6 @@ static tc_status ccd_newton_t(const tc_pattern *p, tc_loss loss, int R, void *co
         }
     }
     if (rc == TC_OK && cudaGetLastError() != cudaSuccess) rc = TC_ERR_CUDA;
-    cudaFreeAsync(sums, st);
-    cudaFreeAsync(buf, st);
     return rc;
 }
 

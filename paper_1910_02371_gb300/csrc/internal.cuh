@@ -31,6 +31,29 @@ struct PatternScratch {
     void *valtmp = nullptr;
 };
 
+// Work space of the calls that need more device memory than their outputs
+// (Solve Factor's Gram batch, cut-row slots, refinement residuals and right-hand
+// side copy, per mode; the general-loss Newton and coordinate-descent
+// buffers).  The pattern keeps
+// each buffer and grows it on demand (tc::work_buffer), so a call at a size
+// the pattern has served before allocates nothing.
+enum WorkSlot {
+    WS_SOLVE_GRAM = 0,                  // + mode
+    WS_SOLVE_CUT = WS_SOLVE_GRAM + 3,   // + mode
+    WS_SOLVE_RES = WS_SOLVE_CUT + 3,    // + mode
+    WS_SOLVE_RHS = WS_SOLVE_RES + 3,    // + mode
+    WS_NEWTON = WS_SOLVE_RHS + 3,
+    WS_NEWTON_SUMS,
+    WS_CCD,
+    WS_CCD_SUMS,
+    WS_COUNT
+};
+
+struct WorkBuf {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+};
+
 struct tc_pattern {
     unsigned flags = 0;
     int order = 0;
@@ -44,10 +67,8 @@ struct tc_pattern {
     int64_t *counts = nullptr;    // device: nonempty rows per mode
     int to0_valid = 0;            // md[d].to0 built (on first use) for the current contents
     PatternScratch work;
-    double *dscratch = nullptr;   // device doubles for reductions (kScratchDoubles)
+    WorkBuf ws[WS_COUNT];
 };
-
-constexpr int kScratchDoubles = 64;
 
 namespace tc {
 
@@ -124,10 +145,12 @@ tc_status launch_ggn_matvec_ax(const tc_pattern *p, tc_loss loss, int R, const v
 // Gram + FP64 Cholesky per row.  If pinv_out != null the inverse of each row
 // system, (G_i + lambda I)^-1, is formed in FP64 from the factor and stored
 // (pattern dtype, I_d x R x R) instead of solving.
+// tun: the tuning to use (nullptr: the process-wide one, solve_tuning).
 tc_status launch_solve_factor(const tc_pattern *p, tc_weights w, const void *s, int R,
                               const void *const *A, int mode, const void *rhs, double lambda,
                               tc_prec prec, void *out, int8_t *row_status, int use_loss_d2,
-                              tc_loss loss, void *pinv_out, cudaStream_t st);
+                              tc_loss loss, void *pinv_out, cudaStream_t st,
+                              const tc_solve_tuning *tun = nullptr);
 tc_status build_pattern_impl(int order, const int64_t *dims, int64_t nnz,
                              const int32_t *const *idx, const void *vals, tc_dtype dtype,
                              unsigned flags, cudaStream_t st, tc_pattern **out);
@@ -151,6 +174,17 @@ void launch_newton_rhs(int64_t n, const T *g, const T *A, double two_lambda, T *
 template <typename T>
 void launch_newton_update(int64_t n, T *A, const T *step, double *sums, cudaStream_t st);
 void free_pattern(tc_pattern *p);
+
+// A device buffer of at least `bytes` bytes held by the pattern in slot `id`.
+// A slot that is too small is replaced (after synchronizing the device, since
+// work in flight may still use it); returns nullptr if the allocation fails.
+// Calls on one pattern that use the same slot must be ordered (one stream, or
+// events): the slot is shared.
+void *work_buffer(const tc_pattern *p, int id, size_t bytes);
+
+// The Solve Factor tuning in force for (dtype, rank tier): a copy of the
+// process-wide setting, read under a lock.
+tc_solve_tuning solve_tuning(tc_dtype dtype, int R);
 
 }  // namespace tc
 

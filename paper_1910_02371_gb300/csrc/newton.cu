@@ -95,15 +95,12 @@ static tc_status newton_t(const tc_pattern *p, tc_loss loss, int R, void *const 
                           double lambda, int inner_iters, double tol, tc_prec prec, int *steps_out,
                           cudaStream_t st) {
     const int64_t m = p->nnz, I = p->dims[mode], n = I * (int64_t)R;
-    T *buf = nullptr;
-    double *sums = nullptr;
-    // m_e, phi', phi'' (nnz each); g, rhs, step (I x R each)
+    // m_e, phi', phi'' (nnz each); g, rhs, step (I x R each): the pattern's
+    // work space (allocated once per size)
     const size_t elems = (size_t)3 * (size_t)(m > 0 ? m : 1) + (size_t)3 * (size_t)n;
-    TC_CUDA(cudaMallocAsync((void **)&buf, sizeof(T) * elems, st));
-    if (cudaMallocAsync((void **)&sums, 2 * sizeof(double), st) != cudaSuccess) {
-        cudaFreeAsync(buf, st);
-        return TC_ERR_OOM;
-    }
+    T *buf = (T *)work_buffer(p, WS_NEWTON, sizeof(T) * elems);
+    double *sums = (double *)work_buffer(p, WS_NEWTON_SUMS, 2 * sizeof(double));
+    if (!buf || !sums) return TC_ERR_OOM;
     T *mv = buf, *d1 = mv + (m > 0 ? m : 1), *d2 = d1 + (m > 0 ? m : 1);
     T *g = d2 + (m > 0 ? m : 1), *rhs = g + n, *step = rhs + n;
     T *Ad = (T *)factors[mode];
@@ -137,8 +134,6 @@ static tc_status newton_t(const tc_pattern *p, tc_loss loss, int R, void *const 
         if (sqrt(h[0]) <= tol * sqrt(h[1])) break;
     }
     if (rc == TC_OK && cudaGetLastError() != cudaSuccess) rc = TC_ERR_CUDA;
-    cudaFreeAsync(sums, st);
-    cudaFreeAsync(buf, st);
     if (steps_out) *steps_out = taken;
     return rc;
 }
@@ -159,7 +154,7 @@ extern "C" tc_status tc_newton_als_mode(const tc_pattern *p, tc_loss loss, int R
         return TC_ERR_ARG;
     if (inner_iters < 1 || !(tol >= 0.0)) return TC_ERR_ARG;
     if (!p->has_vals && p->nnz > 0) return TC_ERR_ARG;
-    const int form = prec & ~TC_PREC_CHOL32;
+    const int form = prec & ~(TC_PREC_CHOL32 | TC_PREC_REFINE2);
     if (form != TC_PREC_FP32 && form != TC_PREC_TF32_REFINE && form != TC_PREC_BF16_REFINE &&
         form != TC_PREC_FP32_REFINE)
         return TC_ERR_ARG;

@@ -27,6 +27,8 @@
 
 #include "internal.cuh"
 
+#include <mutex>
+
 namespace tc {
 
 template <typename T>
@@ -45,7 +47,7 @@ struct SolveParams {
     int8_t *row_status;
     double lambda;
     int R;
-    int refine;                   // one refinement step after the solve
+    int refine;                   // refinement steps after the solve (0, 1 or 2)
     int *status;
 };
 
@@ -1555,8 +1557,10 @@ static int device_sms() {
     return sms[dev];
 }
 
-// Process-wide tuning per dtype and rank tier (0 = automatic).
+// Process-wide tuning per dtype and rank tier (0 = automatic), read and
+// written under g_tuning_mu; a call copies the setting it uses once.
 static tc_solve_tuning g_tuning[2][4];
+static std::mutex g_tuning_mu;
 
 static int tier_slot(int tier) { return tier <= 8 ? 0 : tier <= 16 ? 1 : tier <= 32 ? 2 : 3; }
 
@@ -1616,7 +1620,8 @@ struct GramLaunch {
 };
 
 template <typename T, int RT, bool VEC, int KIND, bool CHOL32>
-static tc_status launch_solve_rt(const SolveParams<T> &P, int64_t m, cudaStream_t st) {
+static tc_status launch_solve_rt(const SolveParams<T> &P, int64_t m, const tc_solve_tuning &tun,
+                                 const tc_pattern *pat, int mode, cudaStream_t st) {
     using GL = GramLaunch<T, RT, VEC, KIND>;
     using CT = typename std::conditional<CHOL32, float, double>::type;   // factorization type
     const int R = P.R, tri = R * (R + 1) / 2;
@@ -1626,7 +1631,6 @@ static tc_status launch_solve_rt(const SolveParams<T> &P, int64_t m, cudaStream_
         const tc_status rc = GL::occupancy(occ);
         if (rc != TC_OK) return rc;
     }
-    const tc_solve_tuning tun = g_tuning[sizeof(T) == 8 ? 1 : 0][tier_slot(RT)];
     const int64_t grid_a = (int64_t)sms * occ;
     const int64_t ch = chunk_nnz(m, GL::PER_WARP ? grid_a * (GL::threads() / 32) : grid_a, tun);
     const int64_t ch_c = ch / 4 > 64 ? ch / 4 : 64;    // refinement: a warp per chunk
@@ -1661,15 +1665,13 @@ static tc_status launch_solve_rt(const SolveParams<T> &P, int64_t m, cudaStream_
     if (batch < align) batch = align;
     if (batch > P.I) batch = P.I;
     const int64_t slots = (m + ch - 1) / ch + 1;
-    T *light = nullptr;
-    double *cut = nullptr, *res = nullptr;
-    TC_CUDA(cudaMallocAsync((void **)&light, sizeof(T) * (size_t)tri * batch, st));
-    if (cudaMallocAsync((void **)&cut, sizeof(double) * (size_t)tri * slots, st) != cudaSuccess ||
-        (P.refine && cudaMallocAsync((void **)&res, sizeof(double) * (size_t)R * batch, st) != cudaSuccess)) {
-        if (cut) cudaFreeAsync(cut, st);
-        cudaFreeAsync(light, st);
-        return TC_ERR_OOM;
-    }
+    // the Gram batch, the cut-row slots and the residuals live in the
+    // pattern's work space for this mode (allocated once per size)
+    T *light = (T *)work_buffer(pat, WS_SOLVE_GRAM + mode, sizeof(T) * (size_t)tri * batch);
+    double *cut = (double *)work_buffer(pat, WS_SOLVE_CUT + mode, sizeof(double) * (size_t)tri * slots);
+    double *res = nullptr;
+    if (P.refine) res = (double *)work_buffer(pat, WS_SOLVE_RES + mode, sizeof(double) * (size_t)R * batch);
+    if (!light || !cut || (P.refine && !res)) return TC_ERR_OOM;
     const int64_t nblk_w0 = (int64_t)sms * 16;
     for (int64_t row0 = 0; row0 < P.I; row0 += batch) {
         Batch<T> Bt{row0, min(batch, P.I - row0), ch, light, cut, res};
@@ -1685,38 +1687,37 @@ static tc_status launch_solve_rt(const SolveParams<T> &P, int64_t m, cudaStream_
         else
             chol_rows_kernel<T, CT><<<(unsigned)((Bt.nrows + rpw - 1) / rpw), 32, smem_b, st>>>(P, Bt, rpw);
         count_launch(3);
-        if (P.refine) {
+        for (int step = 0; step < P.refine; ++step) {
             TC_CUDA(cudaMemsetAsync(res, 0, sizeof(double) * (size_t)R * Bt.nrows, st));
             refine_resid_kernel<T, RT, VEC><<<(unsigned)(sms * 8), 128, 0, st>>>(P, Bt, ch_c);
             refine_correct_kernel<T><<<(unsigned)nblk_w, kCholWarps * 32, 0, st>>>(P, Bt);
             count_launch(2);
         }
     }
-    const cudaError_t le = cudaGetLastError();
-    cudaError_t f0 = cudaSuccess;
-    if (res) f0 = cudaFreeAsync(res, st);
-    const cudaError_t f1 = cudaFreeAsync(cut, st), f2 = cudaFreeAsync(light, st);
-    return (le == cudaSuccess && f0 == cudaSuccess && f1 == cudaSuccess && f2 == cudaSuccess)
-               ? TC_OK
-               : TC_ERR_CUDA;
+    return cudaGetLastError() == cudaSuccess ? TC_OK : TC_ERR_CUDA;
 }
 
 template <typename T, int KIND, bool C32>
 static tc_status dispatch_rt(const SolveParams<T> &P, int tier, bool vec, int64_t m,
+                             const tc_solve_tuning &tun, const tc_pattern *pat, int mode,
                              cudaStream_t st) {
+#define TC_SOLVE_RT(RT)                                                                     \
+    return vec ? launch_solve_rt<T, RT, true, KIND, C32>(P, m, tun, pat, mode, st)          \
+               : launch_solve_rt<T, RT, false, KIND, C32>(P, m, tun, pat, mode, st)
     switch (tier) {
-        case 8: return vec ? launch_solve_rt<T, 8, true, KIND, C32>(P, m, st) : launch_solve_rt<T, 8, false, KIND, C32>(P, m, st);
-        case 16: return vec ? launch_solve_rt<T, 16, true, KIND, C32>(P, m, st) : launch_solve_rt<T, 16, false, KIND, C32>(P, m, st);
-        case 32: return vec ? launch_solve_rt<T, 32, true, KIND, C32>(P, m, st) : launch_solve_rt<T, 32, false, KIND, C32>(P, m, st);
-        default: return vec ? launch_solve_rt<T, 64, true, KIND, C32>(P, m, st) : launch_solve_rt<T, 64, false, KIND, C32>(P, m, st);
+        case 8: TC_SOLVE_RT(8);
+        case 16: TC_SOLVE_RT(16);
+        case 32: TC_SOLVE_RT(32);
+        default: TC_SOLVE_RT(64);
     }
+#undef TC_SOLVE_RT
 }
 
 template <typename T>
 static tc_status solve_t(const tc_pattern *p, tc_weights w, const void *s, int R,
                          const void *const *A, int mode, const void *rhs, double lambda,
                          tc_prec prec, void *out, int8_t *row_status, int use_d2, tc_loss loss,
-                         void *pinv, cudaStream_t st) {
+                         void *pinv, cudaStream_t st, const tc_solve_tuning &tun) {
     const ModeData &md = p->md[mode];
     int o1, o2;
     other_modes(mode, o1, o2);
@@ -1738,7 +1739,8 @@ static tc_status solve_t(const tc_pattern *p, tc_weights w, const void *s, int R
     P.lambda = lambda;
     P.R = R;
     P.status = p->status;
-    P.refine = (!pinv && (prec & ~TC_PREC_CHOL32) != TC_PREC_FP32) ? 1 : 0;
+    const tc_prec form = (tc_prec)(prec & ~(TC_PREC_CHOL32 | TC_PREC_REFINE2));
+    P.refine = (!pinv && form != TC_PREC_FP32) ? ((prec & TC_PREC_REFINE2) ? 2 : 1) : 0;
     if (!use_d2) {
         P.w.kind = (int)w;
         P.w.s = nullptr;
@@ -1758,42 +1760,40 @@ static tc_status solve_t(const tc_pattern *p, tc_weights w, const void *s, int R
     const bool vec = vec_ok(R, tier, sizeof(T)) && aligned16({A[o1], A[o2]}) &&
                      (!use_d2 || aligned16({A[mode]}));
     const int64_t m = p->nnz;
-    if (sizeof(T) == 8 && ((prec & ~TC_PREC_CHOL32) == TC_PREC_TF32_REFINE ||
-                           (prec & ~TC_PREC_CHOL32) == TC_PREC_BF16_REFINE))
+    if (sizeof(T) == 8 && (form == TC_PREC_TF32_REFINE || form == TC_PREC_BF16_REFINE))
         return TC_ERR_UNSUPPORTED;
     // the correction step reads rhs after the solve wrote out: keep a copy
     // when they alias
-    T *rhs_copy = nullptr;
     if (P.refine && (const void *)P.out == (const void *)P.rhs) {
         const size_t bytes = sizeof(T) * (size_t)P.I * R;
-        TC_CUDA(cudaMallocAsync((void **)&rhs_copy, bytes, st));
-        if (cudaMemcpyAsync(rhs_copy, P.rhs, bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
-            cudaFreeAsync(rhs_copy, st);
-            return TC_ERR_CUDA;
-        }
+        T *rhs_copy = (T *)work_buffer(p, WS_SOLVE_RHS + mode, bytes);
+        if (!rhs_copy) return TC_ERR_OOM;
+        TC_CUDA(cudaMemcpyAsync(rhs_copy, P.rhs, bytes, cudaMemcpyDeviceToDevice, st));
         P.rhs = rhs_copy;
     }
     tc_status rc = TC_OK;
-    const tc_prec form = (tc_prec)(prec & ~TC_PREC_CHOL32);
     const bool c32 = (prec & TC_PREC_CHOL32) != 0 && P.refine;
+#define TC_SOLVE_KIND(K)                                                          \
+    (c32 ? dispatch_rt<T, K, true>(P, tier, vec, m, tun, p, mode, st)             \
+         : dispatch_rt<T, K, false>(P, tier, vec, m, tun, p, mode, st))
     if constexpr (sizeof(T) == 4) {
-        if (form == TC_PREC_TF32_REFINE)
-            rc = c32 ? dispatch_rt<T, GK_TF32, true>(P, tier, vec, m, st)
-                     : dispatch_rt<T, GK_TF32, false>(P, tier, vec, m, st);
-        else if (form == TC_PREC_BF16_REFINE)
-            rc = c32 ? dispatch_rt<T, GK_BF16, true>(P, tier, vec, m, st)
-                     : dispatch_rt<T, GK_BF16, false>(P, tier, vec, m, st);
-        else
-            rc = c32 ? dispatch_rt<T, GK_TF32X3, true>(P, tier, vec, m, st)
-                     : dispatch_rt<T, GK_TF32X3, false>(P, tier, vec, m, st);
+        if (form == TC_PREC_TF32_REFINE) rc = TC_SOLVE_KIND(GK_TF32);
+        else if (form == TC_PREC_BF16_REFINE) rc = TC_SOLVE_KIND(GK_BF16);
+        else rc = TC_SOLVE_KIND(GK_TF32X3);
     } else {
-        rc = c32 ? dispatch_rt<T, GK_FFMA, true>(P, tier, vec, m, st)
-                 : dispatch_rt<T, GK_FFMA, false>(P, tier, vec, m, st);
+        rc = TC_SOLVE_KIND(GK_FFMA);
     }
-    if (rhs_copy && cudaFreeAsync(rhs_copy, st) != cudaSuccess && rc == TC_OK) rc = TC_ERR_CUDA;
+#undef TC_SOLVE_KIND
     return rc;
 }
 
+}  // namespace tc
+
+namespace tc {
+tc_solve_tuning solve_tuning(tc_dtype dtype, int R) {
+    std::lock_guard<std::mutex> lock(g_tuning_mu);
+    return g_tuning[dtype == TC_F64 ? 1 : 0][tier_slot(rank_tier(R))];
+}
 }  // namespace tc
 
 extern "C" tc_status tc_set_solve_tuning(tc_dtype dtype, int R, const tc_solve_tuning *t) {
@@ -1805,6 +1805,7 @@ extern "C" tc_status tc_set_solve_tuning(tc_dtype dtype, int R, const tc_solve_t
         if (v < 1 || v > 32 || (v & (v - 1))) return TC_ERR_ARG;
     }
     const tc_solve_tuning v = t ? *t : tc_solve_tuning{0, 0, 0};
+    std::lock_guard<std::mutex> lock(tc::g_tuning_mu);
     for (int k = 0; k < 4; ++k)
         if (R == 0 || tc::tier_slot(tc::rank_tier(R)) == k) tc::g_tuning[dtype][k] = v;
     return TC_OK;
@@ -1812,7 +1813,7 @@ extern "C" tc_status tc_set_solve_tuning(tc_dtype dtype, int R, const tc_solve_t
 
 extern "C" tc_status tc_get_solve_tuning(tc_dtype dtype, int R, tc_solve_tuning *t) {
     if ((dtype != TC_F32 && dtype != TC_F64) || R < 1 || R > TC_MAX_RANK || !t) return TC_ERR_ARG;
-    *t = tc::g_tuning[dtype][tc::tier_slot(tc::rank_tier(R))];
+    *t = tc::solve_tuning(dtype, R);
     return TC_OK;
 }
 
@@ -1826,7 +1827,9 @@ extern "C" tc_status tc_autotune_solve(const tc_pattern *p, tc_weights w, const 
         return TC_ERR_ARG;
     const int dt = p->dtype == TC_F64 ? 1 : 0;
     const int tier = tc::rank_tier(R), slot = tc::tier_slot(tier);
-    const tc_solve_tuning saved = tc::g_tuning[dt][slot];
+    // every candidate is passed to the solve explicitly: the process-wide
+    // setting, which other threads' solves read, only changes to the winner
+    const tc_solve_tuning saved = tc::solve_tuning(p->dtype, R);
     const int64_t chunks[] = {0, 256, 1024, 4096, 16384};
     int rpws[3] = {0, 0, 0};
     int nr = 1;
@@ -1843,14 +1846,14 @@ extern "C" tc_status tc_autotune_solve(const tc_pattern *p, tc_weights w, const 
     tc_status rc = TC_OK;
     for (int64_t ch : chunks) {
         for (int k = 0; k < nr && rc == TC_OK; ++k) {
-            tc::g_tuning[dt][slot] = tc_solve_tuning{ch, saved.batch_bytes, rpws[k]};
-            // one untimed call (allocator, caches), then one timed
+            const tc_solve_tuning cand{ch, saved.batch_bytes, rpws[k]};
+            // one untimed call (caches, work space), then one timed
             rc = tc::launch_solve_factor(p, w, s, R, factors, mode, rhs, lambda, prec, out, nullptr,
-                                         0, TC_LOSS_LS, nullptr, st);
+                                         0, TC_LOSS_LS, nullptr, st, &cand);
             if (rc != TC_OK) break;
             if (cudaEventRecord(e0, st) != cudaSuccess) { rc = TC_ERR_CUDA; break; }
             rc = tc::launch_solve_factor(p, w, s, R, factors, mode, rhs, lambda, prec, out, nullptr,
-                                         0, TC_LOSS_LS, nullptr, st);
+                                         0, TC_LOSS_LS, nullptr, st, &cand);
             if (rc != TC_OK) break;
             float ms = 0.f;
             if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
@@ -1860,15 +1863,18 @@ extern "C" tc_status tc_autotune_solve(const tc_pattern *p, tc_weights w, const 
             }
             if (win_ms < 0.f || ms < win_ms) {
                 win_ms = ms;
-                win = tc::g_tuning[dt][slot];
+                win = cand;
             }
         }
         if (rc != TC_OK) break;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    tc::g_tuning[dt][slot] = rc == TC_OK ? win : saved;
     if (rc != TC_OK) return rc;
+    {
+        std::lock_guard<std::mutex> lock(tc::g_tuning_mu);
+        tc::g_tuning[dt][slot] = win;
+    }
     if (best) *best = win;
     if (ms_out) *ms_out = win_ms;
     return TC_OK;
@@ -1879,12 +1885,14 @@ namespace tc {
 tc_status launch_solve_factor(const tc_pattern *p, tc_weights w, const void *s, int R,
                               const void *const *A, int mode, const void *rhs, double lambda,
                               tc_prec prec, void *out, int8_t *row_status, int use_loss_d2,
-                              tc_loss loss, void *pinv_out, cudaStream_t st) {
+                              tc_loss loss, void *pinv_out, cudaStream_t st,
+                              const tc_solve_tuning *tun) {
+    const tc_solve_tuning t = tun ? *tun : solve_tuning(p->dtype, R);
     if (p->dtype == TC_F64)
         return solve_t<double>(p, w, s, R, A, mode, rhs, lambda, prec, out, row_status,
-                               use_loss_d2, loss, pinv_out, st);
+                               use_loss_d2, loss, pinv_out, st, t);
     return solve_t<float>(p, w, s, R, A, mode, rhs, lambda, prec, out, row_status, use_loss_d2,
-                          loss, pinv_out, st);
+                          loss, pinv_out, st, t);
 }
 
 }  // namespace tc
