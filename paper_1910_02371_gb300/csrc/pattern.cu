@@ -442,18 +442,23 @@ __global__ void range_check_kernel(const int32_t *__restrict__ idx, int64_t n, i
     }
 }
 
-// row_ptr from sorted keys: row r starts at the first position with key >= r.
-// Keys outside [0, I) (already recorded as TC_ERR_RANGE) are clamped so that no
-// write leaves the array.
+// row_ptr from sorted keys: row r (0 <= r <= I) starts at the first position
+// whose key is >= r, found by a binary search per row, so every row costs the
+// same whatever the row lengths.  Keys outside [0, I) (already recorded as
+// TC_ERR_RANGE) are clamped to [-1, I - 1]; the search result is then still
+// nondecreasing in r and within [0, n], so no later kernel leaves its arrays.
 __global__ void row_ptr_kernel(const int32_t *__restrict__ sk, int64_t n, int64_t I,
                                int64_t *__restrict__ row_ptr) {
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
-         q += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t key = min(max((int64_t)sk[q], (int64_t)-1), I - 1);
-        const int64_t prev = q > 0 ? min(max((int64_t)sk[q - 1], (int64_t)-1), I - 1) : -1;
-        for (int64_t r = prev + 1; r <= key; ++r) row_ptr[r] = q;
-        if (q == n - 1)
-            for (int64_t r = key + 1; r <= I; ++r) row_ptr[r] = n;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r <= I;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        int64_t lo = 0, hi = n;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            const int64_t key = min(max((int64_t)__ldg(sk + mid), (int64_t)-1), I - 1);
+            if (key < r) lo = mid + 1;
+            else hi = mid;
+        }
+        row_ptr[r] = lo;
     }
 }
 
@@ -549,10 +554,33 @@ void free_pattern(tc_pattern *p) {
         cudaFree(m.vals);
     }
     free_scratch(p);
+    for (int k = 0; k < WS_COUNT; ++k) cudaFree(p->ws[k].ptr);
     cudaFree(p->status);
     cudaFree(p->counts);
-    cudaFree(p->dscratch);
     delete p;
+}
+
+void *work_buffer(const tc_pattern *pc, int id, size_t bytes) {
+    tc_pattern *p = const_cast<tc_pattern *>(pc);
+    if (id < 0 || id >= WS_COUNT) return nullptr;
+    WorkBuf &b = p->ws[id];
+    if (bytes == 0) bytes = 16;
+    if (b.ptr && b.bytes >= bytes) return b.ptr;
+    if (b.ptr) {
+        // work already queued may still read or write the old buffer
+        if (cudaDeviceSynchronize() != cudaSuccess) return nullptr;
+        cudaFree(b.ptr);
+        b.ptr = nullptr;
+        b.bytes = 0;
+    }
+    const size_t want = (bytes + 255) / 256 * 256;
+    if (cudaMalloc(&b.ptr, want) != cudaSuccess) {
+        cudaGetLastError();
+        b.ptr = nullptr;
+        return nullptr;
+    }
+    b.bytes = want;
+    return b.ptr;
 }
 
 static bool dalloc(void **ptr, size_t bytes) {
@@ -620,8 +648,7 @@ static tc_status alloc_pattern(tc_pattern *p) {
     const size_t es = tsize(p->dtype);
     const bool lean = (p->flags & TC_PATTERN_LEAN) != 0;
     bool ok = dalloc((void **)&p->status, sizeof(int)) &&
-              dalloc((void **)&p->counts, sizeof(int64_t) * TC_ORDER) &&
-              dalloc((void **)&p->dscratch, sizeof(double) * kScratchDoubles);
+              dalloc((void **)&p->counts, sizeof(int64_t) * TC_ORDER);
     for (int d = 0; d < TC_ORDER && ok; ++d) {
         ModeData &m = p->md[d];
         const int64_t I = p->dims[d];
@@ -683,11 +710,8 @@ static void fill_pattern(tc_pattern *p, const int32_t *const *idx, const void *v
         }
         radix_sort_p(p->has_vals ? (int)tsize(p->dtype) : 0, in, out, tmp, n, I - 1, p->dims[o1],
                      p->dims[o2], w.hist, w.scan, first_to_out, st);
-        cudaMemsetAsync(m.row_ptr, 0, sizeof(int64_t) * (I + 1), st);
-        if (n > 0) {
-            row_ptr_kernel<<<grid_for(n, 256), 256, 0, st>>>(out.key, n, I, m.row_ptr);
-            count_launch();
-        }
+        row_ptr_kernel<<<grid_for(I + 1, 256), 256, 0, st>>>(out.key, n, I, m.row_ptr);
+        count_launch();
         nonempty_flags_kernel<<<grid_for(I, 256), 256, 0, st>>>(m.row_ptr, I, w.flags);
         count_launch();
         scan_exclusive(w.flags, w.flags, I, w.scan, st);
@@ -759,6 +783,8 @@ tc_status ensure_to0(const tc_pattern *pc, cudaStream_t st) {
     if (p->to0_valid || p->nnz == 0) return TC_OK;
     if (p->flags & TC_PATTERN_LEAN) return TC_ERR_UNSUPPORTED;   // no positions kept
     const int64_t n = p->nnz;
+    // the inverse permutation is needed once per pattern contents: a refillable
+    // pattern keeps it in its builder work space, others borrow it for this call
     int64_t *inv0 = p->work.inv0;
     const bool temp = inv0 == nullptr;
     if (temp) TC_CUDA(cudaMallocAsync((void **)&inv0, sizeof(int64_t) * n, st));
@@ -868,10 +894,7 @@ extern "C" tc_status tc_sort_mode_noalloc(int64_t nnz, const int32_t *key, int64
         count_launch();
     }
     radix_sort(key, nullptr, nnz, I - 1, kout, perm, ktmp, vtmp, hist, scan, st);
-    if (cudaMemsetAsync(row_ptr, 0, sizeof(int64_t) * (I + 1), st) != cudaSuccess) return TC_ERR_CUDA;
-    if (nnz > 0) {
-        row_ptr_kernel<<<grid_for(nnz, 256), 256, 0, st>>>(kout, nnz, I, row_ptr);
-        count_launch();
-    }
+    row_ptr_kernel<<<grid_for(I + 1, 256), 256, 0, st>>>(kout, nnz, I, row_ptr);
+    count_launch();
     return cudaGetLastError() == cudaSuccess ? TC_OK : TC_ERR_CUDA;
 }
