@@ -159,6 +159,18 @@ __global__ void axpby_kernel(int64_t n, T a, const T *__restrict__ x, T b, T *y)
         y[q] = a * x[q] + b * y[q];
 }
 
+// out (+)= sum x_i y_i in FP64 (one atomic per warp).
+template <typename T>
+__global__ void dot_kernel(int64_t n, const T *__restrict__ x, const T *__restrict__ y,
+                           double *out) {
+    double acc = 0.0;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+         q += (int64_t)gridDim.x * blockDim.x)
+        acc += (double)x[q] * (double)y[q];
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0 && acc != 0.0) atomicAdd(out, acc);
+}
+
 // Interleaved buffer from a factor (part 0) or a direction (part 1).
 template <typename T>
 __global__ void ax_fill_kernel(T *__restrict__ ax, const T *__restrict__ src, int64_t I, int R,
@@ -590,6 +602,45 @@ tc_status tc_ggn_step(tc_cg *cg, int iters, double *loss_out, tc_stream_t stream
                                                                  1.0f, (float *)cg->A[d]);
         count_launch();
     }
+    return cudaGetLastError() == cudaSuccess ? TC_OK : TC_ERR_CUDA;
+}
+
+// ------------------------------------------------------------------ vector steps
+static int64_t vec_blocks(int64_t n) {
+    int64_t b = (n + 255) / 256;
+    if (b > 8LL * sms()) b = 8LL * sms();
+    return b < 1 ? 1 : b;
+}
+
+tc_status tc_axpby(tc_dtype dtype, int64_t n, double alpha, const void *x, double beta, void *y,
+                   tc_stream_t stream) {
+    if ((dtype != TC_F32 && dtype != TC_F64) || n < 0 || (n > 0 && (!x || !y))) return TC_ERR_ARG;
+    if (n == 0) return TC_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (dtype == TC_F64)
+        axpby_kernel<double><<<(unsigned)vec_blocks(n), 256, 0, st>>>(n, alpha, (const double *)x,
+                                                                     beta, (double *)y);
+    else
+        axpby_kernel<float><<<(unsigned)vec_blocks(n), 256, 0, st>>>(n, (float)alpha, (const float *)x,
+                                                                    (float)beta, (float *)y);
+    count_launch();
+    return cudaGetLastError() == cudaSuccess ? TC_OK : TC_ERR_CUDA;
+}
+
+tc_status tc_dot(tc_dtype dtype, int64_t n, const void *x, const void *y, double *out,
+                 int accumulate, tc_stream_t stream) {
+    if ((dtype != TC_F32 && dtype != TC_F64) || n < 0 || !out || (n > 0 && (!x || !y)))
+        return TC_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!accumulate) TC_CUDA(cudaMemsetAsync(out, 0, sizeof(double), st));
+    if (n == 0) return TC_OK;
+    if (dtype == TC_F64)
+        dot_kernel<double><<<(unsigned)vec_blocks(n), 256, 0, st>>>(n, (const double *)x,
+                                                                   (const double *)y, out);
+    else
+        dot_kernel<float><<<(unsigned)vec_blocks(n), 256, 0, st>>>(n, (const float *)x,
+                                                                  (const float *)y, out);
+    count_launch();
     return cudaGetLastError() == cudaSuccess ? TC_OK : TC_ERR_CUDA;
 }
 

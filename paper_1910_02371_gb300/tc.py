@@ -23,8 +23,10 @@ LOSSES = {"ls": 0, "poisson_log": 1, "poisson_id": 2}
 W_ONE, W_VALUES, W_ARRAY = 0, 1, 2
 PRECS = {"fp32": 0, "tf32_refine": 1, "bf16_refine": 2, "fp32_refine": 3}
 CHOL32 = 0x100
-# the refined forms with an FP32 factorization
-PRECS.update({k + "_chol32": v | CHOL32 for k, v in list(PRECS.items()) if k.endswith("_refine")})
+REFINE2 = 0x200
+# the refined forms with two refinement steps, and with an FP32 factorization
+PRECS.update({k + "2": v | REFINE2 for k, v in list(PRECS.items()) if k.endswith("_refine")})
+PRECS.update({k + "_chol32": v | CHOL32 for k, v in list(PRECS.items()) if "_refine" in k})
 CHECK_DUPLICATES = 1
 REFILLABLE = 2
 LEAN = 4
@@ -68,6 +70,8 @@ _SIGS = {
     "tc_cg_set_hessian": [_P, _I],
     "tc_ccd_sweep": [_P, _I, _P, _D, _P],
     "tc_ccd_newton_sweep": [_P, _I, _I, _P, _D, _I, _D, _P, _P],
+    "tc_axpby": [_I, _I64, _D, _P, _D, _P, _P],
+    "tc_dot": [_I, _I64, _P, _P, _P, _I, _P],
 }
 for _name, _args in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -449,3 +453,23 @@ def ccd_newton_sweep(p: Pattern, factors, loss: str, lam: float, inner_iters: in
            "tc_ccd_newton_sweep")
     N = len(factors)
     return [[int(steps[r * N + d]) for d in range(N)] for r in range(R)]
+
+
+def axpby(alpha: float, x: torch.Tensor, beta: float, y: torch.Tensor, stream=None):
+    """tc_axpby: y = alpha x + beta y in place (same dtype and length)."""
+    if x.numel() != y.numel() or x.dtype != y.dtype or not (x.is_contiguous() and y.is_contiguous()):
+        raise ValueError("x, y: contiguous tensors of one dtype and length")
+    _check(_lib.tc_axpby(_dtype_code(y.dtype), y.numel(), float(alpha), _ptr(x), float(beta),
+                         _ptr(y), _stream(stream)), "tc_axpby")
+    return y
+
+
+def dot(x: torch.Tensor, y: torch.Tensor, out=None, accumulate=False, stream=None):
+    """tc_dot: FP64 sum of x_i y_i into a 1-element float64 device tensor."""
+    if x.numel() != y.numel() or x.dtype != y.dtype or not (x.is_contiguous() and y.is_contiguous()):
+        raise ValueError("x, y: contiguous tensors of one dtype and length")
+    if out is None:
+        out = torch.zeros(1, dtype=torch.float64, device=x.device)
+    _check(_lib.tc_dot(_dtype_code(x.dtype), x.numel(), _ptr(x), _ptr(y), _ptr(out),
+                       1 if accumulate else 0, _stream(stream)), "tc_dot")
+    return out
