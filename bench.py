@@ -70,9 +70,16 @@ def metric_of(w):
 # nonzero count (the capture size rule keeps multi-pass ncu runs off the full
 # workload).
 NCU_TRAFFIC = {
+    # 4e6-nonzero capture (36.65 MB read per launch) scaled to 1e7
     ("cp3_10k_m10M_r16", "ggn_matvec"): {"bytes": 3 * 36.65e6 * 2.5,
                                          "file": "paper_1910_02371_gb300/csrc/sweep.cu",
                                          "src": "1d03ab541fb6d2df"},
+    # 1e8-nonzero capture at the same 2^22 rows per mode (26.91 GB read +
+    # 0.28 GB written per launch: every row gather misses L2 at both sizes)
+    # scaled to 4e9
+    ("cp3_4M_m4B_r16", "ggn_matvec"): {"bytes": 3 * (26.911e9 + 0.2808e9) * 40,
+                                       "file": "paper_1910_02371_gb300/csrc/sweep.cu",
+                                       "src": "1d03ab541fb6d2df"},
 }
 
 
@@ -182,6 +189,37 @@ def make_device_inputs(w, seed, dev):
     del pd
     torch.cuda.synchronize()
     return idx, vals, start
+
+
+# ------------------------------------------------------------------ gather peak
+def measure_gather_peak(dev, rows, row_floats, nbags=1 << 22, per_bag=32, reps=5):
+    """Random factor-row fetches per second a library kernel reaches on this
+    GPU: torch's embedding_bag (sum mode) over a rows x row_floats FP32 table
+    (larger than L2 at the sizes used here) with uniform random row ids, 32 rows
+    per bag.  The denominator of the gather roofline: when the factor matrices
+    do not fit in L2 the sweeps are bound by the rate of random row fetches
+    from HBM, not by its streaming bandwidth."""
+    import torch
+    import torch.nn.functional as F
+    table = torch.randn(rows, row_floats, dtype=torch.float32, device=dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(12345)
+    ids = torch.randint(0, rows, (nbags * per_bag,), device=dev, generator=g)
+    offs = torch.arange(0, nbags * per_bag, per_bag, device=dev)
+    F.embedding_bag(ids, table, offs, mode="sum")
+    torch.cuda.synchronize()
+    best = None
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        F.embedding_bag(ids, table, offs, mode="sum")
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    del table, ids, offs
+    torch.cuda.empty_cache()
+    return nbags * per_bag / (best / 1e3)
 
 
 # ------------------------------------------------------------------ CPU sample
@@ -297,7 +335,8 @@ def run_ours(args):
 
     w = synth.WORKLOADS[args.workload]
     if args.nnz:
-        w = synth.scaled(w, args.nnz)
+        w = synth.scaled(w, args.nnz,
+                         dims=(1 << args.bits,) * 3 if (args.bits and w.coords == "feistel") else None)
     m = w.nnz
     f32 = torch.float32
     lean = w.coords == "feistel"
@@ -308,7 +347,7 @@ def run_ours(args):
         idx_h = t_h = None
         # host copies for the end-to-end leg, taken before the build consumes them
         idx_pin = t_pin = None
-        if not args.quick and not args.solve_probe:
+        if not args.quick and args.solve_probe is None and not args.kernel_probe:
             idx_pin = [torch.empty(m, dtype=torch.int32).pin_memory() for _ in range(3)]
             t_pin = torch.empty(m, dtype=f32).pin_memory()
             for dst, src in zip(idx_pin, idx):
@@ -367,6 +406,44 @@ def run_ours(args):
         if rank == 0:
             print(json.dumps({"solve_probe": {"workload": w.name, "nnz": w.nnz, "mode": d,
                                               "rows": w.dims[d], "ms_per_call": ms}}), flush=True)
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    if args.kernel_probe:
+        # one kernel alone, --warmup untimed calls then --steps timed (CUDA
+        # events): the command the per-kernel ncu captures run
+        kind = args.kernel_probe
+        xs = [torch.randn_like(a) for a in A]
+        ys = [torch.empty_like(a) for a in A]
+        if kind == "ggn":
+            cgp = tc.CG(p, A, w.loss, w.lam, precondition=False)
+            fn = lambda: cgp.matvec(xs, ys)
+        elif kind == "mttkrp":
+            fn = lambda: tc.mttkrp(p, A, 0, out=rhs[0])
+        elif kind == "tttp":
+            fn = lambda: tc.tttp(p, A, weights=None, out=xbuf)
+        elif kind == "grad":
+            fn = lambda: tc.loss_grad(p, A, w.loss, w.lam, grads=ys)
+        elif kind == "solve":
+            tc.mttkrp(p, A, 0, out=rhs[0])
+            fn = lambda: tc.solve_factor(p, A, 0, rhs[0], w.lam, out=ys[0], prec=args.prec)
+        else:
+            raise SystemExit(f"unknown --kernel-probe {kind}")
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            fn()
+        e1.record()
+        e1.synchronize()
+        if tc.last_error(p) != tc.OK:
+            raise RuntimeError("device error in the kernel probe")
+        if rank == 0:
+            print(json.dumps({"kernel_probe": kind, "workload": w.name, "dims": list(w.dims),
+                              "nnz": m, "ms_per_call": e0.elapsed_time(e1) / args.steps}), flush=True)
         if world > 1:
             dist.destroy_process_group()
         return
@@ -541,6 +618,22 @@ def run_ours(args):
     roofline["traffic"] = (traffic["bytes"] if traffic and traffic["src"] == src_hash(traffic["file"])
                            else None)
 
+    # ---- gather roofline: random factor-row fetches per second against the
+    # rate a library gather kernel reaches (factors larger than L2 only)
+    gather = None
+    if lean:
+        wide = 2 * w.rank if main_kind == "ggn_matvec" else w.rank   # interleaved A|X rows
+        fetches = {"ggn_matvec": 6 * m, "tttp": 2 * m, "mttkrp": 2 * m, "solve_factor": 2 * m,
+                   "loss_grad": 6 * m}[main_kind]
+        ms_main = roofline["ms"]
+        peak_rows = measure_gather_peak(dev, max(w.dims), wide)
+        gather = {"bound": "hbm random row fetches", "unit": "rows/s",
+                  "row_bytes": 4 * wide, "fetches_per_launch": fetches,
+                  "achieved": fetches / (ms_main / 1e3), "peak": peak_rows,
+                  "frac": fetches / (ms_main / 1e3) / peak_rows, "kernel": main_kind,
+                  "peak_source": "measured in this run: torch embedding_bag (sum) over a "
+                                 f"{max(w.dims)} x {wide} FP32 table, 32 uniform random rows per bag"}
+
     # ---- end to end through the C ABI with host buffers
     if not lean:
         idx_pin = [torch.as_tensor(c).pin_memory() for c in idx_h]
@@ -618,6 +711,7 @@ def run_ours(args):
         "ggn_step_s": kern["ggn_step"] / 1e3,
         "time_share_ms": share,
         "roofline": roofline,
+        "gather_roofline": gather,
         "rooflines": roofs,
         "e2e": {"value": e2e_val, "unit": "nnz/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms / e2e_steps,
@@ -692,6 +786,11 @@ def main():
                     help="setup, warm-up and the timed steps only (for profiler runs)")
     ap.add_argument("--nnz", type=int, default=0,
                     help="use the first NNZ coordinates of the workload (smaller profiling case)")
+    ap.add_argument("--bits", type=int, default=0,
+                    help="with --nnz, on the generated workload: dims 2^BITS per mode")
+    ap.add_argument("--kernel-probe", default=None,
+                    choices=["ggn", "mttkrp", "tttp", "grad", "solve"],
+                    help="time one kernel alone (--warmup + --steps calls) and exit")
     ap.add_argument("--prec", default="fp32",
                     help="Solve Factor precision form of the ALS sweep (tc.PRECS; default fp32)")
     ap.add_argument("--solve-probe", type=int, default=None, metavar="MODE",

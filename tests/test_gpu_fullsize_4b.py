@@ -37,7 +37,9 @@ W = synth.WORKLOADS["cp3_4M_m4B_r16"]
 BITS = 22
 CHUNK = 1 << 24
 ROWS_PER_MODE = 10
-FORM_TOL = {"fp32_refine": TOL["f32"], "tf32_refine": 2e-4}
+# per-row solve error of the refined forms on the sampled rows: two TF32 steps
+# reach the FP32 tolerance; one step is bounded at its measured level
+FORM_TOL = {"fp32_refine": TOL["f32"], "tf32_refine2": TOL["f32"], "tf32_refine": 2e-4}
 # input + lean pattern + build work space (8 + ~1 bytes per nonzero), with margin
 NEED_BYTES = W.nnz * (16 + 36 + 9) + (12 << 30)
 

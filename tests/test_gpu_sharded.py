@@ -40,11 +40,13 @@ def test_sharded_one_process_matches_library(tc):
     B = [a.clone() for a in A0]
     f_sh = sh.objective(A)
     f_tc, _ = tc.loss_grad(p, B, "ls", lam, want_grad=False)
-    assert f_sh == f_tc.item()
+    # (FP64 sums whose partial-sum order is not fixed)
+    assert f_sh == pytest.approx(f_tc.item(), rel=1e-12)
     sh.als_sweep(A)
     drivers.als_sweep(p, B, lam)
     for d in range(3):
-        assert torch.equal(A[d], B[d])
+        # the same kernels; only the order of the chunk-boundary atomics differs
+        assert rel(host(A[d]), host(B[d])) <= 1e-6, d
 
     # Gauss-Newton step from the swept factors: host-driven sharded PCG vs
     # the graph-captured solver, and vs the oracle
