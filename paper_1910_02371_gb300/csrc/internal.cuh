@@ -315,6 +315,20 @@ __device__ __forceinline__ int64_t search_le(const int64_t *__restrict__ a, int6
     return lo;
 }
 
+// The same when the answer is usually at or just after lo (the next nonempty
+// row after a finished one): an exponential probe from lo, then the binary
+// search inside the last interval -- one load when the next row is nonempty,
+// instead of a dependent load per halving of [lo, hi].
+__device__ __forceinline__ int64_t search_le_near(const int64_t *__restrict__ a, int64_t lo,
+                                                  int64_t hi, int64_t key) {
+    int64_t b = lo, d = 1;
+    while (b + d <= hi && __ldg(a + b + d) <= key) {
+        b += d;
+        d <<= 1;
+    }
+    return search_le(a, b, min(b + d - 1, hi), key);
+}
+
 // The same with 32-bit positions in the array (row counts fit in int32).
 __device__ __forceinline__ int search_le32(const int64_t *__restrict__ a, int lo, int hi,
                                           int64_t key) {

@@ -648,31 +648,37 @@ __global__ void __launch_bounds__(GramShape<T, RT, KIND>::NTH, 2)
     E eng;
     eng.init(tid);
 
+    // Software pipeline: the loads of stage s + 1 are issued right after stage
+    // s is in shared memory, so they are in flight while the engine consumes
+    // stage s -- across row boundaries too: the last stage of a row fetches
+    // the next row's first stage, which is in flight during the flush.  pb /
+    // pe / pw hold the fetched factor slices and raw weights (the value t for
+    // phi'') of KB consecutive positions, clamped to the chunk; positions
+    // past the current row are fetched but masked when staged.
+    T pb[Q::NSTEP][V], pe[Q::NSTEP][V], pw[Q::NSTEP];
+    int64_t ce = 0;
+    auto fetch = [&](int64_t base) {
+#pragma unroll
+        for (int st = 0; st < Q::NSTEP; ++st) {
+            const int slot = st * Q::BSTEP + w * NG + g;
+            const int64_t qq = base + slot < ce ? base + slot : ce - 1;
+            load_slice<T, V, VEC>(pb[st], P.A1, __ldcs(P.c1 + qq), R, lg);
+            load_slice<T, V, VEC>(pe[st], P.A2, __ldcs(P.c2 + qq), R, lg);
+            pw[st] = P.use_d2 ? __ldcs(P.t + qq) : weight_at(P.w, qq);
+        }
+    };
     for (int64_t cs = nb + (int64_t)blockIdx.x * B.ch; cs < ne; cs += (int64_t)gridDim.x * B.ch) {
-        const int64_t ce = min(cs + B.ch, ne);
+        ce = min(cs + B.ch, ne);
         int64_t i = search_le(P.row_ptr, B.row0, last, cs);
+        bool ahead = false;
         for (;;) {
             const int64_t rs = __ldg(P.row_ptr + i), re = __ldg(P.row_ptr + i + 1);
             const int64_t ss = max(rs, cs), se = min(re, ce);
             T arow[V];
             if (P.use_d2) load_slice<T, V, VEC>(arow, P.Ad, i, R, lg);
             eng.zero();
-            // Software pipeline: the loads of stage s + 1 are issued right
-            // after stage s is in shared memory, so they are in flight while
-            // the engine consumes stage s.  pb / pe / pw hold the fetched
-            // factor slices and raw weights (the value t for phi'').
-            T pb[Q::NSTEP][V], pe[Q::NSTEP][V], pw[Q::NSTEP];
-            auto fetch = [&](int64_t base) {
-#pragma unroll
-                for (int st = 0; st < Q::NSTEP; ++st) {
-                    const int slot = st * Q::BSTEP + w * NG + g;
-                    const int64_t qq = base + slot < se ? base + slot : se - 1;
-                    load_slice<T, V, VEC>(pb[st], P.A1, __ldcs(P.c1 + qq), R, lg);
-                    load_slice<T, V, VEC>(pe[st], P.A2, __ldcs(P.c2 + qq), R, lg);
-                    pw[st] = P.use_d2 ? __ldcs(P.t + qq) : weight_at(P.w, qq);
-                }
-            };
-            fetch(ss);
+            if (!ahead) fetch(ss);
+            ahead = false;
             for (int64_t base = ss; base < se; base += KB) {
                 // ---- stage KB nonzeros: h_e and weights
 #pragma unroll
@@ -706,7 +712,12 @@ __global__ void __launch_bounds__(GramShape<T, RT, KIND>::NTH, 2)
                     if (lg == 0) ws[slot] = sw;
                 }
                 __syncthreads();
-                if (base + KB < se) fetch(base + KB);
+                if (base + KB < se) {
+                    fetch(base + KB);
+                } else if (se < ce) {
+                    fetch(se);        // the next row's first stage (it starts at se)
+                    ahead = true;
+                }
                 eng.template accumulate<S>(hs, ws, (int)min((int64_t)KB, se - base));
                 __syncthreads();
             }
@@ -736,7 +747,7 @@ __global__ void __launch_bounds__(GramShape<T, RT, KIND>::NTH, 2)
                 }
             }
             if (re >= ce) break;
-            i = search_le(P.row_ptr, i + 1, last, re);   // next nonempty row
+            i = search_le_near(P.row_ptr, i + 1, last, re);   // next nonempty row
         }
     }
 }
@@ -892,7 +903,7 @@ __global__ void __launch_bounds__(128) gram_warp_kernel(const SolveParams<T> P, 
                     }
                 }
             if (re >= ce) break;
-            i = search_le(P.row_ptr, i + 1, last, re);   // next nonempty row
+            i = search_le_near(P.row_ptr, i + 1, last, re);   // next nonempty row
         }
     }
 }
@@ -965,6 +976,7 @@ __global__ void __launch_bounds__(128) gram_warp_mma_kernel(const SolveParams<fl
                     float b[V], e[V], h[V];
                     load_slice<float, V, VEC>(b, P.A1, __ldcs(P.c1 + qq), R, lg);
                     load_slice<float, V, VEC>(e, P.A2, __ldcs(P.c2 + qq), R, lg);
+
 #pragma unroll
                     for (int t = 0; t < V; ++t) h[t] = b[t] * e[t];
                     float sw;
@@ -1043,7 +1055,7 @@ __global__ void __launch_bounds__(128) gram_warp_mma_kernel(const SolveParams<fl
                     }
                 }
             if (re >= ce) break;
-            i = search_le(P.row_ptr, i + 1, last, re);   // next nonempty row
+            i = search_le_near(P.row_ptr, i + 1, last, re);   // next nonempty row
         }
     }
 }
@@ -1498,7 +1510,7 @@ __global__ void __launch_bounds__(128) refine_resid_kernel(const SolveParams<T> 
                 }
             }
             if (re >= ce) break;
-            i = search_le(P.row_ptr, i + 1, last, re);   // next nonempty row
+            i = search_le_near(P.row_ptr, i + 1, last, re);   // next nonempty row
         }
     }
 }
