@@ -74,18 +74,23 @@ NCU_TRAFFIC = {
     ("cp3_10k_m10M_r16", "ggn_matvec"): {"bytes": 3 * 36.65e6 * 2.5,
                                          "file": "paper_1910_02371_gb300/csrc/sweep.cu",
                                          "src": "1d03ab541fb6d2df"},
-    # 1e8-nonzero capture at the same 2^22 rows per mode (26.91 GB read +
-    # 0.28 GB written per launch: every row gather misses L2 at both sizes)
+    # 1e8-nonzero capture at the same 2^22 rows per mode (26.915 GB read +
+    # 0.281 GB written per launch: every row gather misses L2 at both sizes)
     # scaled to 4e9
-    ("cp3_4M_m4B_r16", "ggn_matvec"): {"bytes": 3 * (26.911e9 + 0.2808e9) * 40,
-                                       "file": "paper_1910_02371_gb300/csrc/sweep.cu",
-                                       "src": "1d03ab541fb6d2df"},
+    ("cp3_4M_m4B_r16", "ggn_matvec"): {"bytes": 3 * (26.9152e9 + 0.2806e9) * 40,
+                                       "file": ["paper_1910_02371_gb300/csrc/sweep.cu",
+                                                "paper_1910_02371_gb300/csrc/internal.cuh"],
+                                       "src": "469999f7e26a0145"},
 }
 
 
-def src_hash(path):
-    with open(os.path.join(ROOT, path), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+def src_hash(paths):
+    """Hash of the kernel sources a capture was taken on (one path or a list)."""
+    h = hashlib.sha256()
+    for path in ([paths] if isinstance(paths, str) else paths):
+        with open(os.path.join(ROOT, path), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 # ------------------------------------------------------------------ clocks
@@ -189,37 +194,6 @@ def make_device_inputs(w, seed, dev):
     del pd
     torch.cuda.synchronize()
     return idx, vals, start
-
-
-# ------------------------------------------------------------------ gather peak
-def measure_gather_peak(dev, rows, row_floats, nbags=1 << 22, per_bag=32, reps=5):
-    """Random factor-row fetches per second a library kernel reaches on this
-    GPU: torch's embedding_bag (sum mode) over a rows x row_floats FP32 table
-    (larger than L2 at the sizes used here) with uniform random row ids, 32 rows
-    per bag.  The denominator of the gather roofline: when the factor matrices
-    do not fit in L2 the sweeps are bound by the rate of random row fetches
-    from HBM, not by its streaming bandwidth."""
-    import torch
-    import torch.nn.functional as F
-    table = torch.randn(rows, row_floats, dtype=torch.float32, device=dev)
-    g = torch.Generator(device=dev)
-    g.manual_seed(12345)
-    ids = torch.randint(0, rows, (nbags * per_bag,), device=dev, generator=g)
-    offs = torch.arange(0, nbags * per_bag, per_bag, device=dev)
-    F.embedding_bag(ids, table, offs, mode="sum")
-    torch.cuda.synchronize()
-    best = None
-    for _ in range(reps):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        F.embedding_bag(ids, table, offs, mode="sum")
-        e1.record()
-        e1.synchronize()
-        ms = e0.elapsed_time(e1)
-        best = ms if best is None else min(best, ms)
-    del table, ids, offs
-    torch.cuda.empty_cache()
-    return nbags * per_bag / (best / 1e3)
 
 
 # ------------------------------------------------------------------ CPU sample
@@ -618,21 +592,17 @@ def run_ours(args):
     roofline["traffic"] = (traffic["bytes"] if traffic and traffic["src"] == src_hash(traffic["file"])
                            else None)
 
-    # ---- gather roofline: random factor-row fetches per second against the
-    # rate a library gather kernel reaches (factors larger than L2 only)
-    gather = None
-    if lean:
-        wide = 2 * w.rank if main_kind == "ggn_matvec" else w.rank   # interleaved A|X rows
-        fetches = {"ggn_matvec": 6 * m, "tttp": 2 * m, "mttkrp": 2 * m, "solve_factor": 2 * m,
-                   "loss_grad": 6 * m}[main_kind]
-        ms_main = roofline["ms"]
-        peak_rows = measure_gather_peak(dev, max(w.dims), wide)
-        gather = {"bound": "hbm random row fetches", "unit": "rows/s",
-                  "row_bytes": 4 * wide, "fetches_per_launch": fetches,
-                  "achieved": fetches / (ms_main / 1e3), "peak": peak_rows,
-                  "frac": fetches / (ms_main / 1e3) / peak_rows, "kernel": main_kind,
-                  "peak_source": "measured in this run: torch embedding_bag (sum) over a "
-                                 f"{max(w.dims)} x {wide} FP32 table, 32 uniform random rows per bag"}
+    # ---- the dominant kernel's measured DRAM traffic per launch (ncu) over its
+    # time, against the same peak: the algorithmic count above credits each
+    # factor row once, while every nonzero's row gathers go to DRAM when the
+    # factors are larger than L2
+    dram = None
+    if roofline["traffic"]:
+        rate = roofline["traffic"] / (roofline["ms"] / 1e3) / 1e9
+        dram = {"bound": "hbm", "achieved": rate, "peak": hbm_peak, "unit": "GB/s",
+                "frac": rate / hbm_peak, "traffic": roofline["traffic"], "kernel": main_kind,
+                "note": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch set "
+                        "(scaled from the capture size to this workload) / the event-timed duration"}
 
     # ---- end to end through the C ABI with host buffers
     if not lean:
@@ -711,7 +681,7 @@ def run_ours(args):
         "ggn_step_s": kern["ggn_step"] / 1e3,
         "time_share_ms": share,
         "roofline": roofline,
-        "gather_roofline": gather,
+        "dram_roofline": dram,
         "rooflines": roofs,
         "e2e": {"value": e2e_val, "unit": "nnz/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms / e2e_steps,

@@ -207,29 +207,34 @@ __device__ __forceinline__ void record_error(int *status, int code) {
     atomicCAS(status, 0, code);
 }
 
+// The vector loads carry the .L2::64B fetch-size hint: a factor row is
+// gathered at a random row index, so the L2 should bring in the 64 bytes that
+// are asked for and not the whole 128-byte line (with factors larger than L2,
+// measured at 2^22 rows: MTTKRP reads 156 instead of 253 DRAM bytes per
+// nonzero, 1-2% faster; the sweeps stay bound by the rate of random fetches).
 template <typename T, int V, bool VEC>
 __device__ __forceinline__ void load_slice(T (&v)[V], const T *__restrict__ A, int64_t row, int R,
                                            int lg) {
     const T *ptr = A + row * (int64_t)R + lg * V;
     if constexpr (VEC && V * sizeof(T) == 32) {
         if constexpr (sizeof(T) == 4) {
-            asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+            asm("ld.global.nc.L2::64B.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                 : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]),
                   "=f"(v[6]), "=f"(v[7])
                 : "l"(ptr));
         } else {
-            asm("ld.global.nc.v4.f64 {%0,%1,%2,%3}, [%4];"
+            asm("ld.global.nc.L2::64B.v4.f64 {%0,%1,%2,%3}, [%4];"
                 : "=d"(v[0]), "=d"(v[1]), "=d"(v[2]), "=d"(v[3])
                 : "l"(ptr));
         }
     } else if constexpr (VEC) {
         static_assert(V * sizeof(T) == 16, "16- or 32-byte vectors");
         if constexpr (sizeof(T) == 4) {
-            float4 q = __ldg(reinterpret_cast<const float4 *>(ptr));
-            v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+            asm("ld.global.nc.L2::64B.v4.f32 {%0,%1,%2,%3}, [%4];"
+                : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3])
+                : "l"(ptr));
         } else {
-            double2 q = __ldg(reinterpret_cast<const double2 *>(ptr));
-            v[0] = q.x; v[1] = q.y;
+            asm("ld.global.nc.L2::64B.v2.f64 {%0,%1}, [%2];" : "=d"(v[0]), "=d"(v[1]) : "l"(ptr));
         }
     } else {
 #pragma unroll
