@@ -80,7 +80,10 @@ typedef enum {
     TC_ERR_NOT_SPD = 6,     /* a row system had a pivot <= 0; that row was not written */
     TC_ERR_DOMAIN = 7,      /* Poisson identity-link loss at a model entry <= 0 */
     TC_ERR_BREAKDOWN = 8,   /* CG: p^T H p <= 0; later iterations left x unchanged */
-    TC_ERR_UNSUPPORTED = 9  /* a valid request this build does not implement */
+    TC_ERR_UNSUPPORTED = 9, /* a valid request this build does not implement */
+    TC_ERR_TIMEOUT = 10     /* a kernel's wait for its own tensor-core work passed its time
+                               limit (2 s); the kernel gave up and its outputs are incomplete.
+                               Not expected in normal operation. */
 } tc_status;
 
 typedef enum { TC_F32 = 0, TC_F64 = 1 } tc_dtype;

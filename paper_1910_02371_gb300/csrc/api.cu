@@ -44,6 +44,7 @@ const char *tc_status_string(tc_status s) {
         case TC_ERR_DOMAIN: return "loss evaluated outside its domain";
         case TC_ERR_BREAKDOWN: return "CG breakdown";
         case TC_ERR_UNSUPPORTED: return "unsupported";
+        case TC_ERR_TIMEOUT: return "device wait timed out";
     }
     return "unknown status";
 }

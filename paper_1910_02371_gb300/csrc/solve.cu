@@ -752,6 +752,323 @@ __global__ void __launch_bounds__(GramShape<T, RT, KIND>::NTH, 2)
     }
 }
 
+// ------------------------------------------------------------------ kernel A, tcgen05, R = 64
+// The TF32 and BF16 forms at R = 64 on the fifth-generation tensor cores:
+// tcgen05.mma with the accumulator in tensor memory (TMEM), issued by one
+// thread, the operands staged by the block in shared memory in the no-swizzle
+// K-major layout (core matrices of 8 rows x 16 bytes).  One row segment at a
+// time, in stages of 32 nonzeros: the block gathers h_e (rounded to the input
+// type) and s_e h_e into one of two stage buffers, thread 0 issues the stage's
+// MMAs -- D[m][n] += sum_k A[m][k] B[n][k] with A = h, B = s h -- and commits
+// them to that buffer's mbarrier, and the block gathers the next stage into
+// the other buffer meanwhile.  The MMA shape is M = 128, N = 64: rows 64..127
+// of A stay zero, and D's rows 0..63 (TMEM lanes 0..63) hold G_i.  At the
+// row's end warps 0 and 1 read them (tcgen05.ld) and write the packed lower
+// triangle, or add it with FP64 atomics into the cut slot of a row that
+// crosses a chunk boundary.  Every mbarrier wait has a time limit; past it the
+// block records TC_ERR_TIMEOUT, lets its committed MMAs finish (bounded),
+// frees its TMEM and leaves.
+namespace tc05 {
+
+constexpr int KB = 32;          // nonzeros per stage
+constexpr int MM = 128;         // MMA rows (A's rows 64..127 are zero)
+constexpr int NN = 64;          // MMA columns = R
+constexpr int LBO = 128;        // bytes between core matrices adjacent in K
+constexpr int THREADS = 128;
+constexpr uint32_t TMEM_COLS = 128;    // two accumulators of 64 columns
+constexpr uint64_t WAIT_NS = 2000000000ull;
+
+template <int KIND>
+struct Geo {
+    static constexpr int EB = KIND == GK_BF16 ? 2 : 4;        // bytes per element
+    static constexpr int EPC = 16 / EB;                       // K elements per core-matrix row
+    static constexpr int SBO = (KB / EPC) * 128;              // bytes between 8-row groups
+    static constexpr int A_BYTES = MM * KB * EB;
+    static constexpr int B_BYTES = NN * KB * EB;
+    static constexpr int STAGE = A_BYTES + B_BYTES;
+    static constexpr int KI = KIND == GK_BF16 ? 16 : 8;       // K per instruction
+    static constexpr int NI = KB / KI;                        // instructions per stage
+    static constexpr int SMEM = 2 * STAGE + 128;              // + room to align the base
+    // instruction descriptor: D FP32 (bits 4-5), A and B type (bits 7-9 and
+    // 10-12: 2 = TF32 for kind::tf32, 1 = BF16 for kind::f16), both K-major,
+    // N >> 3 (bits 17-22), M >> 4 (bits 24-28)
+    static constexpr uint32_t IDESC = (1u << 4) | ((KIND == GK_BF16 ? 1u : 2u) << 7) |
+                                      ((KIND == GK_BF16 ? 1u : 2u) << 10) |
+                                      ((uint32_t)(NN >> 3) << 17) | ((uint32_t)(MM >> 4) << 24);
+    // byte offset of element (row, k) of an operand tile
+    __device__ static __forceinline__ int off(int row, int k) {
+        return (row >> 3) * SBO + (k / EPC) * LBO + (row & 7) * 16 + (k % EPC) * EB;
+    }
+};
+
+// Shared-memory matrix descriptor: start address, leading (K) and stride
+// (8-row group) byte offsets in 16-byte units, the fixed version bits 46-48 =
+// 0b001, base offset 0, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, int sbo) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((LBO >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void *ptr) {
+    return (uint32_t)__cvta_generic_to_shared(ptr);
+}
+
+// Orders this thread's generic-proxy shared-memory stores before the tensor
+// core's (asynchronous-proxy) reads of them.
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ uint16_t to_bf16(float x) {
+    uint16_t r;
+    asm("cvt.rn.bf16.f32 %0, %1;" : "=h"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ uint64_t now_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Waits for the completion of phase `parity` of the mbarrier; false if the
+// limit passed first.
+__device__ __forceinline__ bool wait_phase(uint32_t bar, uint32_t parity, uint64_t limit) {
+    uint32_t done = 0;
+    uint64_t t0 = 0;
+    for (;;) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        const uint64_t t = now_ns();
+        if (t0 == 0) t0 = t;
+        else if (t - t0 > limit) return false;
+    }
+}
+
+__device__ __forceinline__ void mma(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc,
+                                    uint32_t acc, int kind_bf16) {
+    if (kind_bf16)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+            : "memory");
+    else
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+            : "memory");
+}
+
+__device__ __forceinline__ void commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+}  // namespace tc05
+
+template <int KIND>
+__global__ void __launch_bounds__(tc05::THREADS) gram_tc05_kernel(const SolveParams<float> P,
+                                                                 const Batch<float> B) {
+    using Q = tc05::Geo<KIND>;
+    constexpr int R = 64, TRI = R * (R + 1) / 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ uint32_t tmem_slot;
+    unsigned char *base =
+        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t sbase = tc05::smem_addr(base);
+    const uint32_t bar0 = tc05::smem_addr(&mbar[0]);
+
+    // rows 64..127 of A stay zero in both stage buffers
+    for (int o = tid * 4; o < Q::A_BYTES / 2; o += tc05::THREADS * 4) {
+        *reinterpret_cast<uint32_t *>(base + Q::A_BYTES / 2 + o) = 0u;
+        *reinterpret_cast<uint32_t *>(base + Q::STAGE + Q::A_BYTES / 2 + o) = 0u;
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         tc05::smem_addr(&tmem_slot)),
+                     "r"(tc05::TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc05::fence_before();
+    __syncthreads();
+    tc05::fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    const int64_t nb = __ldg(P.row_ptr + B.row0), ne = __ldg(P.row_ptr + B.row0 + B.nrows);
+    const int64_t last = B.row0 + B.nrows - 1;
+    // gather mapping: lane i of warp w holds nonzero slots 8w + 4h + i % 4
+    // (h = 0, 1) and components i / 4 + 8j (j = 0..7), so each shared store of
+    // a warp fills one core matrix (or half of one for BF16) without conflicts
+    const int kl = lane & 3, m0 = lane >> 2;
+    int st_cnt = 0;            // stages committed by this block
+    int row_cnt = 0;           // row segments started by this block
+    bool ok = true;
+    // The row segment whose Gram is still in TMEM: its epilogue runs once the
+    // next segment's first MMAs are issued (into the other accumulator), so
+    // its MMA latency and read-out overlap the next segment's work.
+    struct Pending {
+        int64_t row, slot;
+        int stage, dbuf;
+        bool whole, valid;
+    } pend{0, -1, 0, 0, false, false};
+
+    // waits for a segment's last stage, reads its accumulator and writes the
+    // packed lower triangle (or adds it into its cut slot); block-wide
+    auto epilogue = [&](const Pending &pr) -> bool {
+        const bool w = tc05::wait_phase(bar0 + 8 * (pr.stage & 1), (uint32_t)((pr.stage >> 1) & 1),
+                                        tc05::WAIT_NS);
+        if (__syncthreads_or(!w)) return false;
+        tc05::fence_after();
+        if (warp < 2) {
+            const int r = 32 * warp + lane;
+            float *lrow = B.light + (pr.row - B.row0) * (int64_t)TRI + tri_idx(r, 0);
+            double *crow = pr.slot >= 0 ? B.cut + pr.slot * (int64_t)TRI + tri_idx(r, 0) : nullptr;
+#pragma unroll
+            for (int c0 = 0; c0 < R; c0 += 16) {
+                float v[16];
+                tc05::ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(pr.dbuf * tc05::NN + c0), v);
+#pragma unroll
+                for (int c = 0; c < 16; ++c) {
+                    if (c0 + c > r) continue;
+                    if (pr.whole) lrow[c0 + c] = v[c];
+                    else add_cut(crow + c0 + c, v[c]);
+                }
+            }
+        }
+        tc05::fence_before();
+        __syncthreads();              // that accumulator is free again
+        return true;
+    };
+
+    for (int64_t cs = nb + (int64_t)blockIdx.x * B.ch; cs < ne && ok; cs += (int64_t)gridDim.x * B.ch) {
+        const int64_t ce = min(cs + B.ch, ne);
+        int64_t i = search_le(P.row_ptr, B.row0, last, cs);
+        for (;;) {
+            const int64_t rs = __ldg(P.row_ptr + i), re = __ldg(P.row_ptr + i + 1);
+            const int64_t ss = max(rs, cs), se = min(re, ce);
+            const int dbuf = row_cnt & 1;
+            for (int64_t sb = ss; sb < se; sb += tc05::KB) {
+                const int buf = st_cnt & 1;
+                const uint32_t bar = bar0 + 8 * buf;
+                if (st_cnt >= 2) {     // the MMAs that last read this buffer are done
+                    const bool w = tc05::wait_phase(bar, (uint32_t)(((st_cnt - 2) >> 1) & 1), tc05::WAIT_NS);
+                    if (__syncthreads_or(!w)) {
+                        ok = false;
+                        break;
+                    }
+                }
+                unsigned char *As = base + buf * Q::STAGE, *Bs = As + Q::A_BYTES;
+#pragma unroll
+                for (int hh = 0; hh < 2; ++hh) {
+                    const int k = 8 * warp + 4 * hh + kl;
+                    const int64_t q = sb + k;
+                    const bool valid = q < se;
+                    float bv[8], ev[8], sw = 0.f;
+                    if (valid) {
+                        const float *br = P.A1 + (int64_t)__ldcs(P.c1 + q) * R;
+                        const float *er = P.A2 + (int64_t)__ldcs(P.c2 + q) * R;
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            bv[j] = __ldg(br + m0 + 8 * j);
+                            ev[j] = __ldg(er + m0 + 8 * j);
+                        }
+                        sw = weight_at(P.w, q);
+                    }
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const int m = m0 + 8 * j;
+                        const float h = valid ? bv[j] * ev[j] : 0.f;
+                        const float wh = sw * h;
+                        const int o = Q::off(m, k);
+                        if constexpr (KIND == GK_BF16) {
+                            *reinterpret_cast<uint16_t *>(As + o) = tc05::to_bf16(h);
+                            *reinterpret_cast<uint16_t *>(Bs + o) = tc05::to_bf16(wh);
+                        } else {
+                            *reinterpret_cast<uint32_t *>(As + o) = to_tf32(h);
+                            *reinterpret_cast<uint32_t *>(Bs + o) = to_tf32(wh);
+                        }
+                    }
+                }
+                tc05::fence_proxy_async();     // the stores, before the tensor core reads them
+                tc05::fence_before();
+                __syncthreads();
+                if (tid == 0) {
+                    tc05::fence_after();
+                    const uint32_t a0 = sbase + buf * Q::STAGE, b0 = a0 + Q::A_BYTES;
+#pragma unroll
+                    for (int ii = 0; ii < Q::NI; ++ii) {
+                        const uint32_t ko = (uint32_t)(ii * (Q::KI / Q::EPC) * tc05::LBO);
+                        tc05::mma(tmem + (uint32_t)(dbuf * tc05::NN), tc05::smem_desc(a0 + ko, Q::SBO),
+                                  tc05::smem_desc(b0 + ko, Q::SBO), Q::IDESC,
+                                  (sb > ss || ii > 0) ? 1u : 0u, KIND == GK_BF16);
+                    }
+                    tc05::commit(bar);
+                }
+                ++st_cnt;
+                if (sb == ss && pend.valid) {    // the previous segment, behind this one's MMAs
+                    if (!epilogue(pend)) {
+                        ok = false;
+                        break;
+                    }
+                    pend.valid = false;
+                }
+            }
+            if (!ok) break;
+            const bool whole = rs >= cs && re <= ce;
+            pend = Pending{i, whole ? -1 : cut_slot(rs, re, nb, B.ch), st_cnt - 1, dbuf, whole, true};
+            ++row_cnt;
+            if (re >= ce) break;
+            i = search_le_near(P.row_ptr, i + 1, last, re);   // next nonempty row
+        }
+    }
+    if (ok && pend.valid) ok = epilogue(pend);
+    if (!ok) {
+        if (tid == 0) record_error(P.status, TC_ERR_TIMEOUT);
+        // let the committed MMAs finish before the TMEM is released (bounded)
+        for (int s = st_cnt > 2 ? st_cnt - 2 : 0; s < st_cnt; ++s)
+            tc05::wait_phase(bar0 + 8 * (s & 1), (uint32_t)((s >> 1) & 1), tc05::WAIT_NS / 4);
+        tc05::fence_before();
+        __syncthreads();
+    }
+    if (warp == 0) {
+        tc05::fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(tc05::TMEM_COLS)
+                     : "memory");
+    }
+}
+
 // ------------------------------------------------------------------ kernel A, small ranks
 // For R <= 16 (FFMA form) every warp works alone: it takes every nwarps-th
 // chunk of the batch's nonzeros, stages DEPTH x NG nonzeros (h_e and weight)
@@ -1591,31 +1908,52 @@ static int64_t chunk_nnz(int64_t m, int64_t grid, const tc_solve_tuning &t) {
 // kernel otherwise.
 template <typename T, int RT, bool VEC, int KIND>
 struct GramLaunch {
-    static constexpr int VAR = (sizeof(T) == 8 && RT <= 16) ? 1 : (sizeof(T) == 4 && RT <= 32 && KIND != GK_FFMA) ? 2 : 0;
-    static constexpr bool PER_WARP = VAR != 0;
+    static constexpr int VAR = (sizeof(T) == 8 && RT <= 16) ? 1
+                               : (sizeof(T) == 4 && RT <= 32 && KIND != GK_FFMA) ? 2
+                               : (sizeof(T) == 4 && RT == 64 && VEC && (KIND == GK_TF32 || KIND == GK_BF16)) ? 3
+                                                                                                       : 0;
+    static constexpr bool PER_WARP = VAR == 1 || VAR == 2;
     static int threads() {
         if constexpr (VAR == 1) return WarpGram<T, RT>::NTH;
         else if constexpr (VAR == 2) return WarpMma<RT, KIND>::NTH;
+        else if constexpr (VAR == 3) return tc05::THREADS;
         else return GramGeo<T, RT, KIND>::NTH;
     }
     static size_t smem() {
         if constexpr (VAR == 1) return WarpGram<T, RT>::smem;
         else if constexpr (VAR == 2) return WarpMma<RT, KIND>::smem;
+        else if constexpr (VAR == 3) return tc05::Geo<KIND>::SMEM;
         else return GramGeo<T, RT, KIND>::smem;
     }
     static const void *fn() {
         if constexpr (VAR == 1) return (const void *)gram_warp_kernel<T, RT, VEC>;
         else if constexpr (VAR == 2) return (const void *)gram_warp_mma_kernel<RT, VEC, KIND>;
+        else if constexpr (VAR == 3) return (const void *)gram_tc05_kernel<KIND>;
         else return (const void *)gram_chunk_kernel<T, RT, VEC, KIND>;
     }
     // resident blocks per SM (queried once)
     static tc_status occupancy(int &occ) {
         static int cached = 0;
         if (!cached) {
-            if (smem() > 48 * 1024)
+            if (smem() > 48 * 1024) {
                 TC_CUDA(cudaFuncSetAttribute(fn(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem()));
+                // the whole unified L1 / shared array as shared memory, so that
+                // several blocks of this size fit per SM (the occupancy query
+                // below assumes the carveout set here)
+                TC_CUDA(cudaFuncSetAttribute(fn(), cudaFuncAttributePreferredSharedMemoryCarveout,
+                                             (int)cudaSharedmemCarveoutMaxShared));
+            }
             int v = 0;
             TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, fn(), threads(), smem()));
+            if constexpr (VAR == 3) {
+                // the tcgen05 kernel: the query answers 1 block per SM (measured);
+                // shared memory (with 1 KB reserved per block), 64 registers per
+                // thread and 128 of the 512 TMEM columns per block allow more
+                int by_smem = (int)((228 * 1024) / (smem() + 1024 + 64));
+                const int by_tmem = 512 / (int)tc05::TMEM_COLS;
+                if (by_smem > by_tmem) by_smem = by_tmem;
+                if (by_smem > v) v = by_smem;
+            }
             cached = v > 0 ? v : 1;
         }
         occ = cached;
@@ -1626,6 +1964,8 @@ struct GramLaunch {
             gram_warp_kernel<T, RT, VEC><<<(unsigned)grid, threads(), smem(), st>>>(P, Bt);
         else if constexpr (VAR == 2)
             gram_warp_mma_kernel<RT, VEC, KIND><<<(unsigned)grid, threads(), smem(), st>>>(P, Bt);
+        else if constexpr (VAR == 3)
+            gram_tc05_kernel<KIND><<<(unsigned)grid, threads(), smem(), st>>>(P, Bt);
         else
             gram_chunk_kernel<T, RT, VEC, KIND><<<(unsigned)grid, threads(), smem(), st>>>(P, Bt);
     }

@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libtc.so")
 
 OK, ERR_ARG, ERR_RANGE, ERR_DUPLICATE, ERR_OOM, ERR_CUDA, ERR_NOT_SPD, ERR_DOMAIN, \
-    ERR_BREAKDOWN, ERR_UNSUPPORTED = range(10)
+    ERR_BREAKDOWN, ERR_UNSUPPORTED, ERR_TIMEOUT = range(11)
 F32, F64 = 0, 1
 LOSSES = {"ls": 0, "poisson_log": 1, "poisson_id": 2}
 W_ONE, W_VALUES, W_ARRAY = 0, 1, 2
