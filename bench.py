@@ -359,13 +359,19 @@ def run_ours(args):
     if args.solve_probe is not None:
         # Solve Factor on one mode (right-hand side: the MTTKRP of the values),
         # timed alone in each form of --prec (comma-separated, in that order:
-        # one untimed call, then --steps timed calls per form): the command the
-        # Solve Factor profiles use
+        # one untimed call, then --steps timed calls per form; "form@warp" or
+        # "form@tc05" forces the R = 64 Gram engine): the command the Solve
+        # Factor profiles use
         d = args.solve_probe
         b = tc.mttkrp(p, A, d)
         out = torch.empty_like(b)
         ms = {}
-        for form in args.prec.split(","):
+        engines = {"": tc.GRAM_AUTO, "warp": tc.GRAM_WARP_MMA, "tc05": tc.GRAM_TCGEN05}
+        for spec in args.prec.split(","):
+            form, _, eng = spec.partition("@")
+            tc.set_solve_tuning(f32, 0, reset=True)
+            if eng:
+                tc.set_solve_tuning(f32, w.rank, gram_kernel=engines[eng])
             tc.solve_factor(p, A, d, b, w.lam, out=out, prec=form)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -374,7 +380,8 @@ def run_ours(args):
                 tc.solve_factor(p, A, d, b, w.lam, out=out, prec=form)
             e1.record()
             e1.synchronize()
-            ms[form] = e0.elapsed_time(e1) / args.steps
+            ms[spec] = e0.elapsed_time(e1) / args.steps
+        tc.set_solve_tuning(f32, 0, reset=True)
         if tc.last_error(p) != tc.OK:
             raise RuntimeError("device error in the Solve Factor probe")
         if rank == 0:

@@ -248,9 +248,15 @@ tc_status tc_solve_factor(const tc_pattern *p, tc_weights w, const void *s, int 
  *                block, a power of two in [256, 16384]);
  *   batch_bytes  >= 0; 0: automatic (1 GiB).  At least one warp's rows are
  *                taken per batch whatever the value.
- *   chol_rows_per_warp  for R <= 32 the FP64 factorization runs one row per
- *                lane; fewer rows per warp spread a small mode over more
- *                warps (0: automatic).
+ *   chol_rows_per_warp  for R <= 32 one warp factors this many rows
+ *                together, 32 / rows lanes sharing each row's work; fewer
+ *                rows per warp spread a small mode over more warps
+ *                (0: automatic, 16 for R <= 16 and 8 for R <= 32).
+ *   gram_kernel  the Gram engine where two exist -- FP32 data, R = 64, the
+ *                TF32 and BF16 forms: TC_GRAM_AUTO (0, the tcgen05 kernel),
+ *                TC_GRAM_WARP_MMA (warp-level mma.sync, 4-warp blocks
+ *                splitting the output tiles) or TC_GRAM_TCGEN05 (tcgen05.mma
+ *                with the accumulator in tensor memory).  Ignored elsewhere.
  * Settings are process-wide, per dtype and rank tier (the tier of R: 1..8,
  * 9..16, 17..32, 33..64; R = 0 sets every tier).  t == NULL restores the
  * automatic choice.  Reads and writes of the setting are locked, and each
@@ -259,9 +265,12 @@ tc_status tc_solve_factor(const tc_pattern *p, tc_weights w, const void *s, int 
 typedef struct {
     int64_t chunk_nnz;
     int64_t batch_bytes;
-    int32_t chol_rows_per_warp;  /* R <= 32: rows one warp factors (one per lane):
+    int32_t chol_rows_per_warp;  /* R <= 32: rows one warp factors together:
                                     1, 2, 4, 8, 16 or 32; 0: automatic */
+    int32_t gram_kernel;         /* TC_GRAM_*; 0: automatic */
 } tc_solve_tuning;
+
+enum { TC_GRAM_AUTO = 0, TC_GRAM_WARP_MMA = 1, TC_GRAM_TCGEN05 = 2 };
 
 tc_status tc_set_solve_tuning(tc_dtype dtype, int R, const tc_solve_tuning *t);
 tc_status tc_get_solve_tuning(tc_dtype dtype, int R, tc_solve_tuning *t);
@@ -269,8 +278,9 @@ tc_status tc_get_solve_tuning(tc_dtype dtype, int R, tc_solve_tuning *t);
 /* Autotuner for Solve Factor (a service of the library; the paper tunes by
  * hand).  Runs tc_solve_factor on the given inputs at each candidate tuning of
  * the rank tier of R -- chunk_nnz in {automatic, 256, 1024, 4096, 16384} times
- * chol_rows_per_warp in {8, 16, 32} (R <= 16) or {4, 8, 16} (R <= 32) -- once
- * untimed and once timed with CUDA events on `stream`, and installs the
+ * chol_rows_per_warp in {8, 16, 32} (R <= 16) or {4, 8, 16} (R <= 32), times
+ * gram_kernel in {TC_GRAM_WARP_MMA, TC_GRAM_TCGEN05} where both engines exist
+ * (FP32 data, R = 64, the TF32 and BF16 forms) -- once untimed and once timed with CUDA events on `stream`, and installs the
  * fastest for the pattern's dtype (batch_bytes is kept).  Each candidate is
  * handed to the timed calls directly: the process-wide setting that other
  * threads' calls read changes only once, to the winner, and not at all on an

@@ -1399,11 +1399,31 @@ __device__ __forceinline__ void gram_source(const SolveParams<T> &P, const Batch
 }
 
 // ------------------------------------------------------------------ kernel B, R <= 32
-// One row per lane, rpw rows per warp.  Shared layout: packed entry e of slot
-// s at e * (rpw + 1) + s (the pad keeps the transposing loads and the per-lane
-// accesses on distinct banks).  With refinement the factor L is written back
-// over the batch's Gram rows (pattern dtype; a zero first entry marks a row
-// that did not factor) for the correction step.
+// rpw rows per warp, lpr = 32 / rpw lanes per row (lane = slot * lpr + sub).
+// Shared layout: packed entry e of slot s at e * (rpw + 1) + s.  Every slot
+// runs the same sequence of entries, so the lpr lanes of a row deal each
+// step's work among themselves round-robin -- the entries of the trailing
+// update, the rows of a substitution step, the columns of L^-1, the entries
+// of the inverse -- and the warp meets at a barrier between steps.  FP64
+// throughput on this part is charged per warp instruction, so filling all 32
+// lanes (rather than one lane per row) is what keeps the pipe busy with
+// useful work.  A row that is not positive definite runs on, on values that
+// are discarded, so the warp keeps one instruction stream through every
+// barrier.  Inverse mode keeps L^-1 in a second triangle (out of place, so
+// its columns are independent).  With refinement the factor L is written
+// back over the batch's Gram rows (pattern dtype; a zero first entry marks a
+// row that did not factor) for the correction step.
+
+// Moves (a, b) -- row and column of a packed lower-triangle entry -- forward
+// by `step` entries.
+__device__ __forceinline__ void tri_advance(int &a, int &b, int step) {
+    b += step;
+    while (b > a) {
+        b -= a + 1;
+        ++a;
+    }
+}
+
 template <typename T, typename CT>
 __global__ void __launch_bounds__(32) chol_rows_kernel(const SolveParams<T> P, const Batch<T> B,
                                                        int rpw) {
@@ -1411,21 +1431,23 @@ __global__ void __launch_bounds__(32) chol_rows_kernel(const SolveParams<T> P, c
     CT *sh = reinterpret_cast<CT *>(sh_raw);
     const int lane = threadIdx.x;
     const int R = P.R, tri = R * (R + 1) / 2, ps = rpw + 1;
-    const int64_t grp = blockIdx.x;
+    const int lpr = 32 / rpw, slot = lane / lpr, sub = lane - slot * lpr;
+    const bool inv_mode = P.pinv != nullptr;
+    const int64_t q0 = (int64_t)blockIdx.x * rpw;
+    const int nr = (int)min((int64_t)rpw, B.nrows - q0);
     const int64_t nb = __ldg(P.row_ptr + B.row0);
     CT *Tri = sh;
     CT *Vv = sh + (int64_t)tri * ps;
     CT *Dinv = Vv + (int64_t)R * ps;
+    CT *Yt = Dinv + (int64_t)R * ps;         // inverse mode: L^-1
     {
-        // every lane finds its own row's Gram (in parallel), then the warp
-        // copies all rows' triangles in one flat loop, the row pointers
-        // broadcast by shuffles, so no load waits on another
-        const int64_t q0 = grp * rpw;
-        const int nr = (int)min((int64_t)rpw, B.nrows - q0);
+        // the first nr lanes find their rows' Gram sources (in parallel), then
+        // the warp copies every slot's triangle in one flat loop, the row
+        // pointers broadcast by shuffles; slots past the batch get zeros
         const T *lmine = nullptr;
         const double *cmine = nullptr;
         if (lane < nr) gram_source(P, B, nb, B.row0 + q0 + lane, tri, lmine, cmine);
-        const int n = nr * tri;
+        const int n = rpw * tri;
 #pragma unroll 4
         for (int base = 0; base < n; base += 32) {
             const int idx = base + lane;
@@ -1440,126 +1462,145 @@ __global__ void __launch_bounds__(32) chol_rows_kernel(const SolveParams<T> P, c
             }
         }
     }
-    __syncwarp();
-    const int slot = lane;
-    const bool mine = slot < rpw && grp * rpw + slot < B.nrows;
-    const int64_t i = B.row0 + grp * rpw + slot;
+    const bool mine = slot < nr;
+    const int64_t i = B.row0 + q0 + slot;
 #define TC_TRI(r, c) Tri[tri_idx(r, c) * ps + slot]
+#define TC_Y(r, c) Yt[tri_idx(r, c) * ps + slot]
 #define TC_VEC(r) Vv[(r) * ps + slot]
 #define TC_DINV(r) Dinv[(r) * ps + slot]
-    if (mine) {
-        for (int r = 0; r < R; ++r) TC_TRI(r, r) += (CT)P.lambda;
-        bool ok = true;
-        for (int j = 0; j < R; ++j) {
-            const CT dj = TC_TRI(j, j);
-            if (!(dj > CT(0))) {
-                ok = false;
-                break;
-            }
-            const CT inv = rsqrt_nr(dj), ljj = dj * inv;
+    __syncwarp();
+    for (int r = sub; r < R; r += lpr) TC_TRI(r, r) += (CT)P.lambda;
+    __syncwarp();
+    bool ok = true;
+    for (int j = 0; j < R; ++j) {
+        const CT dj = TC_TRI(j, j);
+        ok = ok && dj > CT(0);
+        const CT inv = rsqrt_nr(dj), ljj = dj * inv;
+        __syncwarp();                         // every lane has read the pivot
+        if (sub == 0) {
             TC_TRI(j, j) = ljj;
             TC_DINV(j) = inv;
-            for (int r = j + 1; r < R; ++r) TC_TRI(r, j) *= inv;
-            for (int r = j + 1; r < R; ++r) {
-                const CT lrj = TC_TRI(r, j);
-                // four entries per pass, loads before stores (independent FMAs)
-                int k = j + 1;
-                for (; k + 3 <= r; k += 4) {
-                    const CT a0 = TC_TRI(r, k), a1 = TC_TRI(r, k + 1), a2 = TC_TRI(r, k + 2),
-                                 a3 = TC_TRI(r, k + 3);
-                    const CT b0 = TC_TRI(k, j), b1 = TC_TRI(k + 1, j), b2 = TC_TRI(k + 2, j),
-                                 b3 = TC_TRI(k + 3, j);
-                    TC_TRI(r, k) = a0 - lrj * b0;
-                    TC_TRI(r, k + 1) = a1 - lrj * b1;
-                    TC_TRI(r, k + 2) = a2 - lrj * b2;
-                    TC_TRI(r, k + 3) = a3 - lrj * b3;
+        }
+        for (int r = j + 1 + sub; r < R; r += lpr) TC_TRI(r, j) *= inv;
+        __syncwarp();
+        // trailing update of rows and columns j+1 .. R-1: entry (a, b) of the
+        // trailing triangle is (j+1+a, j+1+b); four entries per pass, loads
+        // before stores (entries of one step are distinct, column j is read only)
+        const int n1 = R - 1 - j, ntr = n1 * (n1 + 1) / 2, c0 = j + 1;
+        int a = 0, b = 0;
+        tri_advance(a, b, sub);
+        int t = sub;
+        for (; t + 3 * lpr < ntr; t += 4 * lpr) {
+            const int a0 = a, b0 = b;
+            tri_advance(a, b, lpr);
+            const int a1 = a, b1 = b;
+            tri_advance(a, b, lpr);
+            const int a2 = a, b2 = b;
+            tri_advance(a, b, lpr);
+            const int a3 = a, b3 = b;
+            tri_advance(a, b, lpr);
+            const CT x0 = TC_TRI(c0 + a0, c0 + b0), x1 = TC_TRI(c0 + a1, c0 + b1),
+                     x2 = TC_TRI(c0 + a2, c0 + b2), x3 = TC_TRI(c0 + a3, c0 + b3);
+            const CT r0 = TC_TRI(c0 + a0, j), r1 = TC_TRI(c0 + a1, j), r2 = TC_TRI(c0 + a2, j),
+                     r3 = TC_TRI(c0 + a3, j);
+            const CT k0 = TC_TRI(c0 + b0, j), k1 = TC_TRI(c0 + b1, j), k2 = TC_TRI(c0 + b2, j),
+                     k3 = TC_TRI(c0 + b3, j);
+            TC_TRI(c0 + a0, c0 + b0) = x0 - r0 * k0;
+            TC_TRI(c0 + a1, c0 + b1) = x1 - r1 * k1;
+            TC_TRI(c0 + a2, c0 + b2) = x2 - r2 * k2;
+            TC_TRI(c0 + a3, c0 + b3) = x3 - r3 * k3;
+        }
+        for (; t < ntr; t += lpr) {
+            TC_TRI(c0 + a, c0 + b) -= TC_TRI(c0 + a, j) * TC_TRI(c0 + b, j);
+            tri_advance(a, b, lpr);
+        }
+        __syncwarp();
+    }
+    if (!inv_mode) {
+        for (int r = sub; r < R; r += lpr) TC_VEC(r) = mine ? (CT)P.rhs[i * (int64_t)R + r] : CT(0);
+        __syncwarp();
+        for (int j = 0; j < R; ++j) {        // L y = b, by columns
+            const CT yj = TC_VEC(j) * TC_DINV(j);
+            __syncwarp();
+            if (sub == 0) TC_VEC(j) = yj;
+            for (int r = j + 1 + sub; r < R; r += lpr) TC_VEC(r) -= TC_TRI(r, j) * yj;
+            __syncwarp();
+        }
+        for (int j = R - 1; j >= 0; --j) {   // L^T x = y, by rows of L
+            const CT xj = TC_VEC(j) * TC_DINV(j);
+            __syncwarp();
+            if (sub == 0) TC_VEC(j) = xj;
+            for (int r = sub; r < j; r += lpr) TC_VEC(r) -= TC_TRI(j, r) * xj;
+            __syncwarp();
+        }
+        if (mine && ok)
+            for (int r = sub; r < R; r += lpr) P.out[i * (int64_t)R + r] = (T)TC_VEC(r);
+    } else {
+        // L^-1, column c by the lane sub == the snake order of c (columns of
+        // decreasing length dealt 0, 1, .., lpr-1, lpr-1, .., 0, ...): for r > c,
+        // L^-1[r][c] = -(sum_{k=c}^{r-1} L[r][k] L^-1[k][c]) / L[r][r]; two
+        // partial sums per dot product (the dots are short, and each extra
+        // fold is one more FP64 warp instruction)
+        for (int c = 0; c < R; ++c) {
+            const int m = c % (2 * lpr);
+            if ((m < lpr ? m : 2 * lpr - 1 - m) != sub) continue;
+            TC_Y(c, c) = TC_DINV(c);
+            for (int r = c + 1; r < R; ++r) {
+                CT v0 = CT(0), v1 = CT(0);
+                int k = c;
+                for (; k + 1 < r; k += 2) {
+                    v0 += TC_TRI(r, k) * TC_Y(k, c);
+                    v1 += TC_TRI(r, k + 1) * TC_Y(k + 1, c);
                 }
-                for (; k <= r; ++k) TC_TRI(r, k) -= lrj * TC_TRI(k, j);
+                if (k < r) v0 += TC_TRI(r, k) * TC_Y(k, c);
+                TC_Y(r, c) = -(v0 + v1) * TC_DINV(r);
             }
         }
-        if (!ok) {
-            record_error(P.status, TC_ERR_NOT_SPD);
-            if (P.row_status) P.row_status[i] = 1;
-            if (P.pinv) {  // an identity block keeps the preconditioner defined
-                T *Po = P.pinv + i * (int64_t)R * R;
-                for (int q = 0; q < R * R; ++q) Po[q] = (q / R == q % R) ? T(1) : T(0);
-            }
-            TC_TRI(0, 0) = CT(0);
-        } else {
-            if (P.row_status) P.row_status[i] = 0;
-            if (!P.pinv) {
-                for (int r = 0; r < R; ++r) {           // L y = b
-                    CT v0 = (CT)P.rhs[i * (int64_t)R + r], v1 = CT(0), v2 = CT(0), v3 = CT(0);
-                    int k = 0;
-                    for (; k + 3 < r; k += 4) {
-                        v0 -= TC_TRI(r, k) * TC_VEC(k);
-                        v1 -= TC_TRI(r, k + 1) * TC_VEC(k + 1);
-                        v2 -= TC_TRI(r, k + 2) * TC_VEC(k + 2);
-                        v3 -= TC_TRI(r, k + 3) * TC_VEC(k + 3);
-                    }
-                    for (; k < r; ++k) v0 -= TC_TRI(r, k) * TC_VEC(k);
-                    TC_VEC(r) = ((v0 + v1) + (v2 + v3)) * TC_DINV(r);
+        __syncwarp();
+        // (L L^T)^-1 [r][c] = sum_{k >= r} L^-1[k][r] L^-1[k][c], c <= r; the
+        // packed entries dealt round-robin
+        if (mine && ok) {
+            T *Po = P.pinv + i * (int64_t)R * R;
+            int r = 0, c = 0;
+            tri_advance(r, c, sub);
+            for (int t = sub; t < tri; t += lpr) {
+                CT v0 = CT(0), v1 = CT(0);
+                int k = r;
+                for (; k + 1 < R; k += 2) {
+                    v0 += TC_Y(k, r) * TC_Y(k, c);
+                    v1 += TC_Y(k + 1, r) * TC_Y(k + 1, c);
                 }
-                for (int r = R - 1; r >= 0; --r) {      // L^T x = y
-                    CT v0 = TC_VEC(r), v1 = CT(0), v2 = CT(0), v3 = CT(0);
-                    int k = r + 1;
-                    for (; k + 3 < R; k += 4) {
-                        v0 -= TC_TRI(k, r) * TC_VEC(k);
-                        v1 -= TC_TRI(k + 1, r) * TC_VEC(k + 1);
-                        v2 -= TC_TRI(k + 2, r) * TC_VEC(k + 2);
-                        v3 -= TC_TRI(k + 3, r) * TC_VEC(k + 3);
-                    }
-                    for (; k < R; ++k) v0 -= TC_TRI(k, r) * TC_VEC(k);
-                    TC_VEC(r) = ((v0 + v1) + (v2 + v3)) * TC_DINV(r);
-                }
-                for (int r = 0; r < R; ++r) P.out[i * (int64_t)R + r] = (T)TC_VEC(r);
-            } else {
-                // L^-1 in place, column by column: for r > j, L^-1[r][j] =
-                // -(sum_{k=j}^{r-1} L[r][k] L^-1[k][j]) / L[r][r]; columns > j still hold L.
-                for (int j = 0; j < R; ++j) {
-                    TC_TRI(j, j) = TC_DINV(j);
-                    for (int r = j + 1; r < R; ++r) {
-                        CT v0 = CT(0), v1 = CT(0), v2 = CT(0), v3 = CT(0);
-                        int k = j;
-                        for (; k + 3 < r; k += 4) {
-                            v0 += TC_TRI(r, k) * TC_TRI(k, j);
-                            v1 += TC_TRI(r, k + 1) * TC_TRI(k + 1, j);
-                            v2 += TC_TRI(r, k + 2) * TC_TRI(k + 2, j);
-                            v3 += TC_TRI(r, k + 3) * TC_TRI(k + 3, j);
-                        }
-                        for (; k < r; ++k) v0 += TC_TRI(r, k) * TC_TRI(k, j);
-                        TC_TRI(r, j) = -((v0 + v1) + (v2 + v3)) * TC_DINV(r);
-                    }
-                }
-                // (L L^T)^-1 [r][c] = sum_{k >= max(r, c)} L^-1[k][r] L^-1[k][c]
-                T *Po = P.pinv + i * (int64_t)R * R;
-                for (int r = 0; r < R; ++r)
-                    for (int c = 0; c <= r; ++c) {
-                        CT v0 = CT(0), v1 = CT(0), v2 = CT(0), v3 = CT(0);
-                        int k = r;
-                        for (; k + 3 < R; k += 4) {
-                            v0 += TC_TRI(k, r) * TC_TRI(k, c);
-                            v1 += TC_TRI(k + 1, r) * TC_TRI(k + 1, c);
-                            v2 += TC_TRI(k + 2, r) * TC_TRI(k + 2, c);
-                            v3 += TC_TRI(k + 3, r) * TC_TRI(k + 3, c);
-                        }
-                        for (; k < R; ++k) v0 += TC_TRI(k, r) * TC_TRI(k, c);
-                        const CT v = (v0 + v1) + (v2 + v3);
-                        Po[r * R + c] = (T)v;
-                        Po[c * R + r] = (T)v;
-                    }
+                if (k < R) v0 += TC_Y(k, r) * TC_Y(k, c);
+                const CT v = v0 + v1;
+                Po[r * R + c] = (T)v;
+                Po[c * R + r] = (T)v;
+                tri_advance(r, c, lpr);
             }
         }
     }
+    if (mine) {
+        if (!ok) {
+            if (sub == 0) {
+                record_error(P.status, TC_ERR_NOT_SPD);
+                if (P.row_status) P.row_status[i] = 1;
+                TC_TRI(0, 0) = CT(0);
+            }
+            if (P.pinv) {  // an identity block keeps the preconditioner defined
+                T *Po = P.pinv + i * (int64_t)R * R;
+                for (int q = sub; q < R * R; q += lpr) Po[q] = (q / R == q % R) ? T(1) : T(0);
+            }
+        } else if (sub == 0 && P.row_status) {
+            P.row_status[i] = 0;
+        }
+    }
 #undef TC_TRI
+#undef TC_Y
 #undef TC_VEC
 #undef TC_DINV
     if (P.refine) {   // the factors, back over the Gram rows (coalesced per row)
         __syncwarp();
-        for (int s = 0; s < rpw; ++s) {
-            const int64_t q = grp * rpw + s;
-            if (q >= B.nrows) break;
-            T *lrow = B.light + q * (int64_t)tri;
+        for (int s = 0; s < nr; ++s) {
+            T *lrow = B.light + (q0 + s) * (int64_t)tri;
             for (int e = lane; e < tri; e += 32) lrow[e] = (T)Tri[e * ps + s];
         }
     }
@@ -1906,12 +1947,15 @@ static int64_t chunk_nnz(int64_t m, int64_t grid, const tc_solve_tuning &t) {
 // Kernel A variant for (dtype, rank tier, form): warp-local kernels (one warp
 // per chunk) for FP64 ranks <= 16 and tensor-core ranks <= 32, the block
 // kernel otherwise.
-template <typename T, int RT, bool VEC, int KIND>
+// WARP_MMA = true takes the block kernel where the tcgen05 kernel would run.
+template <typename T, int RT, bool VEC, int KIND, bool WARP_MMA = false>
 struct GramLaunch {
+    static constexpr bool HAS_TC05 =
+        sizeof(T) == 4 && RT == 64 && VEC && (KIND == GK_TF32 || KIND == GK_BF16);
     static constexpr int VAR = (sizeof(T) == 8 && RT <= 16) ? 1
                                : (sizeof(T) == 4 && RT <= 32 && KIND != GK_FFMA) ? 2
-                               : (sizeof(T) == 4 && RT == 64 && VEC && (KIND == GK_TF32 || KIND == GK_BF16)) ? 3
-                                                                                                       : 0;
+                               : (HAS_TC05 && !WARP_MMA) ? 3
+                                                         : 0;
     static constexpr bool PER_WARP = VAR == 1 || VAR == 2;
     static int threads() {
         if constexpr (VAR == 1) return WarpGram<T, RT>::NTH;
@@ -1971,10 +2015,10 @@ struct GramLaunch {
     }
 };
 
-template <typename T, int RT, bool VEC, int KIND, bool CHOL32>
-static tc_status launch_solve_rt(const SolveParams<T> &P, int64_t m, const tc_solve_tuning &tun,
+template <typename T, int RT, bool VEC, int KIND, bool CHOL32, bool WARP_MMA>
+static tc_status launch_solve_gl(const SolveParams<T> &P, int64_t m, const tc_solve_tuning &tun,
                                  const tc_pattern *pat, int mode, cudaStream_t st) {
-    using GL = GramLaunch<T, RT, VEC, KIND>;
+    using GL = GramLaunch<T, RT, VEC, KIND, WARP_MMA>;
     using CT = typename std::conditional<CHOL32, float, double>::type;   // factorization type
     const int R = P.R, tri = R * (R + 1) / 2;
     const int sms = device_sms();
@@ -1988,10 +2032,10 @@ static tc_status launch_solve_rt(const SolveParams<T> &P, int64_t m, const tc_so
     const int64_t ch_c = ch / 4 > 64 ? ch / 4 : 64;    // refinement: a warp per chunk
 
     const bool warp_b = RT > 32;
-    // rows per warp of the one-row-per-lane factorization.  Measured on
-    // GB300 (FP64 issue is per warp instruction, and each FP64 triangle of a
-    // lane's row takes R(R+1)/2 * 8 bytes of shared memory): 16 for R <= 16,
-    // 8 for R = 32 (more rows per warp leave too few warps per SM)
+    // rows per warp of the R <= 32 factorization (32 / rpw lanes per row):
+    // 16 for R <= 16, 8 for R = 32, so that a mode of 10^4 rows still spreads
+    // over several warps per SM (each row's FP64 triangle takes R(R+1)/2 * 8
+    // bytes of shared memory, twice that in inverse mode)
     int rpw = RT <= 16 ? 16 : 8;
     if (tun.chol_rows_per_warp > 0) rpw = tun.chol_rows_per_warp < 32 ? tun.chol_rows_per_warp : 32;
     if (RT > 16 && rpw > 16) rpw = 16;
@@ -2001,7 +2045,7 @@ static tc_status launch_solve_rt(const SolveParams<T> &P, int64_t m, const tc_so
         smem_b = sizeof(CT) * (size_t)kCholWarps * (tri * (P.pinv ? 2 : 1) + 2 * R) +
                  sizeof(uint32_t) * tri;
     else
-        smem_b = sizeof(CT) * (size_t)(tri + 2 * R) * (rpw + 1);
+        smem_b = sizeof(CT) * (size_t)(tri * (P.pinv ? 2 : 1) + 2 * R) * (rpw + 1);
     if (warp_b) {
         auto kb = chol_warp_kernel<T, CT>;
         TC_CUDA(cudaFuncSetAttribute(kb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b));
@@ -2047,6 +2091,17 @@ static tc_status launch_solve_rt(const SolveParams<T> &P, int64_t m, const tc_so
         }
     }
     return cudaGetLastError() == cudaSuccess ? TC_OK : TC_ERR_CUDA;
+}
+
+// The Gram engine: the tuned choice where both exist.
+template <typename T, int RT, bool VEC, int KIND, bool CHOL32>
+static tc_status launch_solve_rt(const SolveParams<T> &P, int64_t m, const tc_solve_tuning &tun,
+                                 const tc_pattern *pat, int mode, cudaStream_t st) {
+    if constexpr (GramLaunch<T, RT, VEC, KIND>::HAS_TC05) {
+        if (tun.gram_kernel == TC_GRAM_WARP_MMA)
+            return launch_solve_gl<T, RT, VEC, KIND, CHOL32, true>(P, m, tun, pat, mode, st);
+    }
+    return launch_solve_gl<T, RT, VEC, KIND, CHOL32, false>(P, m, tun, pat, mode, st);
 }
 
 template <typename T, int KIND, bool C32>
@@ -2156,7 +2211,8 @@ extern "C" tc_status tc_set_solve_tuning(tc_dtype dtype, int R, const tc_solve_t
         const int v = t->chol_rows_per_warp;
         if (v < 1 || v > 32 || (v & (v - 1))) return TC_ERR_ARG;
     }
-    const tc_solve_tuning v = t ? *t : tc_solve_tuning{0, 0, 0};
+    if (t && (t->gram_kernel < TC_GRAM_AUTO || t->gram_kernel > TC_GRAM_TCGEN05)) return TC_ERR_ARG;
+    const tc_solve_tuning v = t ? *t : tc_solve_tuning{0, 0, 0, 0};
     std::lock_guard<std::mutex> lock(tc::g_tuning_mu);
     for (int k = 0; k < 4; ++k)
         if (R == 0 || tc::tier_slot(tc::rank_tier(R)) == k) tc::g_tuning[dtype][k] = v;
@@ -2170,7 +2226,8 @@ extern "C" tc_status tc_get_solve_tuning(tc_dtype dtype, int R, tc_solve_tuning 
 }
 
 // Candidate tunings for the rank tier: chunk sizes around the automatic
-// choice, and the factorization's rows per warp where it applies.
+// choice, the factorization's rows per warp where it applies, and the Gram
+// engine where two exist.
 extern "C" tc_status tc_autotune_solve(const tc_pattern *p, tc_weights w, const void *s, int R,
                                        const void *const *factors, int mode, const void *rhs,
                                        double lambda, tc_prec prec, void *out,
@@ -2187,6 +2244,14 @@ extern "C" tc_status tc_autotune_solve(const tc_pattern *p, tc_weights w, const 
     int nr = 1;
     if (tier <= 16) { rpws[0] = 8; rpws[1] = 16; rpws[2] = 32; nr = 3; }
     else if (tier <= 32) { rpws[0] = 4; rpws[1] = 8; rpws[2] = 16; nr = 3; }
+    const tc_prec form = (tc_prec)(prec & ~(TC_PREC_CHOL32 | TC_PREC_REFINE2));
+    int engines[2] = {TC_GRAM_AUTO, TC_GRAM_AUTO};
+    int ne = 1;
+    if (p->dtype == TC_F32 && R == 64 && (form == TC_PREC_TF32_REFINE || form == TC_PREC_BF16_REFINE)) {
+        engines[0] = TC_GRAM_TCGEN05;
+        engines[1] = TC_GRAM_WARP_MMA;
+        ne = 2;
+    }
     cudaStream_t st = (cudaStream_t)stream;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
@@ -2197,8 +2262,8 @@ extern "C" tc_status tc_autotune_solve(const tc_pattern *p, tc_weights w, const 
     float win_ms = -1.f;
     tc_status rc = TC_OK;
     for (int64_t ch : chunks) {
-        for (int k = 0; k < nr && rc == TC_OK; ++k) {
-            const tc_solve_tuning cand{ch, saved.batch_bytes, rpws[k]};
+        for (int k = 0; k < nr * ne && rc == TC_OK; ++k) {
+            const tc_solve_tuning cand{ch, saved.batch_bytes, rpws[k % nr], engines[k / nr]};
             // one untimed call (caches, work space), then one timed
             rc = tc::launch_solve_factor(p, w, s, R, factors, mode, rhs, lambda, prec, out, nullptr,
                                          0, TC_LOSS_LS, nullptr, st, &cand);

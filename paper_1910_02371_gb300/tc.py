@@ -384,31 +384,37 @@ def sort_mode_noalloc(key: torch.Tensor, I: int, perm=None, row_ptr=None, status
 
 
 class _SolveTuning(ctypes.Structure):
-    _fields_ = [("chunk_nnz", _I64), ("batch_bytes", _I64), ("chol_rows_per_warp", ctypes.c_int32)]
+    _fields_ = [("chunk_nnz", _I64), ("batch_bytes", _I64), ("chol_rows_per_warp", ctypes.c_int32),
+                ("gram_kernel", ctypes.c_int32)]
+
+
+GRAM_AUTO, GRAM_WARP_MMA, GRAM_TCGEN05 = 0, 1, 2
 
 
 def set_solve_tuning(dtype: torch.dtype, R: int = 0, chunk_nnz: int = 0, batch_bytes: int = 0,
-                     chol_rows_per_warp: int = 0, reset: bool = False):
-    """tc_set_solve_tuning: chunk size, batch budget and factorization rows per
-    warp of Solve Factor for the rank tier of R (R = 0: every tier);
-    reset=True restores the automatic choice."""
+                     chol_rows_per_warp: int = 0, gram_kernel: int = 0, reset: bool = False):
+    """tc_set_solve_tuning: chunk size, batch budget, factorization rows per
+    warp and Gram engine (GRAM_*) of Solve Factor for the rank tier of R
+    (R = 0: every tier); reset=True restores the automatic choice."""
     t = None if reset else ctypes.byref(
-        _SolveTuning(int(chunk_nnz), int(batch_bytes), int(chol_rows_per_warp)))
+        _SolveTuning(int(chunk_nnz), int(batch_bytes), int(chol_rows_per_warp), int(gram_kernel)))
     _check(_lib.tc_set_solve_tuning(_dtype_code(dtype), int(R), t), "tc_set_solve_tuning")
 
 
 def get_solve_tuning(dtype: torch.dtype, R: int):
-    """tc_get_solve_tuning: (chunk_nnz, batch_bytes, chol_rows_per_warp), 0 meaning automatic."""
+    """tc_get_solve_tuning: (chunk_nnz, batch_bytes, chol_rows_per_warp,
+    gram_kernel), 0 meaning automatic."""
     t = _SolveTuning()
     _check(_lib.tc_get_solve_tuning(_dtype_code(dtype), int(R), ctypes.byref(t)),
            "tc_get_solve_tuning")
-    return int(t.chunk_nnz), int(t.batch_bytes), int(t.chol_rows_per_warp)
+    return int(t.chunk_nnz), int(t.batch_bytes), int(t.chol_rows_per_warp), int(t.gram_kernel)
 
 
 def autotune_solve(p: Pattern, factors, mode: int, rhs: torch.Tensor, lam: float, weights=None,
                    out=None, prec: str = "fp32", stream=None):
     """tc_autotune_solve: times Solve Factor at the candidate tunings, installs
-    the fastest; returns ((chunk_nnz, batch_bytes, chol_rows_per_warp), ms)."""
+    the fastest; returns ((chunk_nnz, batch_bytes, chol_rows_per_warp,
+    gram_kernel), ms)."""
     R = rhs.shape[1]
     wk, s = _wcode(weights)
     if out is None:
@@ -418,7 +424,8 @@ def autotune_solve(p: Pattern, factors, mode: int, rhs: torch.Tensor, lam: float
     _check(_lib.tc_autotune_solve(p.handle, wk, _ptr(s), R, _ptrs(factors), mode, _ptr(rhs),
                                   float(lam), PRECS[prec], _ptr(out), ctypes.byref(best),
                                   ctypes.byref(ms), _stream(stream)), "tc_autotune_solve")
-    return (int(best.chunk_nnz), int(best.batch_bytes), int(best.chol_rows_per_warp)), float(ms.value)
+    return (int(best.chunk_nnz), int(best.batch_bytes), int(best.chol_rows_per_warp),
+            int(best.gram_kernel)), float(ms.value)
 
 
 def newton_als_mode(p: Pattern, factors, mode: int, loss: str, lam: float, inner_iters: int = 5,

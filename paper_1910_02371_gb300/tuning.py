@@ -4,7 +4,8 @@
 (tc_autotune_solve) on a real pattern and records the winner under a key of
 the dtype, the rank tier and the mode's shape class (rows and nonzeros per
 row, in powers of two); ``save(path)`` / ``load(path)`` write and read those
-records as JSON, and ``apply(...)`` installs the record that matches a
+records as JSON (a record without ``gram_kernel`` means the automatic
+engine), and ``apply(...)`` installs the record that matches a
 workload.  Everything here is host bookkeeping; the timing runs in the
 library.
 """
@@ -40,7 +41,8 @@ def autotune(p: "tc.Pattern", factors, mode: int, rhs: torch.Tensor, lam: float,
     R = rhs.shape[1]
     best, ms = tc.autotune_solve(p, factors, mode, rhs, lam, prec=prec)
     key = shape_key(p.dtype, R, p.dims[mode], p.nnz, prec)
-    rec = {"chunk_nnz": best[0], "batch_bytes": best[1], "chol_rows_per_warp": best[2], "ms": ms}
+    rec = {"chunk_nnz": best[0], "batch_bytes": best[1], "chol_rows_per_warp": best[2],
+           "gram_kernel": best[3], "ms": ms}
     _records[key] = rec
     return key, rec
 
@@ -72,5 +74,6 @@ def apply(dtype: torch.dtype, R: int, rows: int, nnz: int, prec: str = "fp32") -
     if rec is None:
         return False
     tc.set_solve_tuning(dtype, R, chunk_nnz=rec["chunk_nnz"], batch_bytes=rec["batch_bytes"],
-                        chol_rows_per_warp=rec["chol_rows_per_warp"])
+                        chol_rows_per_warp=rec["chol_rows_per_warp"],
+                        gram_kernel=rec.get("gram_kernel", 0))
     return True

@@ -60,7 +60,7 @@ def _tune(tc, prob, tuning):
     if tuning != (0, 0, 0):
         tc.set_solve_tuning(dt, prob.R, chunk_nnz=tuning[0], batch_bytes=tuning[1],
                             chol_rows_per_warp=tuning[2])
-        assert tc.get_solve_tuning(dt, prob.R) == tuning
+        assert tc.get_solve_tuning(dt, prob.R) == tuple(tuning) + (0,)
 
 
 @pytest.mark.parametrize("name", list(CASES))
@@ -262,3 +262,32 @@ def test_not_spd_rows_warp_cholesky(tc):
     if ok_rows.size:
         assert np.all(np.isfinite(got[ok_rows]))
         assert rel(got[ok_rows], ref[ok_rows]) <= 1e-2
+
+
+@pytest.mark.parametrize("engine", [1, 2])
+@pytest.mark.parametrize("prec,tol", [("tf32_refine", 2e-5), ("bf16_refine", 1.5e-3),
+                                      ("tf32_refine2", 2e-6)])
+def test_gram_engines_r64(tc, engine, prec, tol):
+    """Both Gram engines of the R = 64 tensor-core forms (warp-level mma.sync
+    blocks, and tcgen05.mma with the accumulator in tensor memory), forced by
+    the tuning: each refined solve within the form's measured error of the
+    FP64 oracle's solve (TF32 + one step 5.8e-6, BF16 + one step 3.7e-4 on
+    this case at lambda = 0.5), in every mode."""
+    import torch
+    prob = problem("zipf_f32_r64")
+    tc.set_solve_tuning(torch.float32, 0, reset=True)
+    tc.set_solve_tuning(torch.float32, 64, gram_kernel=engine)
+    assert tc.get_solve_tuning(torch.float32, 64) == (0, 0, 0, engine)
+    try:
+        p = build(prob)
+        A = [to_dev(a, "f32") for a in prob.factors]
+        for mode in range(3):
+            rhs = oracle.mttkrp(prob.dims, prob.idx, prob.t, prob.factors, mode)
+            rhs = rhs.astype(np.float32).astype(np.float64)
+            ref, _, rc = oracle.solve_factor(prob.dims, prob.idx, None, prob.factors, mode, rhs, 0.5)
+            assert rc == 0
+            out = host(tc.solve_factor(p, A, mode, to_dev(rhs, "f32"), 0.5, prec=prec))
+            assert rel(out, ref) <= tol, (engine, prec, mode, rel(out, ref))
+        assert tc.last_error(p) == tc.OK
+    finally:
+        tc.set_solve_tuning(torch.float32, 0, reset=True)

@@ -35,7 +35,7 @@ def test_json_round_trip_and_apply(mods, tmp_path):
     assert data[key]["chunk_nnz"] == 1024
     try:
         assert tuning.apply(torch.float32, 32, 50_000, 50_000_000)
-        assert tc.get_solve_tuning(torch.float32, 32) == (1024, 0, 8)
+        assert tc.get_solve_tuning(torch.float32, 32) == (1024, 0, 8, 0)
         assert not tuning.apply(torch.float32, 64, 50_000, 50_000_000)
     finally:
         tc.set_solve_tuning(torch.float32, 0, reset=True)
@@ -53,3 +53,5 @@ def test_setter_rejects_bad_values(mods):
         tc.set_solve_tuning(torch.float32, 16, chunk_nnz=-1)
     with pytest.raises(tc.TcError):
         tc.set_solve_tuning(torch.float32, 65)
+    with pytest.raises(tc.TcError):
+        tc.set_solve_tuning(torch.float32, 64, gram_kernel=3)
