@@ -212,13 +212,20 @@ def cpu_sample(w):
         n = int(round(w.nnz / w.dims[0] * dims[0]))
         c = synth.feistel_coords(np.arange(n, dtype=np.int64), bits, synth.feistel_keys(w.seed))
         idx = [np.ascontiguousarray(x.astype(np.int32)) for x in c]
-    else:
+    capped = ""
+    if w.coords != "feistel":
+        # a skewed shape scaled this way can ask for more nonzeros than the
+        # sample has cells: draw at most half of them
+        cells = dims[0] * dims[1] * dims[2]
+        if n > cells // 2:
+            n = cells // 2
+            capped = " (capped at half the sample's cells)"
         idx = synth.distinct_coords(dims, n, w.coord_dist, w.seed, w.zipf_s)
     planted = synth.factor_matrices(dims, w.rank, w.factor_dist, w.seed)
     t = synth.observe(oracle.model_entries(dims, idx, planted), w.values, w.seed, w.noise)
     start = synth.perturb(planted, w.seed)
     desc = (f"the workload's recipe scaled to {dims[0]}x{dims[1]}x{dims[2]} with its "
-            f"{w.nnz / w.dims[0]:.0f} nonzeros per row: {n} nonzeros, rank {w.rank}; one "
+            f"{w.nnz / w.dims[0]:.0f} nonzeros per row{capped}: {n} nonzeros, rank {w.rank}; one "
             f"oracle step (3 counting sorts, TTTP, ALS sweep, GGN step with {CG_ITERS} PCG "
             f"iterations; the oracle's preconditioner re-solves its rows each iteration)")
     return dims, idx, t, start, desc
@@ -535,8 +542,8 @@ def run_ours(args):
     if args.als_forms:
         als_forms = {}
         fval = {}
-        for form in ("fp32_refine", "fp32", "tf32_refine", "bf16_refine", "fp32_refine_chol32",
-                     "tf32_refine_chol32", "bf16_refine_chol32"):
+        for form in ("fp32_refine", "fp32", "tf32_refine", "tf32_refine2", "bf16_refine",
+                     "fp32_refine_chol32", "tf32_refine_chol32", "bf16_refine_chol32"):
             B = [a.clone() for a in A0]
 
             def sweep_from_start(form=form, B=B):
