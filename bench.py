@@ -366,19 +366,28 @@ def run_ours(args):
     if args.solve_probe is not None:
         # Solve Factor on one mode (right-hand side: the MTTKRP of the values),
         # timed alone in each form of --prec (comma-separated, in that order:
-        # one untimed call, then --steps timed calls per form; "form@warp" or
-        # "form@tc05" forces the R = 64 Gram engine): the command the Solve
-        # Factor profiles use
+        # one untimed call, then --steps timed calls per form; suffixes force
+        # a tuning: "@warp" or "@tc05" the R = 64 Gram engine, "@rpwN" the
+        # factorization's rows per warp): the command the Solve Factor
+        # profiles use
         d = args.solve_probe
         b = tc.mttkrp(p, A, d)
         out = torch.empty_like(b)
         ms = {}
-        engines = {"": tc.GRAM_AUTO, "warp": tc.GRAM_WARP_MMA, "tc05": tc.GRAM_TCGEN05}
+        engines = {"warp": tc.GRAM_WARP_MMA, "tc05": tc.GRAM_TCGEN05}
         for spec in args.prec.split(","):
-            form, _, eng = spec.partition("@")
+            form, *opts = spec.split("@")
+            eng = rpw = 0
+            for o in opts:
+                if o in engines:
+                    eng = engines[o]
+                elif o.startswith("rpw"):
+                    rpw = int(o[3:])
+                else:
+                    raise SystemExit(f"unknown solve-probe option {o!r}")
             tc.set_solve_tuning(f32, 0, reset=True)
-            if eng:
-                tc.set_solve_tuning(f32, w.rank, gram_kernel=engines[eng])
+            if eng or rpw:
+                tc.set_solve_tuning(f32, w.rank, gram_kernel=eng, chol_rows_per_warp=rpw)
             tc.solve_factor(p, A, d, b, w.lam, out=out, prec=form)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
