@@ -11,7 +11,9 @@ beside the step (the consumed input cannot be sorted twice).
 One step = one pass of every hot-path kernel over the tensor, all through the
 C ABI of libtc:
   1. TTTP of the current model at the observed entries (tc_tttp),
-  2. one ALS sweep: per mode MTTKRP of the tensor, then Solve Factor (Sec. 2.2),
+  2. one ALS sweep: per mode the MTTKRP of the tensor and Solve Factor (Sec. 2.2),
+     fused into one pass where the Gram kernel forms the right-hand side
+     (tc_als_update),
   3. one generalized Gauss-Newton step: objective and gradient, block-diagonal
      preconditioner, 10 PCG iterations replayed from a CUDA graph, update (Sec. 2.5).
 Workloads small enough to draw on the host (``--workload cp3_10k_m10M_r16``)
@@ -531,6 +533,9 @@ def run_ours(args):
     for d in range(3):
         kern[f"solve_factor_mode{d}"] = timed(
             lambda d=d: tc.solve_factor(p, A, d, rhs[d], w.lam, out=yv[d]))
+    for d in range(3):   # the step's ALS: right-hand side formed in the Gram pass
+        kern[f"als_update_mode{d}"] = timed(
+            lambda d=d: tc.als_update(p, A, d, w.lam, out=yv[d], prec=args.prec))
     kern["loss_grad"] = timed(lambda: tc.loss_grad(p, A, w.loss, w.lam, grads=gb))
     kern["ggn_matvec"] = timed(lambda: tc.ggn_matvec(p, A, xv, w.loss, w.lam, y=yv))
     # the product as the PCG runs it (interleaved factor / direction rows)
@@ -572,10 +577,11 @@ def run_ours(args):
             raise RuntimeError("device error in the precision forms")
 
     # ---- roofline of the dominant kernel
+    # the step's time by kernel family (the ALS sweep runs fused updates:
+    # MTTKRP folded into Solve Factor's Gram pass)
     share = {
         "ggn_matvec": CG_ITERS * kern["ggn_matvec_pcg"],
-        "solve_factor": sum(kern[f"solve_factor_mode{d}"] for d in range(3)) + kern["precond_setup"],
-        "mttkrp": sum(kern[f"mttkrp_mode{d}"] for d in range(3)),
+        "solve_factor": sum(kern[f"als_update_mode{d}"] for d in range(3)) + kern["precond_setup"],
         "tttp": kern["tttp"],
         "loss_grad": kern["loss_grad"],
     }
@@ -600,7 +606,7 @@ def run_ours(args):
     roofs = {
         "ggn_matvec": roof("ggn_matvec", kern["ggn_matvec_pcg"]),
         "tttp": roof("tttp", kern["tttp"]),
-        "mttkrp": roof("mttkrp", share["mttkrp"] / 3),
+        "mttkrp": roof("mttkrp", sum(kern[f"mttkrp_mode{d}"] for d in range(3)) / 3),
         "solve_factor": roof("solve_factor", sum(kern[f"solve_factor_mode{d}"] for d in range(3)) / 3),
     }
     main_kind = dominant if dominant in roofs else "ggn_matvec"

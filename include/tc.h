@@ -239,6 +239,22 @@ tc_status tc_solve_factor(const tc_pattern *p, tc_weights w, const void *s, int 
                           double lambda, tc_prec prec, void *out, int8_t *row_status,
                           tc_stream_t stream);
 
+/* One least-squares ALS update of factor `mode` (Sec. 2.2; the MTTKRP of
+ * Sec. 3.2 and Solve Factor of Sec. 3.4 in one call): for every row i,
+ *   (G_i + lambda I) a_i = rhs_i,  G_i = sum_{e in row i} h_e h_e^T,
+ *   rhs_i = sum_{e in row i} t_e h_e   (t: the pattern's values),
+ * i.e. tc_solve_factor with unit weights on the right-hand side
+ * tc_mttkrp(TC_W_VALUES) would give.  The Gram kernel forms rhs_i from the
+ * same gathered rows h_e (one pass over the nonzeros instead of two), except
+ * for FP64 data at R <= 16, where the MTTKRP kernel forms it first.  The right-hand side lives in the pattern's work space (I_mode x R
+ * of the pattern dtype, plus one R slot of doubles per chunk boundary).
+ * The pattern must have values.  out: device I_mode x R; may alias
+ * factors[mode] (the usual in-place sweep).  prec, row_status and errors as
+ * for tc_solve_factor. */
+tc_status tc_als_update(const tc_pattern *p, int R, const void *const *factors, int mode,
+                        double lambda, tc_prec prec, void *out, int8_t *row_status,
+                        tc_stream_t stream);
+
 /* Solve Factor tuning.  The Gram kernel walks a mode's sorted nonzeros in
  * chunks of `chunk_nnz` (rows longer than a chunk are split across blocks and
  * summed with FP64 atomics), and it forms the Gram triangles of at most

@@ -190,6 +190,21 @@ tc_status tc_solve_factor(const tc_pattern *p, tc_weights w, const void *s, int 
     return rc != TC_OK ? rc : launch_status();
 }
 
+tc_status tc_als_update(const tc_pattern *p, int R, const void *const *factors, int mode,
+                        double lambda, tc_prec prec, void *out, int8_t *row_status,
+                        tc_stream_t stream) {
+    if (!p || !rank_ok(R) || !out || mode < 0 || mode >= p->order) return TC_ERR_ARG;
+    if (!factors_ok(factors, mode)) return TC_ERR_ARG;
+    if (!p->has_vals && p->nnz > 0) return TC_ERR_ARG;
+    const int form = prec & ~(TC_PREC_CHOL32 | TC_PREC_REFINE2);
+    if (form != TC_PREC_FP32 && form != TC_PREC_TF32_REFINE && form != TC_PREC_BF16_REFINE &&
+        form != TC_PREC_FP32_REFINE)
+        return TC_ERR_ARG;
+    tc_status rc = launch_als_update(p, R, factors, mode, lambda, prec, out, row_status,
+                                     (cudaStream_t)stream);
+    return rc != TC_OK ? rc : launch_status();
+}
+
 tc_status tc_loss_grad(const tc_pattern *p, tc_loss loss, int R, const void *const *factors,
                        double lambda, double *loss_out, void *const *grads, tc_stream_t stream) {
     if (!p || !rank_ok(R) || !factors_ok(factors, -1)) return TC_ERR_ARG;

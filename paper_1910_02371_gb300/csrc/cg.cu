@@ -357,16 +357,24 @@ static void free_cg(tc_cg *cg) {
 // most of the GPU idle (the R <= 32 factorization keeps a few warps per SM),
 // so mode d is factored on side[d], forked from `st` and joined back into it;
 // `work` runs on `st` meanwhile (the gradient, in a Gauss-Newton step).
+// With_grad: each block's Gram pass also writes the gradient's MTTKRP(phi')
+// of its mode into cg->grad and mode 0's adds sum phi into loss_acc (may be
+// null); see launch_precond_grad.
 template <typename F>
-static tc_status setup_forked(tc_cg *cg, cudaStream_t st, F &&work) {
+static tc_status setup_forked(tc_cg *cg, cudaStream_t st, F &&work, bool with_grad = false,
+                              double *loss_acc = nullptr) {
     if (!cg->precond) return work();
     TC_CUDA(cudaEventRecord(cg->ev_fork, st));
     for (int d = 0; d < TC_ORDER; ++d) TC_CUDA(cudaStreamWaitEvent(cg->side[d], cg->ev_fork, 0));
     tc_status rc = TC_OK;
     for (int d = 0; d < TC_ORDER && rc == TC_OK; ++d)
-        rc = launch_solve_factor(cg->p, TC_W_ONE, nullptr, cg->R, (const void *const *)cg->A, d,
-                                 nullptr, 2.0 * cg->lambda, TC_PREC_FP32, nullptr, nullptr, 1,
-                                 cg->loss, cg->pinv[d], cg->side[d]);
+        rc = with_grad
+                 ? launch_precond_grad(cg->p, cg->R, (const void *const *)cg->A, d, 2.0 * cg->lambda,
+                                       cg->loss, cg->pinv[d], cg->grad[d], d == 0 ? loss_acc : nullptr,
+                                       cg->side[d])
+                 : launch_solve_factor(cg->p, TC_W_ONE, nullptr, cg->R, (const void *const *)cg->A, d,
+                                       nullptr, 2.0 * cg->lambda, TC_PREC_FP32, nullptr, nullptr, 1,
+                                       cg->loss, cg->pinv[d], cg->side[d]);
     const tc_status rw = rc == TC_OK ? work() : TC_OK;
     // join every side stream, whatever happened above
     for (int d = 0; d < TC_ORDER; ++d) {
@@ -564,9 +572,34 @@ tc_status tc_ggn_step(tc_cg *cg, int iters, double *loss_out, tc_stream_t stream
     if (!cg || iters < 0) return TC_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     const tc_pattern *p = cg->p;
+    tc_status rc;
+    if (cg->precond && solve_fuses_rhs(p->dtype, cg->R)) {
+        // The preconditioner's Gram passes (one per mode, on the side streams)
+        // also form MTTKRP(phi') into grad and the loss sum phi, so the gradient
+        // costs no pass of its own; the regularizer's share of the loss runs
+        // on `st` meanwhile.  Then b = -(MTTKRP(phi') + 2 lambda A) in place.
+        if (loss_out) TC_CUDA(cudaMemsetAsync(loss_out, 0, sizeof(double), st));
+        rc = setup_forked(
+            cg, st,
+            [&]() -> tc_status {
+                return loss_out ? launch_regularizer(p, cg->R, (const void *const *)cg->A, cg->lambda,
+                                                     loss_out, st)
+                                : TC_OK;
+            },
+            true, loss_out);
+        if (rc != TC_OK) return rc;
+        for (int d = 0; d < TC_ORDER; ++d) {
+            const int64_t n = p->dims[d] * cg->R;
+            int64_t blocks = (n + 255) / 256;
+            if (blocks > 8LL * sms()) blocks = 8LL * sms();
+            axpby_kernel<float><<<(unsigned)blocks, 256, 0, st>>>(
+                n, (float)(-2.0 * cg->lambda), (const float *)cg->A[d], -1.0f, (float *)cg->grad[d]);
+            count_launch();
+        }
+    } else {
     // the gradient (and b = -grad, in place) on `st` while the preconditioner
     // blocks are factored on the side streams
-    tc_status rc = setup_forked(cg, st, [&]() -> tc_status {
+    rc = setup_forked(cg, st, [&]() -> tc_status {
         const tc_status rg = launch_loss_grad(p, cg->loss, cg->R, (const void *const *)cg->A,
                                               cg->lambda, loss_out, cg->grad, st);
         if (rg != TC_OK) return rg;
@@ -585,6 +618,7 @@ tc_status tc_ggn_step(tc_cg *cg, int iters, double *loss_out, tc_stream_t stream
         return TC_OK;
     });
     if (rc != TC_OK) return rc;
+    }
     // the solution goes to the solver's own buffer dx, then A += dx
     void *dxb[TC_ORDER];
     for (int d = 0; d < TC_ORDER; ++d) dxb[d] = cg->dx[d];

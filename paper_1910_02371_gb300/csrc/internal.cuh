@@ -32,9 +32,9 @@ struct PatternScratch {
 };
 
 // Work space of the calls that need more device memory than their outputs
-// (Solve Factor's Gram batch, cut-row slots, refinement residuals and right-hand
-// side copy, per mode; the general-loss Newton and coordinate-descent
-// buffers).  The pattern keeps
+// (Solve Factor's Gram batch, cut-row slots, refinement residuals, right-hand
+// side copy or the right-hand side an ALS update forms, and its cut-row
+// slots, per mode; the general-loss Newton and coordinate-descent buffers).  The pattern keeps
 // each buffer and grows it on demand (tc::work_buffer), so a call at a size
 // the pattern has served before allocates nothing.
 enum WorkSlot {
@@ -42,7 +42,8 @@ enum WorkSlot {
     WS_SOLVE_CUT = WS_SOLVE_GRAM + 3,   // + mode
     WS_SOLVE_RES = WS_SOLVE_CUT + 3,    // + mode
     WS_SOLVE_RHS = WS_SOLVE_RES + 3,    // + mode
-    WS_NEWTON = WS_SOLVE_RHS + 3,
+    WS_SOLVE_CUT_RHS = WS_SOLVE_RHS + 3,  // + mode
+    WS_NEWTON = WS_SOLVE_CUT_RHS + 3,
     WS_NEWTON_SUMS,
     WS_CCD,
     WS_CCD_SUMS,
@@ -151,6 +152,27 @@ tc_status launch_solve_factor(const tc_pattern *p, tc_weights w, const void *s, 
                               tc_prec prec, void *out, int8_t *row_status, int use_loss_d2,
                               tc_loss loss, void *pinv_out, cudaStream_t st,
                               const tc_solve_tuning *tun = nullptr);
+// One ALS update of factor `mode`: Solve Factor with unit weights and the
+// right-hand side rhs_i = sum_e t_e h_e (the MTTKRP of the values) formed in
+// the Gram pass where the Gram kernel supports it, else by the MTTKRP kernel
+// first; the right-hand side lives in the pattern's work space.
+tc_status launch_als_update(const tc_pattern *p, int R, const void *const *A, int mode,
+                            double lambda, tc_prec prec, void *out, int8_t *row_status,
+                            cudaStream_t st);
+// True where the Gram kernel forms a right-hand side in its own pass (FP32
+// data, R <= 32).
+bool solve_fuses_rhs(tc_dtype dtype, int R);
+// The preconditioner block of `mode` (launch_solve_factor with phi'' weights,
+// inverse into pinv_out) whose Gram pass also writes the gradient's
+// MTTKRP(phi', mode) into grad_out (I_mode x R, overwritten) and, if loss_acc
+// is not null, adds sum_e phi(t_e, m_e) to it; TC_ERR_UNSUPPORTED unless
+// solve_fuses_rhs.
+tc_status launch_precond_grad(const tc_pattern *p, int R, const void *const *A, int mode,
+                              double lambda2, tc_loss loss, void *pinv_out, void *grad_out,
+                              double *loss_acc, cudaStream_t st);
+// acc += lambda * sum_n ||A^(n)||_F^2 (the regularizer of eq. obj).
+tc_status launch_regularizer(const tc_pattern *p, int R, const void *const *A, double lambda,
+                             double *acc, cudaStream_t st);
 tc_status build_pattern_impl(int order, const int64_t *dims, int64_t nnz,
                              const int32_t *const *idx, const void *vals, tc_dtype dtype,
                              unsigned flags, cudaStream_t st, tc_pattern **out);

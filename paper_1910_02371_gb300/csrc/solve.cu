@@ -31,6 +31,12 @@
 
 namespace tc {
 
+// What the Gram pass also forms beside G_i: nothing (the right-hand side is
+// given), rhs_i = sum_e t_e h_e (the MTTKRP of the values: an ALS update), or
+// rhs_i = sum_e phi'(t_e, m_e) h_e (the MTTKRP of phi': the gradient, in a
+// preconditioner pass with phi'' weights).
+enum RhsKind { RHS_GIVEN = 0, RHS_VALUES = 1, RHS_DPHI = 2 };
+
 template <typename T>
 struct SolveParams {
     const int64_t *row_ptr;       // I_d + 1
@@ -49,6 +55,9 @@ struct SolveParams {
     int R;
     int refine;                   // refinement steps after the solve (0, 1 or 2)
     int *status;
+    int rhs_kind;                 // RhsKind: RHS_VALUES / RHS_DPHI form rhs_w in the Gram pass
+    T *rhs_w;                     // I_d x R (rhs_kind != RHS_GIVEN)
+    double *loss_acc;             // RHS_DPHI: += sum_e phi(t_e, m_e) over the pass, or null
 };
 
 // Rows [row0, row0 + nrows) of the mode and the chunks of ch nonzeros that
@@ -61,6 +70,7 @@ struct Batch {
                      // (with refinement: then every row's Cholesky factor)
     double *cut;     // one TRI slot per chunk boundary, for rows that cross one
     double *res;     // refinement: nrows x R residual sums (zeroed), or null
+    double *cut_rhs; // rhs_kind: one R slot per chunk boundary (zeroed), or null
 };
 
 // Packed lower-triangle index of (r, c), c <= r.
@@ -126,13 +136,40 @@ __device__ __forceinline__ int64_t cut_slot(int64_t rs, int64_t re, int64_t nb, 
 }
 
 template <typename T>
-__global__ void zero_cut_kernel(const int64_t *__restrict__ row_ptr, const Batch<T> B, int tri) {
+__global__ void zero_cut_kernel(const int64_t *__restrict__ row_ptr, const Batch<T> B, int tri,
+                                int R) {
     const int64_t nb = __ldg(row_ptr + B.row0), ne = __ldg(row_ptr + B.row0 + B.nrows);
     const int64_t nch = (ne - nb + B.ch - 1) / B.ch;
-    const int64_t n = (nch > 1 ? nch - 1 : 0) * (int64_t)tri;
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
-         q += (int64_t)gridDim.x * blockDim.x)
-        B.cut[q] = 0.0;
+    const int64_t nslot = nch > 1 ? nch - 1 : 0;
+    const int64_t n = nslot * (int64_t)tri, nr = B.cut_rhs ? nslot * (int64_t)R : 0;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n + nr;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        if (q < n) B.cut[q] = 0.0;
+        else B.cut_rhs[q - n] = 0.0;
+    }
+}
+
+// rhs_kind: the right-hand sides of the rows that cross a chunk boundary,
+// summed in FP64 in the row's cut slot by every chunk that covers part of it,
+// copied into rhs_w.  Slot k belongs to the row that holds position
+// nb + (k + 1) ch if that row's first boundary is that one (a row longer than
+// a chunk uses the slot of its first boundary only; the others stay unused).
+template <typename T>
+__global__ void cut_rhs_kernel(const int64_t *__restrict__ row_ptr, const Batch<T> B, int R,
+                               T *__restrict__ rhs_w) {
+    const int64_t nb = __ldg(row_ptr + B.row0), ne = __ldg(row_ptr + B.row0 + B.nrows);
+    const int64_t nch = (ne - nb + B.ch - 1) / B.ch;
+    const int64_t nslot = nch > 1 ? nch - 1 : 0;
+    const int64_t last = B.row0 + B.nrows - 1;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nslot * R;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = q / R;
+        const int r = (int)(q - k * R);
+        const int64_t pos = nb + (k + 1) * B.ch;             // < ne
+        const int64_t i = search_le(row_ptr, B.row0, last, pos);
+        const int64_t rs = __ldg(row_ptr + i), re = __ldg(row_ptr + i + 1);
+        if (cut_slot(rs, re, nb, B.ch) == k) rhs_w[i * (int64_t)R + r] = (T)B.cut_rhs[k * R + r];
+    }
 }
 
 // ------------------------------------------------------------------ Gram engines
@@ -655,7 +692,11 @@ __global__ void __launch_bounds__(GramShape<T, RT, KIND>::NTH, 2)
     // pe / pw hold the fetched factor slices and raw weights (the value t for
     // phi'') of KB consecutive positions, clamped to the chunk; positions
     // past the current row are fetched but masked when staged.
-    T pb[Q::NSTEP][V], pe[Q::NSTEP][V], pw[Q::NSTEP];
+    // RHS_VALUES: the values too (pt), each thread's share of sum_e t_e h_e
+    // for the row (racc), folded over the block through rsm at the row's end
+    const bool want_rhs = P.rhs_kind == RHS_VALUES;
+    __shared__ T rsm[Q::NW][RT];
+    T pb[Q::NSTEP][V], pe[Q::NSTEP][V], pw[Q::NSTEP], pt[Q::NSTEP], racc[V];
     int64_t ce = 0;
     auto fetch = [&](int64_t base) {
 #pragma unroll
@@ -665,6 +706,7 @@ __global__ void __launch_bounds__(GramShape<T, RT, KIND>::NTH, 2)
             load_slice<T, V, VEC>(pb[st], P.A1, __ldcs(P.c1 + qq), R, lg);
             load_slice<T, V, VEC>(pe[st], P.A2, __ldcs(P.c2 + qq), R, lg);
             pw[st] = P.use_d2 ? __ldcs(P.t + qq) : weight_at(P.w, qq);
+            pt[st] = want_rhs ? __ldcs(P.t + qq) : T(0);
         }
     };
     for (int64_t cs = nb + (int64_t)blockIdx.x * B.ch; cs < ne; cs += (int64_t)gridDim.x * B.ch) {
@@ -677,6 +719,8 @@ __global__ void __launch_bounds__(GramShape<T, RT, KIND>::NTH, 2)
             T arow[V];
             if (P.use_d2) load_slice<T, V, VEC>(arow, P.Ad, i, R, lg);
             eng.zero();
+#pragma unroll
+            for (int t = 0; t < V; ++t) racc[t] = T(0);
             if (!ahead) fetch(ss);
             ahead = false;
             for (int64_t base = ss; base < se; base += KB) {
@@ -706,6 +750,10 @@ __global__ void __launch_bounds__(GramShape<T, RT, KIND>::NTH, 2)
                         sw = T(0);
 #pragma unroll
                         for (int t = 0; t < V; ++t) h[t] = T(0);
+                    }
+                    if (want_rhs) {
+#pragma unroll
+                        for (int t = 0; t < V; ++t) racc[t] += pt[st] * h[t];
                     }
 #pragma unroll
                     for (int t = 0; t < V; ++t) hs[slot * S + lg * V + t] = h[t];
@@ -745,6 +793,25 @@ __global__ void __launch_bounds__(GramShape<T, RT, KIND>::NTH, 2)
                         else atomicAdd(crow + e, v);
                     }
                 }
+            }
+            if (want_rhs) {   // the row's right-hand side: groups, then warps
+                T tot[V];
+#pragma unroll
+                for (int t = 0; t < V; ++t) tot[t] = across_groups<G>(racc[t]);
+                if (g == 0) {
+#pragma unroll
+                    for (int t = 0; t < V; ++t)
+                        if (lg * V + t < R) rsm[w][lg * V + t] = tot[t];
+                }
+                __syncthreads();
+                for (int r = tid; r < R; r += Q::NTH) {
+                    T v = T(0);
+#pragma unroll
+                    for (int ww = 0; ww < Q::NW; ++ww) v += rsm[ww][r];
+                    if (whole) P.rhs_w[i * (int64_t)R + r] = v;
+                    else add_cut(B.cut_rhs + slot * (int64_t)R + r, v);
+                }
+                __syncthreads();
             }
             if (re >= ce) break;
             i = search_le_near(P.row_ptr, i + 1, last, re);   // next nonempty row
@@ -897,6 +964,9 @@ __global__ void __launch_bounds__(tc05::THREADS) gram_tc05_kernel(const SolvePar
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t mbar[2];
     __shared__ uint32_t tmem_slot;
+    // RHS_VALUES: each warp's partial right-hand side of the last two row
+    // segments (by accumulator parity), summed by the segment's epilogue
+    __shared__ float rpart[2][tc05::THREADS / 32][64];
     unsigned char *base =
         reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -931,6 +1001,8 @@ __global__ void __launch_bounds__(tc05::THREADS) gram_tc05_kernel(const SolvePar
     // (h = 0, 1) and components i / 4 + 8j (j = 0..7), so each shared store of
     // a warp fills one core matrix (or half of one for BF16) without conflicts
     const int kl = lane & 3, m0 = lane >> 2;
+    const bool want_rhs = P.rhs_kind == RHS_VALUES;
+    float racc[8];             // this thread's sum_e t_e h_e[m0 + 8j] over its slots
     int st_cnt = 0;            // stages committed by this block
     int row_cnt = 0;           // row segments started by this block
     bool ok = true;
@@ -966,6 +1038,13 @@ __global__ void __launch_bounds__(tc05::THREADS) gram_tc05_kernel(const SolvePar
                 }
             }
         }
+        if (want_rhs && tid < R) {
+            float v = 0.f;
+#pragma unroll
+            for (int ww = 0; ww < tc05::THREADS / 32; ++ww) v += rpart[pr.dbuf][ww][tid];
+            if (pr.whole) P.rhs_w[pr.row * (int64_t)R + tid] = v;
+            else add_cut(B.cut_rhs + pr.slot * (int64_t)R + tid, v);
+        }
         tc05::fence_before();
         __syncthreads();              // that accumulator is free again
         return true;
@@ -978,6 +1057,8 @@ __global__ void __launch_bounds__(tc05::THREADS) gram_tc05_kernel(const SolvePar
             const int64_t rs = __ldg(P.row_ptr + i), re = __ldg(P.row_ptr + i + 1);
             const int64_t ss = max(rs, cs), se = min(re, ce);
             const int dbuf = row_cnt & 1;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) racc[j] = 0.f;
             for (int64_t sb = ss; sb < se; sb += tc05::KB) {
                 const int buf = st_cnt & 1;
                 const uint32_t bar = bar0 + 8 * buf;
@@ -994,7 +1075,7 @@ __global__ void __launch_bounds__(tc05::THREADS) gram_tc05_kernel(const SolvePar
                     const int k = 8 * warp + 4 * hh + kl;
                     const int64_t q = sb + k;
                     const bool valid = q < se;
-                    float bv[8], ev[8], sw = 0.f;
+                    float bv[8], ev[8], sw = 0.f, tv = 0.f;
                     if (valid) {
                         const float *br = P.A1 + (int64_t)__ldcs(P.c1 + q) * R;
                         const float *er = P.A2 + (int64_t)__ldcs(P.c2 + q) * R;
@@ -1004,12 +1085,14 @@ __global__ void __launch_bounds__(tc05::THREADS) gram_tc05_kernel(const SolvePar
                             ev[j] = __ldg(er + m0 + 8 * j);
                         }
                         sw = weight_at(P.w, q);
+                        if (want_rhs) tv = __ldcs(P.t + q);
                     }
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
                         const int m = m0 + 8 * j;
                         const float h = valid ? bv[j] * ev[j] : 0.f;
                         const float wh = sw * h;
+                        racc[j] = fmaf(tv, h, racc[j]);
                         const int o = Q::off(m, k);
                         if constexpr (KIND == GK_BF16) {
                             *reinterpret_cast<uint16_t *>(As + o) = tc05::to_bf16(h);
@@ -1045,6 +1128,15 @@ __global__ void __launch_bounds__(tc05::THREADS) gram_tc05_kernel(const SolvePar
                 }
             }
             if (!ok) break;
+            if (want_rhs) {   // this warp's share: its 8 slots per stage, lanes of equal m0 summed
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    float v = racc[j];
+                    v += __shfl_xor_sync(0xffffffffu, v, 1);
+                    v += __shfl_xor_sync(0xffffffffu, v, 2);
+                    if (kl == 0) rpart[dbuf][warp][m0 + 8 * j] = v;
+                }
+            }
             const bool whole = rs >= cs && re <= ce;
             pend = Pending{i, whole ? -1 : cut_slot(rs, re, nb, B.ch), st_cnt - 1, dbuf, whole, true};
             ++row_cnt;
@@ -1244,12 +1336,18 @@ struct WarpMma {
     static constexpr int NTL = Tiles<RT>::NTL;
     static constexpr bool COMP = KIND == GK_TF32X3;
     static constexpr int FOLDK = 16;
-    static constexpr size_t warp_bytes = ((sizeof(float) * (KBW * S + KBW) + 15) / 16) * 16;
+    // per warp: staged h rows, Gram weights, right-hand-side weights
+    static constexpr size_t warp_bytes = ((sizeof(float) * (KBW * S + 2 * KBW) + 15) / 16) * 16;
     static constexpr size_t smem = NW * warp_bytes;
+    // right-hand side: lane l sums component l % RP over the staged rows
+    // k = l / RP, l / RP + 32 / RP, ... (RP: R rounded up to a power of two)
+    static constexpr int RP = RT <= 8 ? 8 : RT <= 16 ? 16 : 32;
     static_assert(KBW % KCH == 0, "whole K steps per stage");
 };
 
-template <int RT, bool VEC, int KIND>
+// RK (RhsKind): what the pass forms beside the Gram -- a compile-time choice,
+// so that the plain Gram keeps its registers (and blocks per SM).
+template <int RT, bool VEC, int KIND, int RK = RHS_GIVEN>
 __global__ void __launch_bounds__(128) gram_warp_mma_kernel(const SolveParams<float> P,
                                                             const Batch<float> B) {
     using Q = WarpMma<RT, KIND>;
@@ -1258,6 +1356,7 @@ __global__ void __launch_bounds__(128) gram_warp_mma_kernel(const SolveParams<fl
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     float *hs = reinterpret_cast<float *>(smem_raw + w * Q::warp_bytes);
     float *ws = hs + KBW * S;
+    float *rws = ws + KBW;      // rhs_kind: the right-hand-side weight of each staged row
     const int g = lane / G, lg = lane % G;
     const int gid = lane >> 2, tig = lane & 3;
     const int R = VEC ? RT : P.R;
@@ -1268,6 +1367,13 @@ __global__ void __launch_bounds__(128) gram_warp_mma_kernel(const SolveParams<fl
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     float d[NTL][4];
     float hi[Q::COMP ? NTL : 1][4], lo[Q::COMP ? NTL : 1][4];
+    // rhs_kind: this lane's share of component lane % RP of the row's
+    // right-hand side, summed from the staged rows (so the staging keeps no
+    // extra registers live)
+    constexpr bool want_rhs = RK != RHS_GIVEN;
+    const int rc_ = lane % Q::RP, rk0 = lane / Q::RP;
+    float racc = 0.f;
+    double lacc = 0.0;  // loss_acc: this lane's share of sum_e phi
     for (int64_t cs = nb + gw * B.ch; cs < ne; cs += nwarps * B.ch) {
         const int64_t ce = min(cs + B.ch, ne);
         int64_t i = search_le(P.row_ptr, B.row0, last, cs);
@@ -1283,6 +1389,7 @@ __global__ void __launch_bounds__(128) gram_warp_mma_kernel(const SolveParams<fl
                     d[u][q] = 0.f;
                     if constexpr (Q::COMP) hi[u][q] = lo[u][q] = 0.f;
                 }
+            racc = 0.f;
             int fc = 0;
             for (int64_t base = ss; base < se; base += KBW) {
 #pragma unroll
@@ -1296,7 +1403,7 @@ __global__ void __launch_bounds__(128) gram_warp_mma_kernel(const SolveParams<fl
 
 #pragma unroll
                     for (int t = 0; t < V; ++t) h[t] = b[t] * e[t];
-                    float sw;
+                    float sw, rw = 0.f;
                     if (P.use_d2) {
                         float part = 0.f;
 #pragma unroll
@@ -1307,8 +1414,13 @@ __global__ void __launch_bounds__(128) gram_warp_mma_kernel(const SolveParams<fl
                         loss_terms(P.loss, __ldcs(P.t + qq), m, phi, d1, d2, ok);
                         if (!ok && valid) record_error(P.status, TC_ERR_DOMAIN);
                         sw = d2;
+                        if constexpr (RK == RHS_DPHI) {
+                            rw = d1;
+                            if (P.loss_acc && valid && lg == 0) lacc += (double)phi;
+                        }
                     } else {
                         sw = weight_at(P.w, qq);
+                        if constexpr (RK == RHS_VALUES) rw = __ldcs(P.t + qq);
                     }
                     if (!valid) {
                         sw = 0.f;
@@ -1317,9 +1429,20 @@ __global__ void __launch_bounds__(128) gram_warp_mma_kernel(const SolveParams<fl
                     }
 #pragma unroll
                     for (int t = 0; t < V; ++t) hs[slot * S + lg * V + t] = h[t];
-                    if (lg == 0) ws[slot] = sw;
+                    if (lg == 0) {
+                        ws[slot] = sw;
+                        if constexpr (want_rhs) rws[slot] = valid ? rw : 0.f;
+                    }
                 }
                 __syncwarp();
+                if constexpr (want_rhs) {
+                    if (rc_ < R) {
+                        const int nk = (int)min((int64_t)KBW, se - base);
+#pragma unroll 1
+                        for (int k = rk0; k < nk; k += 32 / Q::RP)
+                            racc = fmaf(rws[k], hs[k * S + rc_], racc);
+                    }
+                }
                 const int nkc = ((int)min((int64_t)KBW, se - base) + Q::KCH - 1) / Q::KCH;
                 MmaStep<RT, KIND, S> step;
                 for (int kc = 0; kc < nkc; ++kc) {
@@ -1371,9 +1494,21 @@ __global__ void __launch_bounds__(128) gram_warp_mma_kernel(const SolveParams<fl
                         else add_cut(crow + e, d[u][q]);
                     }
                 }
+            if constexpr (want_rhs) {   // the row's right-hand side: lanes of one component summed
+                float v = racc;
+#pragma unroll
+                for (int o = Q::RP; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane < R) {
+                    if (whole) P.rhs_w[i * (int64_t)R + lane] = v;
+                    else add_cut(B.cut_rhs + slot * (int64_t)R + lane, v);
+                }
+            }
             if (re >= ce) break;
             i = search_le_near(P.row_ptr, i + 1, last, re);   // next nonempty row
         }
+    }
+    if constexpr (RK == RHS_DPHI) {
+        if (P.loss_acc) block_add(lacc, P.loss_acc);
     }
 }
 
@@ -1957,6 +2092,11 @@ struct GramLaunch {
                                : (HAS_TC05 && !WARP_MMA) ? 3
                                                          : 0;
     static constexpr bool PER_WARP = VAR == 1 || VAR == 2;
+    // forms an ALS right-hand side (RHS_VALUES) in its own pass; and the
+    // gradient's (RHS_DPHI, with phi'' weights), which solve_fuses_rhs says
+    // on the host
+    static constexpr bool FUSES_RHS = VAR != 1;
+    static constexpr bool FUSES_DPHI = VAR == 2 && KIND == GK_TF32X3;
     static int threads() {
         if constexpr (VAR == 1) return WarpGram<T, RT>::NTH;
         else if constexpr (VAR == 2) return WarpMma<RT, KIND>::NTH;
@@ -1969,45 +2109,65 @@ struct GramLaunch {
         else if constexpr (VAR == 3) return tc05::Geo<KIND>::SMEM;
         else return GramGeo<T, RT, KIND>::smem;
     }
-    static const void *fn() {
+    static const void *fn(int rk = RHS_GIVEN) {
         if constexpr (VAR == 1) return (const void *)gram_warp_kernel<T, RT, VEC>;
-        else if constexpr (VAR == 2) return (const void *)gram_warp_mma_kernel<RT, VEC, KIND>;
+        else if constexpr (VAR == 2) {
+            if (rk == RHS_VALUES) return (const void *)gram_warp_mma_kernel<RT, VEC, KIND, RHS_VALUES>;
+            if constexpr (KIND == GK_TF32X3)
+                if (rk == RHS_DPHI) return (const void *)gram_warp_mma_kernel<RT, VEC, KIND, RHS_DPHI>;
+            return (const void *)gram_warp_mma_kernel<RT, VEC, KIND>;
+        }
         else if constexpr (VAR == 3) return (const void *)gram_tc05_kernel<KIND>;
         else return (const void *)gram_chunk_kernel<T, RT, VEC, KIND>;
     }
     // resident blocks per SM (queried once)
-    static tc_status occupancy(int &occ) {
-        static int cached = 0;
-        if (!cached) {
+    // (per right-hand-side kind: the warp-level kernel's variants differ in
+    // registers)
+    static tc_status occupancy(int &occ, int rk = RHS_GIVEN) {
+        static int cached[3] = {0, 0, 0};
+        const int slot = rk >= 0 && rk < 3 ? rk : 0;
+        if (!cached[slot]) {
+            const void *f = fn(rk);
             if (smem() > 48 * 1024) {
-                TC_CUDA(cudaFuncSetAttribute(fn(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem()));
+                TC_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem()));
                 // the whole unified L1 / shared array as shared memory, so that
                 // several blocks of this size fit per SM (the occupancy query
                 // below assumes the carveout set here)
-                TC_CUDA(cudaFuncSetAttribute(fn(), cudaFuncAttributePreferredSharedMemoryCarveout,
+                TC_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
                                              (int)cudaSharedmemCarveoutMaxShared));
             }
             int v = 0;
-            TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, fn(), threads(), smem()));
+            TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, f, threads(), smem()));
             if constexpr (VAR == 3) {
                 // the tcgen05 kernel: the query answers 1 block per SM (measured);
-                // shared memory (with 1 KB reserved per block), 64 registers per
-                // thread and 128 of the 512 TMEM columns per block allow more
+                // shared memory (with 1 KB reserved per block), at most 128
+                // registers per thread and 128 of the 512 TMEM columns per block
+                // allow more
                 int by_smem = (int)((228 * 1024) / (smem() + 1024 + 64));
                 const int by_tmem = 512 / (int)tc05::TMEM_COLS;
                 if (by_smem > by_tmem) by_smem = by_tmem;
                 if (by_smem > v) v = by_smem;
             }
-            cached = v > 0 ? v : 1;
+            cached[slot] = v > 0 ? v : 1;
         }
-        occ = cached;
+        occ = cached[slot];
         return TC_OK;
     }
     static void launch(int64_t grid, const SolveParams<T> &P, const Batch<T> &Bt, cudaStream_t st) {
         if constexpr (VAR == 1)
             gram_warp_kernel<T, RT, VEC><<<(unsigned)grid, threads(), smem(), st>>>(P, Bt);
-        else if constexpr (VAR == 2)
-            gram_warp_mma_kernel<RT, VEC, KIND><<<(unsigned)grid, threads(), smem(), st>>>(P, Bt);
+        else if constexpr (VAR == 2) {
+            if (P.rhs_kind == RHS_VALUES)
+                gram_warp_mma_kernel<RT, VEC, KIND, RHS_VALUES><<<(unsigned)grid, threads(), smem(), st>>>(P, Bt);
+            else if constexpr (KIND == GK_TF32X3) {
+                if (P.rhs_kind == RHS_DPHI)
+                    gram_warp_mma_kernel<RT, VEC, KIND, RHS_DPHI><<<(unsigned)grid, threads(), smem(), st>>>(P, Bt);
+                else
+                    gram_warp_mma_kernel<RT, VEC, KIND><<<(unsigned)grid, threads(), smem(), st>>>(P, Bt);
+            } else {
+                gram_warp_mma_kernel<RT, VEC, KIND><<<(unsigned)grid, threads(), smem(), st>>>(P, Bt);
+            }
+        }
         else if constexpr (VAR == 3)
             gram_tc05_kernel<KIND><<<(unsigned)grid, threads(), smem(), st>>>(P, Bt);
         else
@@ -2016,15 +2176,25 @@ struct GramLaunch {
 };
 
 template <typename T, int RT, bool VEC, int KIND, bool CHOL32, bool WARP_MMA>
-static tc_status launch_solve_gl(const SolveParams<T> &P, int64_t m, const tc_solve_tuning &tun,
-                                 const tc_pattern *pat, int mode, cudaStream_t st) {
+static tc_status launch_solve_gl(const SolveParams<T> &P0, int64_t m, const tc_solve_tuning &tun,
+                                 const tc_pattern *pat, int mode, const void *const *A,
+                                 cudaStream_t st) {
     using GL = GramLaunch<T, RT, VEC, KIND, WARP_MMA>;
+    SolveParams<T> P = P0;
+    if (P.rhs_kind == RHS_VALUES && !GL::FUSES_RHS) {
+        // a Gram kernel that does not form the right-hand side: the MTTKRP of
+        // the values first, then an ordinary solve on it
+        const tc_status rc = launch_mttkrp(pat, TC_W_VALUES, nullptr, P.R, A, mode, P.rhs_w, 0, st);
+        if (rc != TC_OK) return rc;
+        P.rhs_kind = RHS_GIVEN;
+    }
+    if (P.rhs_kind == RHS_DPHI && !GL::FUSES_DPHI) return TC_ERR_UNSUPPORTED;   // see solve_fuses_rhs
     using CT = typename std::conditional<CHOL32, float, double>::type;   // factorization type
     const int R = P.R, tri = R * (R + 1) / 2;
     const int sms = device_sms();
     int occ = 1;
     {
-        const tc_status rc = GL::occupancy(occ);
+        const tc_status rc = GL::occupancy(occ, P.rhs_kind);
         if (rc != TC_OK) return rc;
     }
     const int64_t grid_a = (int64_t)sms * occ;
@@ -2067,15 +2237,28 @@ static tc_status launch_solve_gl(const SolveParams<T> &P, int64_t m, const tc_so
     double *cut = (double *)work_buffer(pat, WS_SOLVE_CUT + mode, sizeof(double) * (size_t)tri * slots);
     double *res = nullptr;
     if (P.refine) res = (double *)work_buffer(pat, WS_SOLVE_RES + mode, sizeof(double) * (size_t)R * batch);
-    if (!light || !cut || (P.refine && !res)) return TC_ERR_OOM;
+    double *cut_rhs = nullptr;
+    if (P.rhs_kind != RHS_GIVEN)
+        cut_rhs = (double *)work_buffer(pat, WS_SOLVE_CUT_RHS + mode, sizeof(double) * (size_t)R * slots);
+    if (!light || !cut || (P.refine && !res) || (P.rhs_kind != RHS_GIVEN && !cut_rhs)) return TC_ERR_OOM;
     const int64_t nblk_w0 = (int64_t)sms * 16;
     for (int64_t row0 = 0; row0 < P.I; row0 += batch) {
-        Batch<T> Bt{row0, min(batch, P.I - row0), ch, light, cut, res};
-        int64_t zb = (slots * tri + 255) / 256;
+        Batch<T> Bt{row0, min(batch, P.I - row0), ch, light, cut, res, cut_rhs};
+        int64_t zb = (slots * (tri + (cut_rhs ? R : 0)) + 255) / 256;
         if (zb > (int64_t)sms * 4) zb = (int64_t)sms * 4;
         if (zb < 1) zb = 1;
-        zero_cut_kernel<T><<<(unsigned)zb, 256, 0, st>>>(P.row_ptr, Bt, tri);
+        zero_cut_kernel<T><<<(unsigned)zb, 256, 0, st>>>(P.row_ptr, Bt, tri, R);
+        if (P.rhs_kind != RHS_GIVEN)   // empty rows keep a zero right-hand side
+            TC_CUDA(cudaMemsetAsync(P.rhs_w + row0 * (int64_t)R, 0,
+                                    sizeof(T) * (size_t)Bt.nrows * R, st));
         GL::launch(grid_a, P, Bt, st);
+        if (P.rhs_kind != RHS_GIVEN) {
+            int64_t fb = (slots * R + 255) / 256;
+            if (fb > (int64_t)sms * 4) fb = (int64_t)sms * 4;
+            if (fb < 1) fb = 1;
+            cut_rhs_kernel<T><<<(unsigned)fb, 256, 0, st>>>(P.row_ptr, Bt, R, P.rhs_w);
+            count_launch();
+        }
         int64_t nblk_w = (Bt.nrows + kCholWarps - 1) / kCholWarps;
         if (nblk_w > nblk_w0) nblk_w = nblk_w0;
         if (warp_b)
@@ -2096,21 +2279,22 @@ static tc_status launch_solve_gl(const SolveParams<T> &P, int64_t m, const tc_so
 // The Gram engine: the tuned choice where both exist.
 template <typename T, int RT, bool VEC, int KIND, bool CHOL32>
 static tc_status launch_solve_rt(const SolveParams<T> &P, int64_t m, const tc_solve_tuning &tun,
-                                 const tc_pattern *pat, int mode, cudaStream_t st) {
+                                 const tc_pattern *pat, int mode, const void *const *A,
+                                 cudaStream_t st) {
     if constexpr (GramLaunch<T, RT, VEC, KIND>::HAS_TC05) {
         if (tun.gram_kernel == TC_GRAM_WARP_MMA)
-            return launch_solve_gl<T, RT, VEC, KIND, CHOL32, true>(P, m, tun, pat, mode, st);
+            return launch_solve_gl<T, RT, VEC, KIND, CHOL32, true>(P, m, tun, pat, mode, A, st);
     }
-    return launch_solve_gl<T, RT, VEC, KIND, CHOL32, false>(P, m, tun, pat, mode, st);
+    return launch_solve_gl<T, RT, VEC, KIND, CHOL32, false>(P, m, tun, pat, mode, A, st);
 }
 
 template <typename T, int KIND, bool C32>
 static tc_status dispatch_rt(const SolveParams<T> &P, int tier, bool vec, int64_t m,
                              const tc_solve_tuning &tun, const tc_pattern *pat, int mode,
-                             cudaStream_t st) {
+                             const void *const *A, cudaStream_t st) {
 #define TC_SOLVE_RT(RT)                                                                     \
-    return vec ? launch_solve_rt<T, RT, true, KIND, C32>(P, m, tun, pat, mode, st)          \
-               : launch_solve_rt<T, RT, false, KIND, C32>(P, m, tun, pat, mode, st)
+    return vec ? launch_solve_rt<T, RT, true, KIND, C32>(P, m, tun, pat, mode, A, st)       \
+               : launch_solve_rt<T, RT, false, KIND, C32>(P, m, tun, pat, mode, A, st)
     switch (tier) {
         case 8: TC_SOLVE_RT(8);
         case 16: TC_SOLVE_RT(16);
@@ -2124,7 +2308,9 @@ template <typename T>
 static tc_status solve_t(const tc_pattern *p, tc_weights w, const void *s, int R,
                          const void *const *A, int mode, const void *rhs, double lambda,
                          tc_prec prec, void *out, int8_t *row_status, int use_d2, tc_loss loss,
-                         void *pinv, cudaStream_t st, const tc_solve_tuning &tun) {
+                         void *pinv, cudaStream_t st, const tc_solve_tuning &tun,
+                         int rhs_kind = RHS_GIVEN, void *rhs_out = nullptr,
+                         double *loss_acc = nullptr) {
     const ModeData &md = p->md[mode];
     int o1, o2;
     other_modes(mode, o1, o2);
@@ -2169,9 +2355,19 @@ static tc_status solve_t(const tc_pattern *p, tc_weights w, const void *s, int R
     const int64_t m = p->nnz;
     if (sizeof(T) == 8 && (form == TC_PREC_TF32_REFINE || form == TC_PREC_BF16_REFINE))
         return TC_ERR_UNSUPPORTED;
-    // the correction step reads rhs after the solve wrote out: keep a copy
-    // when they alias
-    if (P.refine && (const void *)P.out == (const void *)P.rhs) {
+    if (rhs_kind != RHS_GIVEN) {
+        // the right-hand side is formed here: into the pattern's work space
+        // (an ALS update) or into the caller's buffer (a gradient)
+        P.rhs_w = rhs_kind == RHS_DPHI
+                      ? (T *)rhs_out
+                      : (T *)work_buffer(p, WS_SOLVE_RHS + mode, sizeof(T) * (size_t)P.I * R);
+        if (!P.rhs_w) return TC_ERR_OOM;
+        P.rhs = P.rhs_w;
+        P.rhs_kind = rhs_kind;
+        P.loss_acc = loss_acc;
+    } else if (P.refine && (const void *)P.out == (const void *)P.rhs) {
+        // the correction step reads rhs after the solve wrote out: keep a
+        // copy when they alias
         const size_t bytes = sizeof(T) * (size_t)P.I * R;
         T *rhs_copy = (T *)work_buffer(p, WS_SOLVE_RHS + mode, bytes);
         if (!rhs_copy) return TC_ERR_OOM;
@@ -2181,8 +2377,8 @@ static tc_status solve_t(const tc_pattern *p, tc_weights w, const void *s, int R
     tc_status rc = TC_OK;
     const bool c32 = (prec & TC_PREC_CHOL32) != 0 && P.refine;
 #define TC_SOLVE_KIND(K)                                                          \
-    (c32 ? dispatch_rt<T, K, true>(P, tier, vec, m, tun, p, mode, st)             \
-         : dispatch_rt<T, K, false>(P, tier, vec, m, tun, p, mode, st))
+    (c32 ? dispatch_rt<T, K, true>(P, tier, vec, m, tun, p, mode, A, st)          \
+         : dispatch_rt<T, K, false>(P, tier, vec, m, tun, p, mode, A, st))
     if constexpr (sizeof(T) == 4) {
         if (form == TC_PREC_TF32_REFINE) rc = TC_SOLVE_KIND(GK_TF32);
         else if (form == TC_PREC_BF16_REFINE) rc = TC_SOLVE_KIND(GK_BF16);
@@ -2310,6 +2506,31 @@ tc_status launch_solve_factor(const tc_pattern *p, tc_weights w, const void *s, 
                                use_loss_d2, loss, pinv_out, st, t);
     return solve_t<float>(p, w, s, R, A, mode, rhs, lambda, prec, out, row_status, use_loss_d2,
                           loss, pinv_out, st, t);
+}
+
+tc_status launch_als_update(const tc_pattern *p, int R, const void *const *A, int mode,
+                            double lambda, tc_prec prec, void *out, int8_t *row_status,
+                            cudaStream_t st) {
+    const tc_solve_tuning t = solve_tuning(p->dtype, R);
+    if (p->dtype == TC_F64)
+        return solve_t<double>(p, TC_W_ONE, nullptr, R, A, mode, nullptr, lambda, prec, out,
+                               row_status, 0, TC_LOSS_LS, nullptr, st, t, RHS_VALUES);
+    return solve_t<float>(p, TC_W_ONE, nullptr, R, A, mode, nullptr, lambda, prec, out,
+                          row_status, 0, TC_LOSS_LS, nullptr, st, t, RHS_VALUES);
+}
+
+bool solve_fuses_rhs(tc_dtype dtype, int R) {
+    // GramLaunch<float, RT <= 32, *, FP32-class or tensor-core form>::FUSES_DPHI
+    return dtype == TC_F32 && rank_tier(R) <= 32;
+}
+
+tc_status launch_precond_grad(const tc_pattern *p, int R, const void *const *A, int mode,
+                              double lambda2, tc_loss loss, void *pinv_out, void *grad_out,
+                              double *loss_acc, cudaStream_t st) {
+    if (!solve_fuses_rhs(p->dtype, R)) return TC_ERR_UNSUPPORTED;
+    const tc_solve_tuning t = solve_tuning(p->dtype, R);
+    return solve_t<float>(p, TC_W_ONE, nullptr, R, A, mode, nullptr, lambda2, TC_PREC_FP32,
+                          nullptr, nullptr, 1, loss, pinv_out, st, t, RHS_DPHI, grad_out, loss_acc);
 }
 
 }  // namespace tc

@@ -642,6 +642,15 @@ static tc_status mttkrp_t(const tc_pattern *p, tc_weights w, const void *s, int 
     return TC_OK;
 }
 
+tc_status launch_regularizer(const tc_pattern *p, int R, const void *const *A, double lambda,
+                             double *acc, cudaStream_t st) {
+    for (int n = 0; n < TC_ORDER; ++n) {
+        if (p->dtype == TC_F64) launch_sumsq<double>((const double *)A[n], p->dims[n] * R, lambda, acc, st);
+        else launch_sumsq<float>((const float *)A[n], p->dims[n] * R, lambda, acc, st);
+    }
+    return cudaGetLastError() == cudaSuccess ? TC_OK : TC_ERR_CUDA;
+}
+
 tc_status launch_mttkrp(const tc_pattern *p, tc_weights w, const void *s, int R,
                         const void *const *A, int mode, void *out, int accumulate,
                         cudaStream_t st) {

@@ -15,15 +15,21 @@ from . import tc
 
 
 def als_sweep(p: "tc.Pattern", factors, lam: float, rhs=None, row_status=None, prec="fp32",
-              stream=None):
-    """One ALS sweep in place over modes 0, 1, 2.  rhs: optional work buffers;
-    prec: the Solve Factor precision form (tc.PRECS)."""
+              stream=None, fused=True):
+    """One ALS sweep in place over modes 0, 1, 2; prec: the Solve Factor
+    precision form (tc.PRECS).  fused: each mode in one tc_als_update (the
+    right-hand side formed in the Gram pass); otherwise tc_mttkrp into rhs[d]
+    (optional work buffers) and tc_solve_factor."""
     for d in range(len(factors)):
+        rs = None if row_status is None else row_status[d]
+        if fused:
+            tc.als_update(p, factors, d, lam, out=factors[d], row_status=rs, prec=prec,
+                          stream=stream)
+            continue
         b = tc.mttkrp(p, factors, d, weights="values", out=None if rhs is None else rhs[d],
                       stream=stream)
-        tc.solve_factor(p, factors, d, b, lam, weights=None, out=factors[d],
-                        row_status=None if row_status is None else row_status[d], prec=prec,
-                        stream=stream)
+        tc.solve_factor(p, factors, d, b, lam, weights=None, out=factors[d], row_status=rs,
+                        prec=prec, stream=stream)
     return factors
 
 

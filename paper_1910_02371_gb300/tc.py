@@ -52,6 +52,7 @@ _SIGS = {
     "tc_tttp": [_P, _I, _P, _I, _P, _P, _P],
     "tc_mttkrp": [_P, _I, _P, _I, _P, _I, _P, _I, _P],
     "tc_solve_factor": [_P, _I, _P, _I, _P, _I, _P, _D, _I, _P, _P, _P],
+    "tc_als_update": [_P, _I, _P, _I, _D, _I, _P, _P, _P],
     "tc_loss_grad": [_P, _I, _I, _P, _D, _P, _P, _P],
     "tc_ggn_matvec": [_P, _I, _I, _P, _P, _D, _P, _P],
     "tc_cg_create": [_P, _I, _I, _P, _D, _I, _P],
@@ -277,6 +278,19 @@ def solve_factor(p: Pattern, factors, mode: int, rhs: torch.Tensor, lam: float, 
                                 float(lam), PRECS[prec], _ptr(out), _ptr(row_status),
                                 _stream(stream)),
            "tc_solve_factor")
+    return out
+
+
+def als_update(p: Pattern, factors, mode: int, lam: float, out=None, row_status=None,
+               prec: str = "fp32", stream=None):
+    """tc_als_update: one least-squares ALS update of factors[mode] -- the
+    MTTKRP of the values and Solve Factor in one call.  out defaults to
+    factors[mode] (in place)."""
+    R = factors[0].shape[1]
+    if out is None:
+        out = factors[mode]
+    _check(_lib.tc_als_update(p.handle, R, _ptrs(factors), mode, float(lam), PRECS[prec],
+                              _ptr(out), _ptr(row_status), _stream(stream)), "tc_als_update")
     return out
 
 
