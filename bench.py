@@ -76,13 +76,13 @@ NCU_TRAFFIC = {
     ("cp3_10k_m10M_r16", "ggn_matvec"): {"bytes": 3 * 36.65e6 * 2.5,
                                          "file": "paper_1910_02371_gb300/csrc/sweep.cu",
                                          "src": "1d03ab541fb6d2df"},
-    # 1e8-nonzero capture at the same 2^22 rows per mode (26.915 GB read +
-    # 0.281 GB written per launch: every row gather misses L2 at both sizes)
+    # 1e8-nonzero capture at the same 2^22 rows per mode (26.914 GB read +
+    # 0.280 GB written per launch: every row gather misses L2 at both sizes)
     # scaled to 4e9
-    ("cp3_4M_m4B_r16", "ggn_matvec"): {"bytes": 3 * (26.9152e9 + 0.2806e9) * 40,
+    ("cp3_4M_m4B_r16", "ggn_matvec"): {"bytes": 3 * (26.9144e9 + 0.2805e9) * 40,
                                        "file": ["paper_1910_02371_gb300/csrc/sweep.cu",
                                                 "paper_1910_02371_gb300/csrc/internal.cuh"],
-                                       "src": "469999f7e26a0145"},
+                                       "src": "f069761d853dfe63"},
 }
 
 

@@ -1371,7 +1371,7 @@ __global__ void __launch_bounds__(128) gram_warp_mma_kernel(const SolveParams<fl
     // right-hand side, summed from the staged rows (so the staging keeps no
     // extra registers live)
     constexpr bool want_rhs = RK != RHS_GIVEN;
-    const int rc_ = lane % Q::RP, rk0 = lane / Q::RP;
+    const int rcomp = lane % Q::RP, rk0 = lane / Q::RP;
     float racc = 0.f;
     double lacc = 0.0;  // loss_acc: this lane's share of sum_e phi
     for (int64_t cs = nb + gw * B.ch; cs < ne; cs += nwarps * B.ch) {
@@ -1436,11 +1436,11 @@ __global__ void __launch_bounds__(128) gram_warp_mma_kernel(const SolveParams<fl
                 }
                 __syncwarp();
                 if constexpr (want_rhs) {
-                    if (rc_ < R) {
+                    if (rcomp < R) {
                         const int nk = (int)min((int64_t)KBW, se - base);
 #pragma unroll 1
                         for (int k = rk0; k < nk; k += 32 / Q::RP)
-                            racc = fmaf(rws[k], hs[k * S + rc_], racc);
+                            racc = fmaf(rws[k], hs[k * S + rcomp], racc);
                     }
                 }
                 const int nkc = ((int)min((int64_t)KBW, se - base) + Q::KCH - 1) / Q::KCH;
