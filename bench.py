@@ -72,10 +72,11 @@ def metric_of(w):
 # nonzero count (the capture size rule keeps multi-pass ncu runs off the full
 # workload).
 NCU_TRAFFIC = {
-    # 4e6-nonzero capture (36.65 MB read per launch) scaled to 1e7
-    ("cp3_10k_m10M_r16", "ggn_matvec"): {"bytes": 3 * 36.65e6 * 2.5,
-                                         "file": "paper_1910_02371_gb300/csrc/sweep.cu",
-                                         "src": "1d03ab541fb6d2df"},
+    # 4e6-nonzero capture (36.64 MB read per launch) scaled to 1e7
+    ("cp3_10k_m10M_r16", "ggn_matvec"): {"bytes": 3 * 36.64e6 * 2.5,
+                                         "file": ["paper_1910_02371_gb300/csrc/sweep.cu",
+                                                  "paper_1910_02371_gb300/csrc/internal.cuh"],
+                                         "src": "f069761d853dfe63"},
     # 1e8-nonzero capture at the same 2^22 rows per mode (26.914 GB read +
     # 0.280 GB written per launch: every row gather misses L2 at both sizes)
     # scaled to 4e9
