@@ -267,7 +267,7 @@ tc_status tc_als_update(const tc_pattern *p, int R, const void *const *factors, 
  *   chol_rows_per_warp  for R <= 32 one warp factors this many rows
  *                together, 32 / rows lanes sharing each row's work; fewer
  *                rows per warp spread a small mode over more warps
- *                (0: automatic, 16 for R <= 16 and 8 for R <= 32).
+ *                (0: automatic, 16 for R <= 16 and 4 for R <= 32).
  *   gram_kernel  the Gram engine where two exist -- FP32 data, R = 64, the
  *                TF32 and BF16 forms: TC_GRAM_AUTO (0, the tcgen05 kernel),
  *                TC_GRAM_WARP_MMA (warp-level mma.sync, 4-warp blocks

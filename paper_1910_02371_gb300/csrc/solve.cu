@@ -2203,10 +2203,14 @@ static tc_status launch_solve_gl(const SolveParams<T> &P0, int64_t m, const tc_s
 
     const bool warp_b = RT > 32;
     // rows per warp of the R <= 32 factorization (32 / rpw lanes per row):
-    // 16 for R <= 16, 8 for R = 32, so that a mode of 10^4 rows still spreads
-    // over several warps per SM (each row's FP64 triangle takes R(R+1)/2 * 8
-    // bytes of shared memory, twice that in inverse mode)
-    int rpw = RT <= 16 ? 16 : 8;
+    // 16 for R <= 16, 4 for R = 32.  Each row's FP64 triangle takes
+    // R(R+1)/2 * 8 bytes of shared memory (twice that in inverse mode), so at
+    // R = 32 fewer rows per one-warp block fit more blocks per SM: measured on
+    // GB300, 4.70 / 5.28 / 7.75 ms at 4 / 8 / 16 for a 5e4-row mode; at R = 16
+    // 0.361 / 0.338 / 0.356 / 0.408 ms at 4 / 8 / 16 / 32 for a 1e4-row mode,
+    // where larger modes favour fewer lanes per row (each warp computes its
+    // rows' pivots once whatever its lanes per row)
+    int rpw = RT <= 16 ? 16 : 4;
     if (tun.chol_rows_per_warp > 0) rpw = tun.chol_rows_per_warp < 32 ? tun.chol_rows_per_warp : 32;
     if (RT > 16 && rpw > 16) rpw = 16;
     const int align = warp_b ? kCholWarps : rpw;

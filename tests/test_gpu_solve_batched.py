@@ -26,6 +26,9 @@ CASES = {
     "zipf_f32_r7": dict(dims=(3000, 400, 30), nnz=40000, R=7, dtype="f32",
                         dist=("zipf", "zipf", "uniform")),
     "uni_f32_r16": dict(dims=(2000, 2000, 2000), nnz=200000, R=16, dtype="f32"),
+    "zipf_f32_r32": dict(dims=(3000, 500, 60), nnz=50000, R=32, dtype="f32",
+                         dist=("zipf", "zipf", "uniform")),
+    "f64_r24": dict(dims=(400, 300, 80), nnz=20000, R=24, dtype="f64"),
 }
 # (chunk_nnz, batch_bytes, chol_rows_per_warp): automatic, tiny chunks (nearly
 # every row is cut), odd chunks with one warp's rows per batch, a chunk longer
@@ -101,7 +104,8 @@ def row_conditions(prob, mode, lam2, weight=2.0):
     return kappa
 
 
-@pytest.mark.parametrize("name", ["zipf_f32_r64", "f32_r40", "zipf_f32_r16", "f64_r64"])
+@pytest.mark.parametrize("name", ["zipf_f32_r64", "f32_r40", "zipf_f32_r16", "f64_r64",
+                                  "zipf_f32_r32", "f64_r24"])
 @pytest.mark.parametrize("tuning", [(0, 0, 0), (37, 1, 4)])
 def test_preconditioner_uneven_rows(tc, name, tuning):
     """The preconditioner is an operator built once from an FP32 (or FP64)
