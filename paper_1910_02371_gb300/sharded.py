@@ -68,6 +68,10 @@ class LibtcOps:
     def solve_factor(self, h, A, d, rhs, lam, out, prec="fp32"):
         return self.tc.solve_factor(h, A, d, rhs, lam, out=out, prec=prec)
 
+    def als_update(self, h, A, d, lam, out, prec="fp32"):
+        # the MTTKRP of the values and Solve Factor in one pass over the block
+        return self.tc.als_update(h, A, d, lam, out=out, prec=prec)
+
     def loss(self, h, A, loss, lam):
         f, _ = self.tc.loss_grad(h, A, loss, lam, want_grad=False)
         return f
@@ -171,12 +175,11 @@ class ShardedCP:
 
     def als_sweep(self, A, prec="fp32"):
         """One ALS sweep (Sec. 2.2) in place: for each mode the owned rows are
-        solved locally from the mode's block, then all-gathered."""
+        solved locally from the mode's block (its MTTKRP and Solve Factor, one
+        ops.als_update), then all-gathered."""
         for d in range(3):
-            rhs = self.ops.empty(A[d].shape, A[d])
-            self.ops.mttkrp(self.block[d], A, d, rhs)
             new = self.ops.empty(A[d].shape, A[d])
-            self.ops.solve_factor(self.block[d], A, d, rhs, self.lam, new, prec)
+            self.ops.als_update(self.block[d], A, d, self.lam, new, prec)
             lo, hi = self.own(d)
             A[d][lo:hi] = new[lo:hi]
             self._allgather_rows(A[d], d)

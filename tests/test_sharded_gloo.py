@@ -46,6 +46,10 @@ class OracleOps:
         assert rc == 0
         out.copy_(torch.from_numpy(res))
 
+    def als_update(self, h, A, d, lam, out, prec="fp32"):
+        rhs = torch.from_numpy(self.o.mttkrp(h["dims"], h["idx"], h["t"], self._np(A), d))
+        self.solve_factor(h, A, d, rhs, lam, out, prec)
+
     def loss(self, h, A, loss, lam):
         f, _ = self.o.loss_grad(h["dims"], h["idx"], h["t"], self._np(A), loss, lam, want_grad=False)
         return torch.tensor([f], dtype=torch.float64)
