@@ -16,13 +16,18 @@
 // forms for the refined mixed-precision solves).  At the end of a row's
 // segment the packed lower triangle is written: plainly when the whole row
 // lies in the chunk, otherwise added with FP64 atomics into a zeroed slot
-// owned by the first chunk boundary the row crosses.
+// owned by the first chunk boundary the row crosses.  The same pass can also
+// form a right-hand side from the gathered rows (RhsKind): sum_e t_e h_e for
+// an ALS update, or sum_e phi'_e h_e (the gradient's MTTKRP) with the loss
+// for a Gauss-Newton preconditioner block; cut rows' shares go to FP64 slots.
 //
 // Kernel B runs the FP64 part: lambda on the diagonal, the unpivoted Cholesky
 // factorization, then the two triangular solves, or the inverse
-// (L L^T)^-1 = L^-T L^-1 for the preconditioner.  For R <= 32 one lane owns
-// one row (every FP64 instruction does a warp of useful work); for R > 32 a
-// warp owns one row and the trailing updates are spread evenly over the lanes.
+// (L L^T)^-1 = L^-T L^-1 for the preconditioner.  For R <= 32 a warp factors
+// 16 (R <= 16) or 4 (R = 32) rows together, the lanes of a row sharing each
+// step's work (every FP64 instruction does a warp of useful work); for R > 32
+// a warp owns one row and the trailing updates are spread evenly over the
+// lanes.
 #include <type_traits>
 
 #include "internal.cuh"
@@ -832,9 +837,12 @@ __global__ void __launch_bounds__(GramShape<T, RT, KIND>::NTH, 2)
 // of A stay zero, and D's rows 0..63 (TMEM lanes 0..63) hold G_i.  At the
 // row's end warps 0 and 1 read them (tcgen05.ld) and write the packed lower
 // triangle, or add it with FP64 atomics into the cut slot of a row that
-// crosses a chunk boundary.  Every mbarrier wait has a time limit; past it the
-// block records TC_ERR_TIMEOUT, lets its committed MMAs finish (bounded),
-// frees its TMEM and leaves.
+// crosses a chunk boundary.  For an ALS update each thread also sums t_e h_e
+// for its components (FP32, on the CUDA cores: a TF32 or BF16 right-hand side
+// would not do), the warps' shares meet in shared memory and the segment's
+// epilogue writes the row's right-hand side.  Every mbarrier wait has a time
+// limit; past it the block records TC_ERR_TIMEOUT, lets its committed MMAs
+// finish (bounded), frees its TMEM and leaves.
 namespace tc05 {
 
 constexpr int KB = 32;          // nonzeros per stage
