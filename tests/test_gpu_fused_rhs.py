@@ -32,6 +32,8 @@ CASES = {
                          dist=("zipf", "zipf", "uniform")),
     "zipf_f64_r16": dict(dims=(2000, 300, 40), nnz=30000, R=16, dtype="f64",
                          dist=("zipf", "zipf", "uniform")),
+    "zipf_f64_r24": dict(dims=(1500, 300, 40), nnz=25000, R=24, dtype="f64",
+                         dist=("zipf", "zipf", "uniform")),
     # more rows than the coordinates reach: empty rows solve lambda a_i = 0
     "sparse_f32_r16": dict(dims=(20000, 3000, 50), nnz=20000, R=16, dtype="f32"),
 }
