@@ -55,3 +55,27 @@ def test_setter_rejects_bad_values(mods):
         tc.set_solve_tuning(torch.float32, 65)
     with pytest.raises(tc.TcError):
         tc.set_solve_tuning(torch.float32, 64, gram_kernel=3)
+
+
+def test_record_without_gram_kernel_installs_the_automatic_engine(mods, tmp_path):
+    """Records written before the Gram engine was a tuning dimension carry no
+    gram_kernel: applying one installs the automatic engine (0); a record
+    with one installs it."""
+    torch, tc, tuning = mods
+    k64 = tuning.shape_key(torch.float32, 64, 480_000, 100_000_000, "tf32_refine")
+    k16 = tuning.shape_key(torch.float32, 16, 10_000, 10_000_000)
+    path = tmp_path / "old.json"
+    path.write_text(json.dumps({k16: {"chunk_nnz": 4096, "batch_bytes": 0, "chol_rows_per_warp": 8,
+                                      "ms": 0.3},
+                                k64: {"chunk_nnz": 0, "batch_bytes": 0, "chol_rows_per_warp": 0,
+                                      "gram_kernel": tc.GRAM_WARP_MMA, "ms": 140.0}}))
+    tuning._records.clear()
+    tuning.load(str(path))
+    try:
+        assert tuning.apply(torch.float32, 16, 10_000, 10_000_000)
+        assert tc.get_solve_tuning(torch.float32, 16) == (4096, 0, 8, 0)
+        assert tuning.apply(torch.float32, 64, 480_000, 100_000_000, "tf32_refine")
+        assert tc.get_solve_tuning(torch.float32, 64) == (0, 0, 0, tc.GRAM_WARP_MMA)
+    finally:
+        tc.set_solve_tuning(torch.float32, 0, reset=True)
+        tuning._records.clear()
