@@ -76,14 +76,14 @@ NCU_TRAFFIC = {
     ("cp3_10k_m10M_r16", "ggn_matvec"): {"bytes": 3 * 36.64e6 * 2.5,
                                          "file": ["paper_1910_02371_gb300/csrc/sweep.cu",
                                                   "paper_1910_02371_gb300/csrc/internal.cuh"],
-                                         "src": "f069761d853dfe63"},
+                                         "src": "f6a6ccaa2cb4861c"},
     # 1e8-nonzero capture at the same 2^22 rows per mode (26.914 GB read +
     # 0.280 GB written per launch: every row gather misses L2 at both sizes)
     # scaled to 4e9
     ("cp3_4M_m4B_r16", "ggn_matvec"): {"bytes": 3 * (26.9144e9 + 0.2805e9) * 40,
                                        "file": ["paper_1910_02371_gb300/csrc/sweep.cu",
                                                 "paper_1910_02371_gb300/csrc/internal.cuh"],
-                                       "src": "f069761d853dfe63"},
+                                       "src": "f6a6ccaa2cb4861c"},
 }
 
 

@@ -32,6 +32,7 @@
 
 #include "internal.cuh"
 
+#include <atomic>
 #include <mutex>
 
 namespace tc {
@@ -2057,17 +2058,19 @@ __global__ void __launch_bounds__(kCholWarps * 32) refine_correct_kernel(const S
 }
 
 // ------------------------------------------------------------------ host side
+// SM count per device, queried once (host threads may race to fill an entry;
+// they store the same value, and the atomics make that well defined)
 static int device_sms() {
-    static int sms[64] = {0};
+    static std::atomic<int> sms[64];
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
-    if (!sms[dev]) {
-        int v = 0;
+    int v = sms[dev].load(std::memory_order_relaxed);
+    if (!v) {
         if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0)
             v = 152;
-        sms[dev] = v;
+        sms[dev].store(v, std::memory_order_relaxed);
     }
-    return sms[dev];
+    return v;
 }
 
 // Process-wide tuning per dtype and rank tier (0 = automatic), read and
@@ -2130,11 +2133,12 @@ struct GramLaunch {
     }
     // resident blocks per SM (queried once)
     // (per right-hand-side kind: the warp-level kernel's variants differ in
-    // registers)
+    // registers; host threads may race to fill an entry with the same value)
     static tc_status occupancy(int &occ, int rk = RHS_GIVEN) {
-        static int cached[3] = {0, 0, 0};
+        static std::atomic<int> cached[3];
         const int slot = rk >= 0 && rk < 3 ? rk : 0;
-        if (!cached[slot]) {
+        int have = cached[slot].load(std::memory_order_relaxed);
+        if (!have) {
             const void *f = fn(rk);
             if (smem() > 48 * 1024) {
                 TC_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem()));
@@ -2156,9 +2160,10 @@ struct GramLaunch {
                 if (by_smem > by_tmem) by_smem = by_tmem;
                 if (by_smem > v) v = by_smem;
             }
-            cached[slot] = v > 0 ? v : 1;
+            have = v > 0 ? v : 1;
+            cached[slot].store(have, std::memory_order_relaxed);
         }
-        occ = cached[slot];
+        occ = have;
         return TC_OK;
     }
     static void launch(int64_t grid, const SolveParams<T> &P, const Batch<T> &Bt, cudaStream_t st) {

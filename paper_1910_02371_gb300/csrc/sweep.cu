@@ -13,6 +13,7 @@
 // chunks may share, are added atomically.
 #include "internal.cuh"
 
+#include <atomic>
 #include <mutex>
 #include <unordered_map>
 
@@ -450,15 +451,19 @@ __global__ void sumsq_kernel(const T *__restrict__ x, int64_t n, double scale, d
 }
 
 // ------------------------------------------------------------------ launchers
-static int g_sm_count = 0;
+// SM count, queried once (host threads may race to fill it; they store the
+// same value, and the atomic makes that well defined)
+static std::atomic<int> g_sm_count{0};
 static int sm_count() {
-    if (!g_sm_count) {
+    int v = g_sm_count.load(std::memory_order_relaxed);
+    if (!v) {
         int dev = 0;
         cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev);
-        if (g_sm_count <= 0) g_sm_count = 1;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        if (v <= 0) v = 1;
+        g_sm_count.store(v, std::memory_order_relaxed);
     }
-    return g_sm_count;
+    return v;
 }
 
 // Blocks of `kern` (256 threads, no dynamic shared memory) resident per SM,
